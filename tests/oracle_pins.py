@@ -1,0 +1,233 @@
+"""Pins of the FP64 oracle: closed forms, invariants and exact discrete
+solutions that fix each part of the coupled step independently of the oracle
+itself.  Each check takes a factory ``make(nx, ny, **kw) -> Oracle`` so the
+same checks run on the real oracle and on copies with planted mistakes.
+
+Every check returns (ok: bool, detail: str).
+"""
+
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+W, E, S, N = 0, 1, 2, 3
+DIR, ADI, PER, MOV = 0, 1, 2, 3
+
+
+def rest_state(make):
+    """No force, fluid at rest: f stays at the weights of Eq. 9 and u = 0 exactly."""
+    o = make(20, 13, nu=0.1, alpha=0.2, gbeta=0.0)
+    w = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)[:, None, None]
+    o.step(100)
+    f = o.f()
+    _, u, v, _ = o.fields()
+    err = np.abs(f - w).max()
+    ok = err <= 4e-16 and np.all(u == 0.0) and np.all(v == 0.0)
+    return ok, f"max|f - w| = {err:.3g}, u == 0: {np.all(u == 0.0) and np.all(v == 0.0)}"
+
+
+def mass_periodic(make, steps=10_000):
+    """Periodic box with buoyancy from a random T field: the collision, the
+    force (sum_i F_i = 0) and streaming conserve sum f to round-off."""
+    rng = np.random.default_rng(7)
+    o = make(32, 17, bc=(PER, PER, PER, PER), nu=0.1, alpha=0.2, gbeta=1e-5, t_ref=0.5)
+    o.set_state(T=rng.random((17, 32)))
+    m0 = o.f().sum()
+    o.step(steps)
+    rel = abs(o.f().sum() - m0) / m0
+    return rel <= 1e-11, f"relative mass change over {steps} steps = {rel:.3g}"
+
+
+def shear_wave(make):
+    """Periodic shear wave u_x = A sin(2 pi y / L): decays as exp(-nu k^2 t)
+    with nu = (tau - 1/2)/3 (Eq. 15)."""
+    L, nu, A = 64, 0.1, 1e-4
+    o = make(3, L, bc=(PER, PER, PER, PER), nu=nu, alpha=0.1, gbeta=0.0)
+    y = np.arange(L)
+    u0 = np.tile(A * np.sin(2 * np.pi * y / L)[:, None], (1, 3))
+    o.set_state(u=u0)
+    k = 2 * np.pi / L
+    amp = []
+    for t in (300, 3000):
+        o.step(t - o.step_count)
+        u = o.fields()[1][:, 1]
+        amp.append(2 / L * np.sum(u * np.sin(k * y)))
+    rate = math.log(amp[0] / amp[1]) / 2700
+    rel = abs(rate / (nu * k * k) - 1)
+    return rel <= 0.01, f"decay rate / (nu k^2) - 1 = {rel:.3g}"
+
+
+def advected_wave(make):
+    """Transverse wave on a uniform stream (Galilean invariance of Eq. 8's
+    quadratic terms): v = A sin(k x) on (U, 0) and u = A sin(k y) on (0, U)
+    both travel downstream at U."""
+    L, nu, A, U, t = 64, 0.05, 1e-4, 0.05, 320
+    k = 2 * np.pi / L
+    s = np.arange(L)
+    speeds = []
+    for along_x in (True, False):
+        if along_x:
+            o = make(L, 3, bc=(PER, PER, PER, PER), nu=nu, alpha=0.1, gbeta=0.0)
+            o.set_state(u=np.full((3, L), U), v=np.tile(A * np.sin(k * s), (3, 1)))
+        else:
+            o = make(3, L, bc=(PER, PER, PER, PER), nu=nu, alpha=0.1, gbeta=0.0)
+            o.set_state(u=np.tile(A * np.sin(k * s)[:, None], (1, 3)), v=np.full((L, 3), U))
+        o.step(t)
+        prof = o.fields()[2][1] if along_x else o.fields()[1][:, 1]
+        c = np.sum(prof * np.cos(k * s))
+        sn = np.sum(prof * np.sin(k * s))
+        shift = math.atan2(-c, sn) / k  # profile ~ sin(k (s - shift))
+        speeds.append(shift / t)
+    rel = max(abs(sp / U - 1) for sp in speeds)
+    return rel <= 0.02, f"phase speeds / U - 1 = {[round(sp / U - 1, 6) for sp in speeds]}"
+
+
+def poiseuille(make, Hs=(8, 16, 32)):
+    """Force-driven channel between non-equilibrium-extrapolation walls:
+    steady u(y) = g y (H - y) / (2 nu); L2 error falls at second order."""
+    errs = []
+    for H in Hs:
+        nu, umax = 0.1, 0.01
+        g = 8 * nu * umax / H**2
+        o = make(3, H + 1, bc=(PER, PER, ADI, ADI), nu=nu, alpha=0.1, gbeta=0.0, fx=g)
+        o.step(int(3 * H * H / nu))
+        u = o.fields()[1][:, 1]
+        y = np.arange(H + 1)
+        ex = g * y * (H - y) / (2 * nu)
+        errs.append(float(np.sqrt(np.mean((u - ex) ** 2)) / umax))
+    orders = [math.log2(errs[i] / errs[i + 1]) for i in range(len(errs) - 1)]
+    ok = min(orders) >= 1.8 and errs[0] < 0.05
+    return ok, f"errors {['%.3g' % e for e in errs]}, orders {['%.3f' % p for p in orders]}"
+
+
+def conduction_linear(make, H=16):
+    """Pure conduction between T = 1 (west) and T = 0 (east), adiabatic top
+    and bottom: the steady field is T = 1 - x/H to round-off and the one-sided
+    Nusselt number is exactly 1."""
+    o = make(H + 1, H + 1, nu=0.1, alpha=0.2, gbeta=0.0)
+    o.step(6000)
+    T = o.fields()[3]
+    x = np.arange(H + 1) / H
+    err = np.abs(T - (1 - x)[None, :]).max()
+    nh, _, nc, _ = o.nusselt()
+    ok = err <= 1e-12 and abs(nh - 1) <= 1e-12 and abs(nc - 1) <= 1e-12
+    return ok, f"max|T - (1 - x/H)| = {err:.3g}, Nu hot - 1 = {nh - 1:.3g}, Nu cold - 1 = {nc - 1:.3g}"
+
+
+def sine_mode_x(make, H=20, n=500, alpha=0.2):
+    """T_W = T_E = 0, adiabatic top/bottom, T0 = sin(pi x / H), no flow: the
+    discrete eigenvector decays by (1 - 4 alpha sin^2(pi/(2H))) per step."""
+    o = make(H + 1, 9, t_wall=(0, 0, 0, 0), nu=0.1, alpha=alpha, gbeta=0.0)
+    x = np.arange(H + 1)
+    T0 = np.tile(np.sin(np.pi * x / H), (9, 1))
+    o.set_state(T=T0)
+    o.step(n)
+    g = 1 - 4 * alpha * math.sin(math.pi / (2 * H)) ** 2
+    err = np.abs(o.fields()[3] - g**n * T0).max()
+    cont = math.exp(-alpha * (math.pi / H) ** 2 * n)
+    return err <= 1e-12, f"max error vs exact discrete decay = {err:.3g} (continuum factor {cont:.6f}, discrete {g**n:.6f})"
+
+
+def cosine_mode_y(make, H=16, n=400, alpha=0.2):
+    """Periodic in x, adiabatic bottom/top (half control volumes at the wall
+    rows): T0 = cos(pi y / H) decays by (1 - 4 alpha sin^2(pi/(2H))) per step."""
+    o = make(5, H + 1, bc=(PER, PER, ADI, ADI), nu=0.1, alpha=alpha, gbeta=0.0)
+    y = np.arange(H + 1)
+    T0 = np.tile(np.cos(np.pi * y / H)[:, None], (1, 5))
+    o.set_state(T=T0)
+    o.step(n)
+    g = 1 - 4 * alpha * math.sin(math.pi / (2 * H)) ** 2
+    err = np.abs(o.fields()[3] - g**n * T0).max()
+    return err <= 1e-12, f"max error vs exact discrete decay = {err:.3g}"
+
+
+def advected_temperature(make, L=32, n=200, alpha=0.05):
+    """Uniform stream (U, V) in a periodic box (an exact steady state of the
+    lattice Boltzmann part), T0 = cos(k x + l y): the explicit central
+    finite-volume update multiplies the Fourier mode by
+    g = 1 - 4 alpha (sin^2(k/2) + sin^2(l/2)) - i (U sin k + V sin l) per step."""
+    U, V = 0.06, -0.03
+    o = make(L, L, bc=(PER, PER, PER, PER), nu=0.1, alpha=alpha, gbeta=0.0)
+    k = 2 * np.pi * 2 / L
+    l = 2 * np.pi * 1 / L
+    yy, xx = np.mgrid[0:L, 0:L]
+    o.set_state(u=np.full((L, L), U), v=np.full((L, L), V), T=np.cos(k * xx + l * yy))
+    o.step(n)
+    g = 1 - 4 * alpha * (math.sin(k / 2) ** 2 + math.sin(l / 2) ** 2) - 1j * (U * math.sin(k) + V * math.sin(l))
+    exact = np.real(g**n * np.exp(1j * (k * xx + l * yy)))
+    err = np.abs(o.fields()[3] - exact).max()
+    return err <= 1e-11, f"max error vs exact discrete mode = {err:.3g}"
+
+
+def energy_adiabatic(make, n=1000):
+    """All walls adiabatic, buoyant flow from a random T: the conservative
+    flux form keeps sum V_P T_P constant to round-off."""
+    rng = np.random.default_rng(3)
+    o = make(24, 19, bc=(ADI, ADI, ADI, ADI), nu=0.05, alpha=0.15, gbeta=2e-3, t_ref=0.5)
+    o.set_state(T=rng.random((19, 24)))
+    V = o.cv_volumes()
+    e0 = np.sum(V * o.fields()[3])
+    o.step(n)
+    _, u, _, T = o.fields()
+    rel = abs(np.sum(V * T) - e0) / e0
+    moving = np.abs(u).max()
+    return rel <= 1e-13 and moving > 1e-5, f"relative energy change = {rel:.3g} (max|u| = {moving:.3g})"
+
+
+def quadratic_nusselt(make, H=20):
+    """Eq. 90 from the one-sided second-order stencil is exact for T quadratic
+    in x: T = 1 - X + c(Y) X (X - 1) gives Nu(Y) = 1 + c(Y); with c linear in Y
+    the trapezoid mean is 1 + c0 + c1/2."""
+    ny = H + 1  # X = x/H and Y = y/H share the cavity height H = ny - 1
+    o = make(H + 1, ny, nu=0.1, alpha=0.2, gbeta=0.0)
+    X = np.arange(H + 1) / H
+    Y = np.arange(ny) / (ny - 1)
+    c0, c1 = 0.7, -0.4
+    c = c0 + c1 * Y
+    T = 1 - X[None, :] + c[:, None] * X[None, :] * (X[None, :] - 1)
+    o.set_state(T=T)
+    mh, loc, _, _ = o.nusselt()
+    err = max(np.abs(loc - (1 + c)).max(), abs(mh - (1 + c0 + c1 / 2)))
+    return err <= 1e-12, f"max Nusselt error = {err:.3g}"
+
+
+def eq112_conduction(make, Hs=(8, 16, 32), alpha=0.25):
+    """Top-hot square conduction (Section 6.3.1, Eqs. 103-111) against the
+    series solution Eq. 112: the error at fixed interior points falls at
+    second order with the grid."""
+    pts = [(0.25, 0.5), (0.5, 0.5), (0.75, 0.75), (0.5, 0.25)]
+
+    def series(X, Y, terms=400):
+        s = 0.0
+        for n in range(1, terms + 1):
+            s += ((-1) ** (n + 1) + 1) / n * math.sin(n * math.pi * X) * \
+                 math.exp(n * math.pi * (Y - 1)) * (1 - math.exp(-2 * n * math.pi * Y)) / (1 - math.exp(-2 * n * math.pi))
+        return 2 / math.pi * s
+
+    errs = []
+    for H in Hs:
+        o = make(H + 1, H + 1, bc=(DIR, DIR, DIR, DIR), t_wall=(0, 0, 0, 1), t_init=0.0, nu=0.1,
+                 alpha=alpha, gbeta=0.0)
+        o.step(int(4 * H * H / alpha))
+        T = o.fields()[3]
+        e = max(abs(T[int(round(Y * H)), int(round(X * H))] - series(X, Y)) for X, Y in pts)
+        errs.append(e)
+    orders = [math.log2(errs[i] / errs[i + 1]) for i in range(len(errs) - 1)]
+    return min(orders) >= 1.8, f"errors {['%.3g' % e for e in errs]}, orders {['%.3f' % p for p in orders]}"
+
+
+QUICK = {
+    "rest_state": rest_state,
+    "mass_periodic": lambda m: mass_periodic(m, 2000),
+    "shear_wave": shear_wave,
+    "advected_wave": advected_wave,
+    "poiseuille": lambda m: poiseuille(m, (8, 16)),
+    "conduction_linear": conduction_linear,
+    "sine_mode_x": sine_mode_x,
+    "cosine_mode_y": cosine_mode_y,
+    "advected_temperature": advected_temperature,
+    "energy_adiabatic": energy_adiabatic,
+    "quadratic_nusselt": quadratic_nusselt,
+}

@@ -1,0 +1,53 @@
+"""Plant plausible mistakes in a copy of the oracle (on the CPU) and check that
+each one fails at least one pin: the pins constrain every part of the step."""
+
+import os
+
+import pytest
+
+import oracle
+import oracle_pins as P
+
+MUTANTS = {
+    "collision_sign": ("o->fs[q * n + k] = fv - (fv - fe) / tau + F;", "o->fs[q * n + k] = fv + (fv - fe) / tau + F;"),
+    "feq_drop_quadratic": ("eu * eu / (2.0 * CS2 * CS2)", "0.0"),
+    "feq_drop_u2": ("- uu / (2.0 * CS2))", ")"),
+    "force_drop_minus_u": ("(Gx * (EX[q] - ux) + Gy * (EY[q] - uy))", "(Gx * EX[q] + Gy * EY[q])"),
+    "force_missing_cs2": ("* fe / (RHO0 * CS2);", "* fe / RHO0;"),
+    "weight_diagonal": ("1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0}", "1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 35.0}"),
+    "tau_without_half": ("o->tau = nu / CS2 + 0.5;", "o->tau = nu / CS2 + 0.6;"),
+    "stream_push_direction": ("int s = nbr(o, i, j, -EX[q], -EY[q]);", "int s = nbr(o, i, j, -EX[q], EY[q]);"),
+    "nee_partner_velocity": ("feq(q, rf, o->uw[k], o->vw[k])", "feq(q, rf, uf, vf)"),
+    "fv_convective_sign": ("acc += -Fl * Tf + alpha", "acc += Fl * Tf + alpha"),
+    "fv_face_velocity_one_sided": ("(o->ux[k] + o->ux[m]) * dx", "(o->ux[k] + o->ux[k]) * dx"),
+    "fv_half_cv_y": ("return 0.5 * (j > 0) + 0.5 * (j < o->ny - 1);", "return 1.0;"),
+    "fv_diffusion_area": ("alpha * A * (o->T[m] - TP)", "alpha * (o->T[m] - TP)"),
+    "nusselt_first_order": ("(-3.0 * r[0] + 4.0 * r[1] - r[2]) / (2.0 * dT)", "(-r[0] + r[1]) / dT"),
+    "nusselt_trapezoid": ("(j == 0 || j == ny - 1) ? 0.5 : 1.0", "1.0"),
+}
+
+
+@pytest.fixture(scope="module")
+def source():
+    return oracle.source_text()
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_mutant_is_caught(name, source, tmp_path):
+    old, new = MUTANTS[name]
+    assert source.count(old) == 1, f"mutation site for {name} not found exactly once"
+    path = oracle.build_variant(source.replace(old, new), os.path.join(str(tmp_path), f"m_{name}.so"))
+    lib = oracle.load_library(path)
+
+    def make(*a, **k):
+        return oracle.Oracle(*a, lib=lib, **k)
+
+    failures = []
+    for pin_name, pin in P.QUICK.items():
+        try:
+            ok, detail = pin(make)
+        except Exception as exc:  # a mutant may also blow up outright
+            ok, detail = False, f"raised {exc!r}"
+        if not ok:
+            failures.append(pin_name)
+    assert failures, f"mutant {name} passed every pin"

@@ -1,0 +1,72 @@
+"""The oracle's steady cavity solutions against the numbers the paper prints
+(tests/golden/paper_tables.json): Section 5.2 Tables 1-2 (hybrid method,
+160 x 160 grid, Pr = 0.71) and Section 6.3.2 Table 3 (benchmark mean Nusselt
+numbers).  The paper states that every method lies within 3 % of the
+reference; the oracle is held to 2 % of the hybrid column, the location of
+the maximum to one node, and the mean to 2 % of the benchmark."""
+
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+
+GOLDEN = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_tables.json")))
+MA = 0.1 * 3**0.5  # U0 = 0.1
+
+
+def steady(n, Ra, tol=1e-7, max_k=400):
+    """Run in chunks of 1000 steps until the velocity residual is below tol."""
+    o = oracle.Oracle.from_groups(n, n, Ra, 0.71, MA)
+    for _ in range(max_k):
+        o.step(1000)
+        r = o.residual()
+        if r < tol:
+            break
+    assert r < tol, f"not steady after {max_k * 1000} steps (residual {r:.3g})"
+    return o
+
+
+def nu_max_interior(loc):
+    # Eq. 90 evaluated on the rows strictly between the corner rows.
+    j = int(np.argmax(loc[1:-1])) + 1
+    return loc[j], j
+
+
+def test_table1_table2_table3_ra1e4_160_grid():
+    H = 160
+    o = steady(H + 1, 1e4)
+    mean_hot, loc, mean_cold, _ = o.nusselt()
+    t1 = GOLDEN["table1_nu_max"]
+    t2 = GOLDEN["table2_y_nu_max"]
+    t3 = GOLDEN["table3_nu"]
+    nmax, j = nu_max_interior(loc)
+    assert nmax == pytest.approx(t1["hybrid"][0], rel=0.02)
+    assert abs(j / H - t2["hybrid"][0]) <= 1.0 / H + 1e-9
+    assert mean_hot == pytest.approx(t3["reference_nu_ave"][0], rel=0.02)
+    # energy balance at steady state: hot wall, cold wall and every vertical
+    # face line carry the same heat
+    flux = o.flux_nusselt()
+    assert np.ptp(flux) <= 1e-4 * flux.mean()
+    assert mean_cold == pytest.approx(mean_hot, rel=1e-3)
+    assert flux.mean() == pytest.approx(mean_hot, rel=1e-3)
+
+
+def test_table3_mean_nusselt_ra1e5_80_grid():
+    o = steady(81, 1e5, max_k=150)
+    mean_hot, _, _, _ = o.nusselt()
+    assert mean_hot == pytest.approx(GOLDEN["table3_nu"]["reference_nu_ave"][1], rel=0.02)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("idx", [1, 2])
+def test_table1_table2_ra1e5_ra1e6_160_grid(idx):
+    H = 160
+    Ra = GOLDEN["table1_nu_max"]["Ra"][idx]
+    o = steady(H + 1, Ra, max_k=600)
+    _, loc, _, _ = o.nusselt()
+    nmax, j = nu_max_interior(loc)
+    assert nmax == pytest.approx(GOLDEN["table1_nu_max"]["hybrid"][idx], rel=0.03)
+    assert abs(j / H - GOLDEN["table2_y_nu_max"]["hybrid"][idx]) <= 1.0 / H + 1e-9
