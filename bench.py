@@ -1,0 +1,348 @@
+#!/usr/bin/env python3
+"""Benchmark of the coupled LBM-FVM natural-convection step on GB300.
+
+Workload: the differentially heated square cavity of 1024 x 1024 nodes,
+Ra = 1e6, Pr = 0.71, U0 = 0.1 (100,000 coupled steps when run with the
+default --steps 100 --chunk 1000), synthetic and seeded (no dataset exists or
+is needed).  One benchmark step is one pass over the whole hot path: `chunk`
+fused coupled steps (pull stream, wall extrapolation, moments, explicit
+finite-volume energy update, forced BGK collision), the FP64 residual
+reduction and the FP64 Nusselt reduction, with the residual and Nusselt
+number read back to the host.
+
+Metric: coupled MLUPS = nodes x coupled steps / second / 1e6, whole job.
+`--impl reference` times the FP64 CPU oracle on the host cores instead.
+
+Prints one JSON line (rank 0).
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "coupled MLUPS (1024^2 cavity, Ra 1e6) & % HBM peak"
+# Algorithmic bytes per lattice update of the fused step: read + write the
+# nine populations, read + write T, read the node code.
+BYTES_PER_LU = {"f64": 72 + 72 + 8 + 8 + 1, "f32": 36 + 36 + 4 + 4 + 1, "f16": 18 + 18 + 4 + 4 + 1,
+                "bf16": 18 + 18 + 4 + 4 + 1}
+L2_FLUSH_BYTES = 512 << 20
+FALLBACK_HBM_GBS = 6800.0
+
+# DRAM bytes per launch of step_kernel from one ncu capture
+# (profiles/step_kernel_*.md), valid only for the kernel source hashed here.
+NCU_TRAFFIC = {}
+
+
+def kernel_hash() -> str:
+    p = os.path.join(ROOT, "paper_1908_08386_gb300", "csrc", "kernels.cuh")
+    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+
+
+def measured_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.out = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.out, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.out.close()
+        rows = [ln.split(",") for ln in open(self.path).read().strip().splitlines() if ln.strip()]
+        os.unlink(self.path)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, r[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup(n_gpus: int):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+
+        local = int(os.environ.get("LOCAL_RANK", "0"))
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+        return dist.get_rank(), world, local
+    return 0, 1, 0
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def oracle_mlups(n: int, seconds: float, chunk: int = 2):
+    """Time the FP64 oracle on the host cores on the n x n Ra 1e6 cavity:
+    steps in chunks until `seconds` have passed."""
+    import oracle
+    from paper_1908_08386_gb300 import workloads as WL
+
+    case = WL.config_large(n)
+    o = oracle.Oracle.from_groups(case.nx, case.ny, case.Ra, case.Pr, case.Ma)
+    o.step(1)  # first touch of the arrays
+    steps, t0 = 0, time.perf_counter()
+    while True:
+        o.step(chunk)
+        steps += chunk
+        dt = time.perf_counter() - t0
+        if dt >= seconds:
+            break
+    return case.nx * case.ny * steps / dt / 1e6, steps, dt, oracle.num_threads()
+
+
+def run_reference(args):
+    rank, world, _ = dist_setup(args.gpus)
+    if rank != 0:
+        return
+    import oracle
+    from paper_1908_08386_gb300 import workloads as WL
+
+    case = WL.config_large(args.size)
+    o = oracle.Oracle.from_groups(case.nx, case.ny, case.Ra, case.Pr, case.Ma)
+    per = args.ref_chunk
+    for _ in range(args.warmup):
+        o.step(per)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        o.step(per)
+        o.residual()
+        o.nusselt()
+    dt = time.perf_counter() - t0
+    value = case.nx * case.ny * per * args.steps / dt / 1e6
+    cores = oracle.num_threads()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"cavity {case.nx}x{case.ny}, Ra 1e6, Pr 0.71, U0 0.1",
+                   "coupled_steps_per_step": per, "l2": "host CPU run"},
+        "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+                         "sample": f"{per * args.steps} coupled steps of the {case.nx}x{case.ny} cavity "
+                                   f"(plus residual and Nusselt every {per})"},
+        "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_setup(args.gpus)
+    if world == 1:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    import paper_1908_08386_gb300 as L
+    from paper_1908_08386_gb300 import workloads as WL
+
+    # CPU baseline first (rank 0, N = 1 only), before any device work.
+    cpu = None
+    if rank == 0 and world == 1 and args.cpu_seconds > 0:
+        v, steps, dt, cores = oracle_mlups(args.size, args.cpu_seconds)
+        cpu = {"value": v, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+               "sample": f"{steps} coupled steps of the {args.size}x{args.size} Ra 1e6 cavity in {dt:.1f} s"}
+
+    case = WL.config_large(args.size)
+    n_nodes = case.nx * case.ny
+    cav = L.Cavity(case.nx, case.ny, Ra=case.Ra, Pr=case.Pr, Ma=case.Ma, store=args.store, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    def bench_step():
+        cav.step(args.chunk)
+        r = cav.residual()
+        nu, _, _ = cav.nusselt()
+        return r, nu
+
+    for _ in range(args.warmup):
+        bench_step()
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(local) if rank == 0 else None
+    barrier(world)
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.start()
+    t_wall0 = time.perf_counter()
+    total_ms = 0.0
+    last = None
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        last = bench_step()
+        e1.record(stream)
+        e1.synchronize()
+        total_ms += e0.elapsed_time(e1)
+    torch.cuda.synchronize()
+    barrier(world)
+    wall_s = time.perf_counter() - t_wall0
+    clocks = sampler.stop() if sampler else None
+    total_ms = max_over_ranks(total_ms, world)
+    value = world * n_nodes * args.chunk * args.steps / (total_ms * 1e-3) / 1e6
+
+    # Dominant kernel: step_kernel.  Average launch duration over a run of
+    # back-to-back launches (graph replays) on the same stream.
+    flush.zero_()
+    torch.cuda.synchronize()
+    k_launches = args.chunk
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    cav.step(k_launches)
+    e1.record(stream)
+    e1.synchronize()
+    launch_s = e0.elapsed_time(e1) * 1e-3 / k_launches
+    bytes_per_launch = BYTES_PER_LU[args.store] * n_nodes
+    achieved = bytes_per_launch / launch_s / 1e9
+    peak, peak_kind = measured_peak()
+    traffic = NCU_TRAFFIC.get((args.store, args.size, kernel_hash()))
+
+    # End to end through the C-ABI with host buffers: each step uploads the
+    # initial (u, v, T) from pinned host memory, runs the chunk, reads back the
+    # residual, the Nusselt number and (u, v, T).
+    e2e = None
+    if not args.no_e2e:
+        shp = (case.ny, case.nx)
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).pin_memory()
+        u0 = pin(np.zeros(shp))
+        v0 = pin(np.zeros(shp))
+        T0 = pin(np.full(shp, 0.5))
+        uo, vo, To = (torch.empty(shp, dtype=torch.float32).pin_memory() for _ in range(3))
+        loc = np.empty(case.ny)
+        ke = max(1, min(args.steps, args.e2e_steps))
+        torch.cuda.synchronize()
+        barrier(world)
+        t0 = time.perf_counter()
+        for _ in range(ke):
+            L.lbmfvm_set_state(cav.h, u0, v0, T0)
+            cav.step(args.chunk)
+            cav.residual()
+            L.lbmfvm_nusselt(cav.h, loc)
+            L.lbmfvm_fields_f32(cav.h, None, uo, vo, To)
+        torch.cuda.synchronize()
+        e2e_s = max_over_ranks(time.perf_counter() - t0, world)
+        e2e = {"value": world * n_nodes * args.chunk * ke / e2e_s / 1e6, "unit": "MLUPS",
+               "h2d_bytes_per_step": 3 * 4 * n_nodes,
+               "d2h_bytes_per_step": 3 * 4 * n_nodes + 8 * case.ny + 16, "steps": ke}
+
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": args.store, "data": "synthetic",
+        "config": {"workload": f"cavity {case.nx}x{case.ny}, Ra 1e6, Pr 0.71, U0 0.1, {args.store} storage",
+                   "coupled_steps_per_step": args.chunk, "total_coupled_steps": args.chunk * args.steps,
+                   "parallelism": f"replicas x{world} (one cavity per GPU)",
+                   "l2": "512 MB buffer written between timed steps; the state is re-read every coupled step",
+                   "wall_s": wall_s, "final_residual": last[0] if last else None,
+                   "final_nusselt": last[1] if last else None},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": traffic, "kernel": "step_kernel", "peak_kind": peak_kind,
+                     "algorithmic_bytes_per_launch": bytes_per_launch, "avg_launch_us": launch_s * 1e6},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": args.steps * (args.chunk + 3),
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--size", type=int, default=1024)
+    ap.add_argument("--chunk", type=int, default=1000, help="coupled steps per benchmark step")
+    ap.add_argument("--store", choices=["f32", "f16", "bf16", "f64"], default="f32")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--ref-chunk", type=int, default=10, help="coupled steps per reference-arm step")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,185 @@
+/*
+ * lbmfvm — GB300 (sm_103a) coupled lattice-Boltzmann / finite-volume solver
+ * for natural convection: the hybrid LBM(velocity) + FVM(temperature) method
+ * of Li, Yang & Zhang, arXiv 1908.08386, Section 5.
+ *
+ * One time step of a handle is one launch of a fused CUDA kernel that, per
+ * node,
+ *   - pulls the post-collision D2Q9 populations of the previous step from the
+ *     neighbours (Eq. 5, velocity set of Eq. 4, weights of Eq. 9);
+ *   - rebuilds wall nodes by non-equilibrium extrapolation from their inner
+ *     partner node x_f with rho_b = rho(x_f) (Eqs. 60, 94, 96);
+ *   - takes the moments rho, u (Eqs. 16-17);
+ *   - advances T by an explicit finite-volume energy balance over the
+ *     node-centred control volume (grid setting 1 of Section 5.1, energy
+ *     equation Eq. 76), with face velocities interpolated from the new u;
+ *   - relaxes toward the equilibrium of Eq. 8 with the Boussinesq buoyancy
+ *     force of Eqs. 18 and 81 evaluated with the new T, and stores the result.
+ *
+ * Conventions shared by every entry point:
+ *   - Every function returns an int status: LBMFVM_OK (0) or a negative
+ *     LBMFVM_ERR_* code.  Nothing throws or exits across this boundary.
+ *     lbmfvm_last_error() gives a one-line message for the last failure.
+ *   - Fields are row-major [ny][nx], x fastest, j = 0 the bottom row.
+ *     Lengths are in lattice units (node spacing 1, time step 1); the cavity
+ *     height is H = ny - 1 (N nodes per side span N - 1 spacings).
+ *   - Input and output pointers may be host or device memory (the library
+ *     copies with cudaMemcpyDefault).  The caller keeps ownership of all of
+ *     them; nothing is retained after the call returns.
+ *   - Work is ordered after all work previously enqueued on the handle's
+ *     stream (lbmfvm_opts_t.cuda_stream), and later work on that stream is
+ *     ordered after it.  Calls that return values to the caller synchronise.
+ *   - A handle is not thread-safe: use one handle per host thread.
+ */
+#ifndef LBMFVM_H
+#define LBMFVM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+#define LBMFVM_OK 0
+#define LBMFVM_ERR_ARG (-1)      /* invalid argument, size or null handle */
+#define LBMFVM_ERR_UNSTABLE (-2) /* parameters outside the scheme's stability limits */
+#define LBMFVM_ERR_CUDA (-3)     /* a CUDA runtime call or kernel failed */
+#define LBMFVM_ERR_DIVERGED (-4) /* a reduction met a non-finite value */
+#define LBMFVM_ERR_TIMEOUT (-5)  /* a bounded device-side wait ran out */
+#define LBMFVM_ERR_NOMEM (-6)    /* device allocation failed or workspace too small */
+
+/* Sides of the rectangle, index into lbmfvm_grid_t.bc / t_wall. */
+#define LBMFVM_SIDE_W 0
+#define LBMFVM_SIDE_E 1
+#define LBMFVM_SIDE_S 2
+#define LBMFVM_SIDE_N 3
+
+/* Boundary kinds.  Walls are no-slip nodes rebuilt by non-equilibrium
+ * extrapolation (Eqs. 94, 96).  DIRICHLET holds T at t_wall (Eqs. 77-78);
+ * ADIABATIC has zero heat flux through the wall (Eqs. 79-80); MOVING is an
+ * adiabatic wall sliding tangentially at u_lid (lid-driven flow, Section 3);
+ * PERIODIC must be set on both opposite sides. */
+#define LBMFVM_BC_DIRICHLET 0
+#define LBMFVM_BC_ADIABATIC 1
+#define LBMFVM_BC_PERIODIC 2
+#define LBMFVM_BC_MOVING 3
+
+/* Storage precision of the distributions.  F32/F16/BF16 store f - w_i and
+ * compute in FP32 with FP32 temperature; F64 stores and computes in FP64. */
+#define LBMFVM_F64 0
+#define LBMFVM_F32 1
+#define LBMFVM_F16 2
+#define LBMFVM_BF16 3
+
+typedef struct lbmfvm lbmfvm_t;
+
+/* Geometry and boundary conditions of one cavity. */
+typedef struct {
+    int32_t nx, ny;    /* nodes along x and y, each >= 3 */
+    int32_t bc[4];     /* LBMFVM_BC_* per side W, E, S, N */
+    double t_wall[4];  /* wall temperature of DIRICHLET sides (W = hot, E = cold) */
+    double u_lid;      /* tangential speed of MOVING sides */
+    double t_init;     /* uniform initial temperature of the default state */
+} lbmfvm_grid_t;
+
+/* Options; fill with lbmfvm_opts_default() first. */
+typedef struct {
+    int32_t store;          /* LBMFVM_F64/F32/F16/BF16; default LBMFVM_F32 */
+    int32_t tile_y;         /* rows per thread block of the step kernel: 0 = default,
+                               else one of 4, 8, 16 */
+    double t_ref;           /* reference temperature of the buoyancy term; NaN (the
+                               default) selects T_l = t_wall[E] as in Eq. 81 */
+    void *cuda_stream;      /* cudaStream_t the handle orders its work on; NULL =
+                               the legacy default stream */
+    void *workspace;        /* device memory of at least lbmfvm_workspace_bytes(),
+                               256-byte aligned, owned by the caller and kept alive
+                               until lbmfvm_destroy; NULL = the library allocates */
+    size_t workspace_bytes; /* size of workspace */
+} lbmfvm_opts_t;
+
+/* Fill *opts with the defaults listed above. */
+void lbmfvm_opts_default(lbmfvm_opts_t *opts);
+
+/* Device bytes one handle of this grid and options needs (the distributions,
+ * two temperature planes, node codes, a velocity snapshot and reduction
+ * scratch).  Returns LBMFVM_ERR_ARG for an invalid grid. */
+int lbmfvm_workspace_bytes(const lbmfvm_grid_t *grid, const lbmfvm_opts_t *opts, size_t *bytes);
+
+/* Create a cavity from the nondimensional groups (Eqs. 83-89):
+ *   U0 = Ma/sqrt(3) (Eq. 84, u_c = sqrt(g beta dT H), c_s = 1/sqrt(3)),
+ *   nu = U0 H sqrt(Pr/Ra), alpha = U0 H / sqrt(Ra Pr), g beta dT = U0^2/H,
+ *   tau = 3 nu + 1/2 (Eq. 15), dT = t_wall[W] - t_wall[E] (must be non-zero).
+ * mask: ny*nx bytes, 1 = solid obstacle node, may be NULL; copied at create.
+ * The state starts at rest, f = w_i, T = grid->t_init, Dirichlet nodes at
+ * their wall value.  opts may be NULL (defaults).
+ * Returns LBMFVM_ERR_UNSTABLE if tau < 0.51, alpha > 0.25 (explicit diffusion
+ * limit), U0^2 > 2 alpha (explicit central advection limit) or Ma > 0.3. */
+int lbmfvm_create(const lbmfvm_grid_t *grid, const uint8_t *mask, double Ra, double Pr, double Ma,
+                  const lbmfvm_opts_t *opts, lbmfvm_t **out);
+
+/* Create from lattice parameters: kinematic viscosity nu (tau = 3 nu + 1/2),
+ * thermal diffusivity alpha, buoyancy coefficient gbeta and an extra uniform
+ * body force (force[0], force[1]) (may be NULL), so that the body force per
+ * unit mass is G = (force[0], force[1] + gbeta (T - t_ref)) (Eq. 81 with
+ * gravity along -y).  Returns LBMFVM_ERR_UNSTABLE if tau < 0.51 or
+ * alpha > 0.25. */
+int lbmfvm_create_lattice(const lbmfvm_grid_t *grid, const uint8_t *mask, double nu, double alpha,
+                          double gbeta, const double *force, const lbmfvm_opts_t *opts,
+                          lbmfvm_t **out);
+
+/* Reset the state: f = f_eq(1, (u, v)) (Eq. 8), T as given (Dirichlet nodes
+ * are reset to their wall value), step count 0, and the residual snapshot set
+ * to this velocity.  u, v, T: ny*nx floats each, host or device; any may be
+ * NULL (zero velocity, grid->t_init). */
+int lbmfvm_set_state(lbmfvm_t *h, const float *u, const float *v, const float *T);
+
+/* Enqueue n coupled time steps (n >= 0) on the handle's stream and return. */
+int lbmfvm_step(lbmfvm_t *h, int64_t n);
+
+/* Number of time steps taken since the last set_state. */
+int lbmfvm_step_count(const lbmfvm_t *h, int64_t *steps);
+
+/* Macroscopic fields of the current state: density, velocity (lattice units;
+ * divide by U0 for the nondimensional U, V of Eq. 85) and temperature.
+ * Each pointer may be NULL; otherwise ny*nx values, host or device.  Inert
+ * solid nodes report rho = u = v = 0.  Synchronises. */
+int lbmfvm_fields(lbmfvm_t *h, double *rho, double *u, double *v, double *T);
+int lbmfvm_fields_f32(lbmfvm_t *h, float *rho, float *u, float *v, float *T);
+
+/* Nusselt number of Eq. 90, Nu = -d theta/dX, at the hot west wall from the
+ * second-order one-sided difference (-3 T0 + 4 T1 - T2)/2 along each node row,
+ * theta = (T - t_wall[E])/(t_wall[W] - t_wall[E]), X = x/H; the mean is the
+ * trapezoid integral over Y in [0, 1].  The cold east wall uses the mirrored
+ * stencil.  Accumulated in FP64.  local_hot may be NULL, else ny doubles
+ * (host or device); either mean pointer may be NULL.  Synchronises. */
+int lbmfvm_nusselt(lbmfvm_t *h, double *mean_hot, double *local_hot, double *mean_cold);
+
+/* Steady-state residual ||u^n - u^s||_2 / ||u^n||_2 over fluid nodes in FP64,
+ * where u^s is the snapshot taken by the previous call (or by set_state); the
+ * current velocity becomes the new snapshot.  Returns LBMFVM_ERR_DIVERGED
+ * (with *r set to NaN) if a non-finite velocity was met.  Synchronises. */
+int lbmfvm_residual(lbmfvm_t *h, double *r);
+
+/* Step in chunks of check_every, computing the residual after each chunk,
+ * until it falls below tol or max_steps steps were taken.  steps_done and
+ * r_final may be NULL. */
+int lbmfvm_run_to_steady(lbmfvm_t *h, double tol, int64_t check_every, int64_t max_steps,
+                         int64_t *steps_done, double *r_final);
+
+/* Derived lattice parameters: nu, alpha, gbeta, tau (any may be NULL). */
+int lbmfvm_params(const lbmfvm_t *h, double *nu, double *alpha, double *gbeta, double *tau);
+
+/* Release the handle and any memory the library allocated.  NULL is a no-op. */
+void lbmfvm_destroy(lbmfvm_t *h);
+
+/* Message of the last failed call on h (or, for h == NULL, of the last failed
+ * create or argument check on this thread).  Never NULL. */
+const char *lbmfvm_last_error(const lbmfvm_t *h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBMFVM_H */

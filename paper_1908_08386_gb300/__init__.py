@@ -1,0 +1,293 @@
+"""Python binding of ``liblbmfvm.so``, the GB300 coupled LBM-FVM solver.
+
+The functions here carry the names of the C-ABI entry points declared in
+``include/lbmfvm.h`` and only marshal arguments; every step of the method runs
+in the CUDA kernels of the library.  PyTorch supplies device memory (the
+handle's workspace) and the CUDA stream.  There is no CPU fallback: if the
+library cannot be built or loaded, :func:`lib` raises.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+# Status codes
+LBMFVM_OK = 0
+LBMFVM_ERR_ARG = -1
+LBMFVM_ERR_UNSTABLE = -2
+LBMFVM_ERR_CUDA = -3
+LBMFVM_ERR_DIVERGED = -4
+LBMFVM_ERR_TIMEOUT = -5
+LBMFVM_ERR_NOMEM = -6
+# Sides
+LBMFVM_SIDE_W, LBMFVM_SIDE_E, LBMFVM_SIDE_S, LBMFVM_SIDE_N = 0, 1, 2, 3
+# Boundary kinds
+LBMFVM_BC_DIRICHLET, LBMFVM_BC_ADIABATIC, LBMFVM_BC_PERIODIC, LBMFVM_BC_MOVING = 0, 1, 2, 3
+# Storage precisions
+LBMFVM_F64, LBMFVM_F32, LBMFVM_F16, LBMFVM_BF16 = 0, 1, 2, 3
+PRECISIONS = {"f64": LBMFVM_F64, "f32": LBMFVM_F32, "f16": LBMFVM_F16, "bf16": LBMFVM_BF16}
+
+# Every entry point the header declares (checked by the test-suite).
+EXPORTS = (
+    "lbmfvm_opts_default", "lbmfvm_workspace_bytes", "lbmfvm_create", "lbmfvm_create_lattice",
+    "lbmfvm_set_state", "lbmfvm_step", "lbmfvm_step_count", "lbmfvm_fields", "lbmfvm_fields_f32",
+    "lbmfvm_nusselt", "lbmfvm_residual", "lbmfvm_run_to_steady", "lbmfvm_params", "lbmfvm_destroy",
+    "lbmfvm_last_error",
+)
+
+
+class lbmfvm_grid_t(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("bc", ctypes.c_int32 * 4),
+                ("t_wall", ctypes.c_double * 4), ("u_lid", ctypes.c_double), ("t_init", ctypes.c_double)]
+
+
+class lbmfvm_opts_t(ctypes.Structure):
+    _fields_ = [("store", ctypes.c_int32), ("tile_y", ctypes.c_int32), ("t_ref", ctypes.c_double),
+                ("cuda_stream", ctypes.c_void_p), ("workspace", ctypes.c_void_p),
+                ("workspace_bytes", ctypes.c_size_t)]
+
+
+class LbmfvmError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"lbmfvm error {code}: {msg}")
+        self.code = code
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load liblbmfvm.so (building it with nvcc if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            if not os.path.exists(path):
+                raise RuntimeError(f"liblbmfvm.so missing at {path}")
+            L = ctypes.CDLL(path)
+            vp, i32, i64, d = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+            G, O = ctypes.POINTER(lbmfvm_grid_t), ctypes.POINTER(lbmfvm_opts_t)
+            pp = ctypes.POINTER(ctypes.c_void_p)
+            dp, i64p = ctypes.POINTER(d), ctypes.POINTER(i64)
+            sig = {
+                "lbmfvm_opts_default": (None, [O]),
+                "lbmfvm_workspace_bytes": (ctypes.c_int, [G, O, ctypes.POINTER(ctypes.c_size_t)]),
+                "lbmfvm_create": (ctypes.c_int, [G, vp, d, d, d, O, pp]),
+                "lbmfvm_create_lattice": (ctypes.c_int, [G, vp, d, d, d, vp, O, pp]),
+                "lbmfvm_set_state": (ctypes.c_int, [vp, vp, vp, vp]),
+                "lbmfvm_step": (ctypes.c_int, [vp, i64]),
+                "lbmfvm_step_count": (ctypes.c_int, [vp, i64p]),
+                "lbmfvm_fields": (ctypes.c_int, [vp, vp, vp, vp, vp]),
+                "lbmfvm_fields_f32": (ctypes.c_int, [vp, vp, vp, vp, vp]),
+                "lbmfvm_nusselt": (ctypes.c_int, [vp, dp, vp, dp]),
+                "lbmfvm_residual": (ctypes.c_int, [vp, dp]),
+                "lbmfvm_run_to_steady": (ctypes.c_int, [vp, d, i64, i64, i64p, dp]),
+                "lbmfvm_params": (ctypes.c_int, [vp, dp, dp, dp, dp]),
+                "lbmfvm_destroy": (None, [vp]),
+                "lbmfvm_last_error": (ctypes.c_char_p, [vp]),
+            }
+            for name, (res, args) in sig.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+        return _lib
+
+
+def _check(code: int, handle=None):
+    if code != LBMFVM_OK:
+        msg = lib().lbmfvm_last_error(handle)
+        raise LbmfvmError(code, msg.decode() if msg else "")
+
+
+def _addr(a):
+    """Address of a numpy array or torch tensor (None passes NULL)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return ctypes.c_void_p(a.data_ptr())
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def make_grid(nx, ny, bc=(LBMFVM_BC_DIRICHLET, LBMFVM_BC_DIRICHLET, LBMFVM_BC_ADIABATIC, LBMFVM_BC_ADIABATIC),
+              t_wall=(1.0, 0.0, 0.0, 0.0), u_lid=0.0, t_init=0.5) -> lbmfvm_grid_t:
+    g = lbmfvm_grid_t()
+    g.nx, g.ny = int(nx), int(ny)
+    for s in range(4):
+        g.bc[s] = int(bc[s])
+        g.t_wall[s] = float(t_wall[s])
+    g.u_lid, g.t_init = float(u_lid), float(t_init)
+    return g
+
+
+def lbmfvm_opts_default() -> lbmfvm_opts_t:
+    o = lbmfvm_opts_t()
+    lib().lbmfvm_opts_default(ctypes.byref(o))
+    return o
+
+
+def lbmfvm_workspace_bytes(grid: lbmfvm_grid_t, opts: lbmfvm_opts_t | None = None) -> int:
+    out = ctypes.c_size_t()
+    _check(lib().lbmfvm_workspace_bytes(ctypes.byref(grid), ctypes.byref(opts) if opts else None, ctypes.byref(out)))
+    return out.value
+
+
+def lbmfvm_create(grid, mask, Ra, Pr, Ma, opts=None):
+    h = ctypes.c_void_p()
+    _check(lib().lbmfvm_create(ctypes.byref(grid), _addr(mask), float(Ra), float(Pr), float(Ma),
+                               ctypes.byref(opts) if opts else None, ctypes.byref(h)))
+    return h
+
+
+def lbmfvm_create_lattice(grid, mask, nu, alpha, gbeta, force=None, opts=None):
+    h = ctypes.c_void_p()
+    fp = None
+    if force is not None:
+        fp = (ctypes.c_double * 2)(float(force[0]), float(force[1]))
+    _check(lib().lbmfvm_create_lattice(ctypes.byref(grid), _addr(mask), float(nu), float(alpha), float(gbeta),
+                                       fp, ctypes.byref(opts) if opts else None, ctypes.byref(h)))
+    return h
+
+
+def lbmfvm_set_state(h, u=None, v=None, T=None):
+    _check(lib().lbmfvm_set_state(h, _addr(u), _addr(v), _addr(T)), h)
+
+
+def lbmfvm_step(h, n):
+    _check(lib().lbmfvm_step(h, int(n)), h)
+
+
+def lbmfvm_step_count(h) -> int:
+    out = ctypes.c_int64()
+    _check(lib().lbmfvm_step_count(h, ctypes.byref(out)), h)
+    return out.value
+
+
+def lbmfvm_fields(h, rho=None, u=None, v=None, T=None):
+    _check(lib().lbmfvm_fields(h, _addr(rho), _addr(u), _addr(v), _addr(T)), h)
+
+
+def lbmfvm_fields_f32(h, rho=None, u=None, v=None, T=None):
+    _check(lib().lbmfvm_fields_f32(h, _addr(rho), _addr(u), _addr(v), _addr(T)), h)
+
+
+def lbmfvm_nusselt(h, local_hot=None):
+    mh, mc = ctypes.c_double(), ctypes.c_double()
+    _check(lib().lbmfvm_nusselt(h, ctypes.byref(mh), _addr(local_hot), ctypes.byref(mc)), h)
+    return mh.value, mc.value
+
+
+def lbmfvm_residual(h) -> float:
+    r = ctypes.c_double()
+    _check(lib().lbmfvm_residual(h, ctypes.byref(r)), h)
+    return r.value
+
+
+def lbmfvm_run_to_steady(h, tol=1e-8, check_every=1000, max_steps=10**8):
+    done, r = ctypes.c_int64(), ctypes.c_double()
+    _check(lib().lbmfvm_run_to_steady(h, float(tol), int(check_every), int(max_steps), ctypes.byref(done),
+                                      ctypes.byref(r)), h)
+    return done.value, r.value
+
+
+def lbmfvm_params(h):
+    out = [ctypes.c_double() for _ in range(4)]
+    _check(lib().lbmfvm_params(h, *[ctypes.byref(x) for x in out]), h)
+    return tuple(x.value for x in out)
+
+
+def lbmfvm_destroy(h):
+    if h:
+        lib().lbmfvm_destroy(h)
+
+
+def lbmfvm_last_error(h=None) -> str:
+    return lib().lbmfvm_last_error(h).decode()
+
+
+class Cavity:
+    """One cavity on the current CUDA device.
+
+    Device memory for the state comes from a PyTorch uint8 tensor handed to
+    the library as its workspace; work is ordered on PyTorch's current stream.
+    Build it either from the nondimensional groups (``Ra``, ``Pr``, ``Ma``) or
+    from lattice parameters (``nu``, ``alpha``, ``gbeta``, ``force``).
+    """
+
+    def __init__(self, nx, ny, *, Ra=None, Pr=None, Ma=None, nu=None, alpha=None, gbeta=0.0, force=None,
+                 mask=None, store="f32", bc=(LBMFVM_BC_DIRICHLET, LBMFVM_BC_DIRICHLET, LBMFVM_BC_ADIABATIC,
+                                             LBMFVM_BC_ADIABATIC),
+                 t_wall=(1.0, 0.0, 0.0, 0.0), u_lid=0.0, t_init=0.5, t_ref=None, tile_y=0, device=None):
+        import torch
+
+        self.nx, self.ny = int(nx), int(ny)
+        self.grid = make_grid(nx, ny, bc, t_wall, u_lid, t_init)
+        self.opts = lbmfvm_opts_default()
+        self.opts.store = PRECISIONS[store] if isinstance(store, str) else int(store)
+        self.opts.tile_y = int(tile_y)
+        self.opts.t_ref = math.nan if t_ref is None else float(t_ref)
+        dev = torch.device("cuda" if device is None else device)
+        self.device = dev
+        nbytes = lbmfvm_workspace_bytes(self.grid, self.opts)
+        self._ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=dev)
+        base = self._ws.data_ptr()
+        aligned = (base + 255) // 256 * 256
+        self.opts.workspace = aligned
+        self.opts.workspace_bytes = nbytes
+        self.opts.cuda_stream = torch.cuda.current_stream(dev).cuda_stream
+        self._mask = None if mask is None else np.ascontiguousarray(mask, dtype=np.uint8).reshape(self.ny, self.nx)
+        with torch.cuda.device(dev):
+            if Ra is not None:
+                self.h = lbmfvm_create(self.grid, self._mask, Ra, Pr, Ma, self.opts)
+            else:
+                self.h = lbmfvm_create_lattice(self.grid, self._mask, nu, alpha, gbeta, force, self.opts)
+        self.nu, self.alpha, self.gbeta, self.tau = lbmfvm_params(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lbmfvm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_state(self, u=None, v=None, T=None):
+        conv = lambda a: None if a is None else (a if hasattr(a, "data_ptr") else
+                                                np.ascontiguousarray(a, dtype=np.float32).reshape(self.ny, self.nx))
+        u, v, T = conv(u), conv(v), conv(T)
+        lbmfvm_set_state(self.h, u, v, T)
+
+    def step(self, n=1):
+        lbmfvm_step(self.h, n)
+
+    @property
+    def steps(self):
+        return lbmfvm_step_count(self.h)
+
+    def fields(self):
+        shp = (self.ny, self.nx)
+        rho, u, v, T = (np.empty(shp) for _ in range(4))
+        lbmfvm_fields(self.h, rho, u, v, T)
+        return rho, u, v, T
+
+    def nusselt(self):
+        loc = np.empty(self.ny)
+        mh, mc = lbmfvm_nusselt(self.h, loc)
+        return mh, loc, mc
+
+    def residual(self):
+        return lbmfvm_residual(self.h)
+
+    def run_to_steady(self, tol=1e-8, check_every=1000, max_steps=10**8):
+        return lbmfvm_run_to_steady(self.h, tol, check_every, max_steps)

@@ -1,0 +1,56 @@
+"""Build the sm_103a CUDA library ``liblbmfvm.so`` in place with nvcc.
+
+One translation unit, one ``-gencode`` (compute_103a / sm_103a), static CUDA
+runtime, so the library loads on a machine without a GPU driver (the driver
+is only needed at the first CUDA call).
+"""
+
+from __future__ import annotations
+
+import os
+import shutil
+import subprocess
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(PKG)
+CSRC = os.path.join(PKG, "csrc")
+INCLUDE = os.path.join(ROOT, "include")
+LIB = os.path.join(PKG, "liblbmfvm.so")
+SOURCES = [os.path.join(CSRC, "lbmfvm.cu")]
+DEPS = SOURCES + [os.path.join(CSRC, "kernels.cuh"), os.path.join(INCLUDE, "lbmfvm.h")]
+ARCH = "-gencode=arch=compute_103a,code=sm_103a"
+
+
+def nvcc() -> str:
+    for cand in (shutil.which("nvcc"), "/usr/local/cuda/bin/nvcc"):
+        if cand and os.path.exists(cand):
+            return cand
+    raise RuntimeError("nvcc not found: the CUDA toolkit is required to build liblbmfvm.so")
+
+
+def command(out: str = LIB, verbose_ptxas: bool = False) -> list[str]:
+    cmd = [nvcc(), "-O3", "-std=c++17", ARCH, "-lineinfo", "-Xcompiler", "-fPIC", "-shared",
+           "-I" + INCLUDE, "-o", out] + SOURCES
+    if verbose_ptxas:
+        cmd.insert(1, "-Xptxas=-v")
+    return cmd
+
+
+def stale() -> bool:
+    if not os.path.exists(LIB):
+        return True
+    t = os.path.getmtime(LIB)
+    return any(os.path.getmtime(p) > t for p in DEPS)
+
+
+def build(force: bool = False, verbose_ptxas: bool = False) -> str:
+    """Compile liblbmfvm.so if missing or older than its sources; return its path."""
+    if force or stale():
+        tmp = LIB + ".tmp"
+        subprocess.run(command(tmp, verbose_ptxas), check=True, cwd=ROOT)
+        os.replace(tmp, LIB)
+    return LIB
+
+
+if __name__ == "__main__":
+    print(build(force=True, verbose_ptxas=True))

@@ -1,0 +1,651 @@
+// Host runtime and C-ABI of the coupled LBM-FVM solver (include/lbmfvm.h).
+//
+// A handle owns (or borrows, when the caller passes a workspace) one device
+// block holding the double-buffered distributions, two temperature planes,
+// per-node codes, the residual snapshot and reduction scratch.  Steps run on
+// a private non-blocking stream joined to the caller's stream with events,
+// so that long runs can replay a captured CUDA graph of many launches.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "kernels.cuh"
+#include "lbmfvm.h"
+
+using namespace lbmfvm_dev;
+
+namespace {
+
+constexpr int kGraphSteps = 64;      // launches per captured graph (even)
+constexpr int kResidualBlocks = 608; // 4 x 152 SMs
+constexpr size_t kAlign = 256;
+
+thread_local char g_err[512] = "";
+
+int fail_thread(int code, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+size_t store_size(int prec) {
+    switch (prec) {
+        case LBMFVM_F64: return 8;
+        case LBMFVM_F32: return 4;
+        case LBMFVM_F16: return 2;
+        case LBMFVM_BF16: return 2;
+    }
+    return 0;
+}
+
+struct Layout {
+    int pitch;
+    long long plane;
+    size_t f[2], T[2], code, snap, stage, red, total;
+};
+
+Layout make_layout(const lbmfvm_grid_t &g, int prec) {
+    Layout L{};
+    L.pitch = (int)align_up((size_t)g.nx, 64);
+    L.plane = (long long)g.ny * L.pitch;
+    const size_t ss = store_size(prec), cs = prec == LBMFVM_F64 ? 8 : 4;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off = align_up(off + bytes, kAlign);
+        return o;
+    };
+    L.f[0] = take(9 * (size_t)L.plane * ss);
+    L.f[1] = take(9 * (size_t)L.plane * ss);
+    L.T[0] = take((size_t)L.plane * cs);
+    L.T[1] = take((size_t)L.plane * cs);
+    L.code = take((size_t)L.plane);
+    L.snap = take(2 * (size_t)g.nx * g.ny * sizeof(double));
+    L.stage = take(2 * (size_t)g.nx * g.ny * sizeof(double));
+    L.red = take((2 * kResidualBlocks + 8 + (size_t)g.ny) * sizeof(double));
+    L.total = off;
+    return L;
+}
+
+int check_grid(const lbmfvm_grid_t *g) {
+    if (!g) return fail_thread(LBMFVM_ERR_ARG, "grid is NULL");
+    if (g->nx < 3 || g->ny < 3) return fail_thread(LBMFVM_ERR_ARG, "nx and ny must be >= 3 (got %d x %d)", g->nx, g->ny);
+    if ((long long)g->nx * g->ny > (1LL << 30))
+        return fail_thread(LBMFVM_ERR_ARG, "grid of %d x %d nodes exceeds 2^30 nodes", g->nx, g->ny);
+    for (int s = 0; s < 4; s++)
+        if (g->bc[s] < LBMFVM_BC_DIRICHLET || g->bc[s] > LBMFVM_BC_MOVING)
+            return fail_thread(LBMFVM_ERR_ARG, "bc[%d] = %d is not a LBMFVM_BC_* value", s, g->bc[s]);
+    if ((g->bc[0] == LBMFVM_BC_PERIODIC) != (g->bc[1] == LBMFVM_BC_PERIODIC) ||
+        (g->bc[2] == LBMFVM_BC_PERIODIC) != (g->bc[3] == LBMFVM_BC_PERIODIC))
+        return fail_thread(LBMFVM_ERR_ARG, "periodic sides must come in opposite pairs");
+    return LBMFVM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Node classification (boundary treatment of the non-equilibrium
+// extrapolation scheme, Eqs. 94 and 96; thermal conditions Eqs. 77-80).
+//   box-border nodes of non-periodic sides -> wall, partner = inward normal
+//   neighbour (inward diagonal at corners);
+//   mask-solid nodes with a fluid 8-neighbour -> obstacle wall, partner = first
+//   fluid neighbour in the order E, N, W, S, NE, NW, SW, SE (the same search is
+//   the fallback of a box wall whose normal neighbour is not fluid);
+//   walls without any fluid neighbour -> inert.
+// Thermal roles: Dirichlet on DIRICHLET sides (vertical sides own corners,
+// a corner is Dirichlet if either side is), obstacle nodes copy their
+// partner's temperature, everything else is a finite-volume node.
+// ---------------------------------------------------------------------------
+std::vector<uint8_t> classify(const lbmfvm_grid_t &g, const uint8_t *mask, int pitch) {
+    const int nx = g.nx, ny = g.ny;
+    const bool perx = g.bc[LBMFVM_SIDE_W] == LBMFVM_BC_PERIODIC;
+    const bool pery = g.bc[LBMFVM_SIDE_S] == LBMFVM_BC_PERIODIC;
+    auto at = [&](int i, int j) { return (size_t)j * nx + i; };
+    auto onW = [&](int i) { return !perx && i == 0; };
+    auto onE = [&](int i) { return !perx && i == nx - 1; };
+    auto onS = [&](int j) { return !pery && j == 0; };
+    auto onN = [&](int j) { return !pery && j == ny - 1; };
+    auto neighbour = [&](int i, int j, int dx, int dy, int &a, int &b) {
+        a = i + dx;
+        b = j + dy;
+        if (a < 0 || a >= nx) {
+            if (!perx) return false;
+            a = (a + nx) % nx;
+        }
+        if (b < 0 || b >= ny) {
+            if (!pery) return false;
+            b = (b + ny) % ny;
+        }
+        return true;
+    };
+    std::vector<uint8_t> kind(g.nx * (size_t)g.ny), dir(kind.size(), 0);
+    for (int j = 0; j < ny; j++)
+        for (int i = 0; i < nx; i++) {
+            const bool solid = mask && mask[at(i, j)];
+            const bool border = onW(i) || onE(i) || onS(j) || onN(j);
+            kind[at(i, j)] = (solid || border) ? KIND_WALL : KIND_FLUID;
+        }
+    auto dir_of = [](int dx, int dy) {
+        for (int q = 1; q < 9; q++)
+            if (cx(q) == dx && cy(q) == dy) return q;
+        return 0;
+    };
+    for (int j = 0; j < ny; j++)
+        for (int i = 0; i < nx; i++) {
+            const size_t k = at(i, j);
+            if (kind[k] != KIND_WALL) continue;
+            const bool solid = mask && mask[k];
+            int d = 0, a, b;
+            if (!solid) {
+                const int dx = onW(i) ? 1 : (onE(i) ? -1 : 0);
+                const int dy = onS(j) ? 1 : (onN(j) ? -1 : 0);
+                if (neighbour(i, j, dx, dy, a, b) && kind[at(a, b)] == KIND_FLUID) d = dir_of(dx, dy);
+            }
+            for (int q = 1; q < 9 && d == 0; q++)
+                if (neighbour(i, j, cx(q), cy(q), a, b) && kind[at(a, b)] == KIND_FLUID) d = q;
+            dir[k] = (uint8_t)d;
+        }
+    std::vector<uint8_t> code((size_t)ny * pitch, CODE_OUTSIDE);
+    for (int j = 0; j < ny; j++)
+        for (int i = 0; i < nx; i++) {
+            const size_t k = at(i, j);
+            int kd = kind[k];
+            if (kd == KIND_WALL && dir[k] == 0) kd = KIND_SOLID;
+            int th;
+            if (kd == KIND_SOLID) th = TH_INERT;
+            else if (mask && mask[k]) th = TH_OBSTACLE;
+            else {
+                const int vert = onW(i) ? LBMFVM_SIDE_W : (onE(i) ? LBMFVM_SIDE_E : -1);
+                const int hor = onS(j) ? LBMFVM_SIDE_S : (onN(j) ? LBMFVM_SIDE_N : -1);
+                const bool dv = vert >= 0 && g.bc[vert] == LBMFVM_BC_DIRICHLET;
+                const bool dh = hor >= 0 && g.bc[hor] == LBMFVM_BC_DIRICHLET;
+                th = (dv || dh) ? TH_DIRICHLET : TH_FV;
+            }
+            code[(size_t)j * pitch + i] = make_code(kd, kd == KIND_WALL ? dir[k] : 0, th);
+        }
+    return code;
+}
+
+}  // namespace
+
+struct lbmfvm {
+    lbmfvm_grid_t grid;
+    int prec;
+    int tile_y;
+    Layout L;
+    double nu, alpha, gbeta, tau, t_ref, force[2];
+    unsigned char *base;
+    bool owns;
+    cudaStream_t user;
+    cudaStream_t s;
+    cudaEvent_t ev_in, ev_out;
+    int parity;       // buffer holding the current post-collision state
+    int64_t steps;    // steps since set_state
+    cudaGraphExec_t graph;
+    char err[512];
+};
+
+namespace {
+
+int fail(lbmfvm_t *h, int code, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(h->err, sizeof(h->err), fmt, ap);
+    va_end(ap);
+    snprintf(g_err, sizeof(g_err), "%s", h->err);
+    return code;
+}
+
+#define CU(h, call)                                                                         \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess)                                                              \
+            return fail((h), LBMFVM_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+template <class S>
+StepArgs<S> args_for(const lbmfvm_t *h, int cur) {
+    using C = typename Compute<S>::type;
+    StepArgs<S> a{};
+    a.fin = reinterpret_cast<const S *>(h->base + h->L.f[cur]);
+    a.fout = reinterpret_cast<S *>(h->base + h->L.f[cur ^ 1]);
+    a.Tin = reinterpret_cast<const C *>(h->base + h->L.T[cur]);
+    a.Tout = reinterpret_cast<C *>(h->base + h->L.T[cur ^ 1]);
+    a.code = h->base + h->L.code;
+    a.nx = h->grid.nx;
+    a.ny = h->grid.ny;
+    a.pitch = h->L.pitch;
+    a.plane = h->L.plane;
+    a.perx = h->grid.bc[LBMFVM_SIDE_W] == LBMFVM_BC_PERIODIC;
+    a.pery = h->grid.bc[LBMFVM_SIDE_S] == LBMFVM_BC_PERIODIC;
+    a.omega = C(1.0 / h->tau);
+    a.alpha = C(h->alpha);
+    a.gbeta = C(h->gbeta);
+    a.t_ref = C(h->t_ref);
+    a.fx = C(h->force[0]);
+    a.fy = C(h->force[1]);
+    for (int s = 0; s < 4; s++) {
+        const bool moving = h->grid.bc[s] == LBMFVM_BC_MOVING;
+        const bool vertical = s < 2;
+        a.wall_u[s] = C(moving && !vertical ? h->grid.u_lid : 0.0);
+        a.wall_v[s] = C(moving && vertical ? h->grid.u_lid : 0.0);
+    }
+    return a;
+}
+
+template <class S, int TY>
+void launch_step_ty(const lbmfvm_t *h, int cur, cudaStream_t s) {
+    const StepArgs<S> a = args_for<S>(h, cur);
+    dim3 block(32, TY), grid((h->grid.nx + 31) / 32, (h->grid.ny + TY - 1) / TY);
+    step_kernel<S, TY><<<grid, block, 0, s>>>(a);
+}
+
+template <class S>
+void launch_step(const lbmfvm_t *h, int cur, cudaStream_t s) {
+    switch (h->tile_y) {
+        case 4: launch_step_ty<S, 4>(h, cur, s); break;
+        case 16: launch_step_ty<S, 16>(h, cur, s); break;
+        default: launch_step_ty<S, 8>(h, cur, s); break;
+    }
+}
+
+void launch_one(const lbmfvm_t *h, int cur, cudaStream_t s) {
+    switch (h->prec) {
+        case LBMFVM_F64: launch_step<double>(h, cur, s); break;
+        case LBMFVM_F32: launch_step<float>(h, cur, s); break;
+        case LBMFVM_F16: launch_step<__half>(h, cur, s); break;
+        case LBMFVM_BF16: launch_step<__nv_bfloat16>(h, cur, s); break;
+    }
+}
+
+int join_in(lbmfvm_t *h) {
+    CU(h, cudaEventRecord(h->ev_in, h->user));
+    CU(h, cudaStreamWaitEvent(h->s, h->ev_in, 0));
+    return LBMFVM_OK;
+}
+
+int join_out(lbmfvm_t *h) {
+    CU(h, cudaEventRecord(h->ev_out, h->s));
+    CU(h, cudaStreamWaitEvent(h->user, h->ev_out, 0));
+    return LBMFVM_OK;
+}
+
+int build_graph(lbmfvm_t *h) {
+    cudaGraph_t g = nullptr;
+    CU(h, cudaStreamBeginCapture(h->s, cudaStreamCaptureModeThreadLocal));
+    for (int i = 0; i < kGraphSteps; i++) launch_one(h, i & 1, h->s);
+    cudaError_t e = cudaStreamEndCapture(h->s, &g);
+    if (e != cudaSuccess) return fail(h, LBMFVM_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&h->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        h->graph = nullptr;
+        return fail(h, LBMFVM_ERR_CUDA, "graph instantiation failed: %s", cudaGetErrorString(e));
+    }
+    return LBMFVM_OK;
+}
+
+template <class S>
+void launch_init(lbmfvm_t *h, const float *u0, const float *v0, const float *T0) {
+    using C = typename Compute<S>::type;
+    StepArgs<S> a = args_for<S>(h, 0);
+    S *fstar = reinterpret_cast<S *>(h->base + h->L.f[0]);
+    S *f0 = reinterpret_cast<S *>(h->base + h->L.f[1]);
+    C *Ta = reinterpret_cast<C *>(h->base + h->L.T[0]);
+    C *Tb = reinterpret_cast<C *>(h->base + h->L.T[1]);
+    double *tw = reinterpret_cast<double *>(h->base + h->L.red) + 2 * kResidualBlocks + 2;
+    dim3 block(32, 8), grid((h->grid.nx + 31) / 32, (h->grid.ny + 7) / 8);
+    init_kernel<S><<<grid, block, 0, h->s>>>(a, f0, fstar, u0, v0, T0, h->grid.t_init, tw, h->grid.bc[0],
+                                             h->grid.bc[1], h->grid.bc[2], h->grid.bc[3], Ta, Tb);
+}
+
+// Arguments of the kernels that read the state of the current step: the
+// buffer with the previous post-collision populations (or the unrelaxed
+// initial populations at step 0) and the current temperature.
+template <class S>
+StepArgs<S> read_args(const lbmfvm_t *h, int &direct) {
+    direct = h->steps == 0;
+    StepArgs<S> a = args_for<S>(h, h->parity);
+    const int prev = h->parity ^ 1;  // f*^{n-1}, or f^0 at step 0
+    a.fin = reinterpret_cast<const S *>(h->base + h->L.f[prev]);
+    return a;
+}
+
+template <class S>
+void launch_residual(lbmfvm_t *h, int update_only) {
+    int direct;
+    StepArgs<S> a = read_args<S>(h, direct);
+    double *su = reinterpret_cast<double *>(h->base + h->L.snap);
+    double *sv = su + (size_t)h->grid.nx * h->grid.ny;
+    double *red = reinterpret_cast<double *>(h->base + h->L.red);
+    residual_kernel<S><<<kResidualBlocks, 256, 0, h->s>>>(a, direct, su, sv, red, update_only);
+    if (!update_only) residual_finish_kernel<<<1, 32, 0, h->s>>>(red, kResidualBlocks, red + 2 * kResidualBlocks);
+}
+
+template <class S, class O>
+void launch_fields(lbmfvm_t *h, int which, O *o0, O *o1) {
+    int direct;
+    StepArgs<S> a = read_args<S>(h, direct);
+    dim3 block(32, 8), grid((h->grid.nx + 31) / 32, (h->grid.ny + 7) / 8);
+    fields_kernel<S, O><<<grid, block, 0, h->s>>>(a, direct, which, o0, o1);
+}
+
+template <class S>
+void launch_nusselt(lbmfvm_t *h) {
+    StepArgs<S> a = args_for<S>(h, h->parity);
+    double *red = reinterpret_cast<double *>(h->base + h->L.red);
+    const double dT = h->grid.t_wall[LBMFVM_SIDE_W] - h->grid.t_wall[LBMFVM_SIDE_E];
+    nusselt_kernel<S><<<1, 256, 0, h->s>>>(a, (double)(h->grid.ny - 1), dT, red + 2 * kResidualBlocks + 8,
+                                           red + 2 * kResidualBlocks + 6);
+}
+
+#define DISPATCH(h, FN, ...)                                          \
+    do {                                                              \
+        switch ((h)->prec) {                                          \
+            case LBMFVM_F64: FN<double>(__VA_ARGS__); break;          \
+            case LBMFVM_F32: FN<float>(__VA_ARGS__); break;           \
+            case LBMFVM_F16: FN<__half>(__VA_ARGS__); break;          \
+            case LBMFVM_BF16: FN<__nv_bfloat16>(__VA_ARGS__); break;  \
+        }                                                             \
+    } while (0)
+
+int set_state_impl(lbmfvm_t *h, const float *u, const float *v, const float *T) {
+    const size_t n = (size_t)h->grid.nx * h->grid.ny;
+    float *stage = reinterpret_cast<float *>(h->base + h->L.stage);
+    const float *du = nullptr, *dv = nullptr, *dT = nullptr;
+    if (int r = join_in(h)) return r;
+    if (u) { CU(h, cudaMemcpyAsync(stage, u, n * sizeof(float), cudaMemcpyDefault, h->s)); du = stage; }
+    if (v) { CU(h, cudaMemcpyAsync(stage + n, v, n * sizeof(float), cudaMemcpyDefault, h->s)); dv = stage + n; }
+    if (T) { CU(h, cudaMemcpyAsync(stage + 2 * n, T, n * sizeof(float), cudaMemcpyDefault, h->s)); dT = stage + 2 * n; }
+    double tw[4];
+    for (int s = 0; s < 4; s++) tw[s] = h->grid.t_wall[s];
+    double *dtw = reinterpret_cast<double *>(h->base + h->L.red) + 2 * kResidualBlocks + 2;
+    CU(h, cudaMemcpyAsync(dtw, tw, sizeof(tw), cudaMemcpyHostToDevice, h->s));
+    DISPATCH(h, launch_init, h, du, dv, dT);
+    CU(h, cudaGetLastError());
+    h->parity = 0;
+    h->steps = 0;
+    DISPATCH(h, launch_residual, h, 1);  // snapshot := u^0
+    CU(h, cudaGetLastError());
+    // The host copy of the wall temperatures and the staged inputs must stay
+    // valid until the kernels above have read them.
+    CU(h, cudaStreamSynchronize(h->s));
+    return join_out(h);
+}
+
+int create_impl(const lbmfvm_grid_t *grid, const uint8_t *mask, double nu, double alpha, double gbeta,
+                const double *force, const lbmfvm_opts_t *opts_in, lbmfvm_t **out) {
+    if (!out) return fail_thread(LBMFVM_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (int r = check_grid(grid)) return r;
+    lbmfvm_opts_t opts;
+    lbmfvm_opts_default(&opts);
+    if (opts_in) opts = *opts_in;
+    if (opts.store < LBMFVM_F64 || opts.store > LBMFVM_BF16)
+        return fail_thread(LBMFVM_ERR_ARG, "store = %d is not a LBMFVM_F* value", opts.store);
+    if (opts.tile_y != 0 && opts.tile_y != 4 && opts.tile_y != 8 && opts.tile_y != 16)
+        return fail_thread(LBMFVM_ERR_ARG, "tile_y must be 0, 4, 8 or 16 (got %d)", opts.tile_y);
+    if (!(nu > 0.0) || !std::isfinite(nu) || !(alpha > 0.0) || !std::isfinite(alpha) || !std::isfinite(gbeta))
+        return fail_thread(LBMFVM_ERR_ARG, "nu and alpha must be positive and finite, gbeta finite");
+    const double tau = 3.0 * nu + 0.5;
+    if (tau < 0.51) return fail_thread(LBMFVM_ERR_UNSTABLE, "tau = %.6g < 0.51", tau);
+    if (alpha > 0.25)
+        return fail_thread(LBMFVM_ERR_UNSTABLE, "alpha = %.6g exceeds the explicit diffusion limit 0.25", alpha);
+    const Layout L = make_layout(*grid, opts.store);
+    if (opts.workspace && opts.workspace_bytes < L.total)
+        return fail_thread(LBMFVM_ERR_NOMEM, "workspace of %zu bytes is smaller than the %zu needed",
+                           opts.workspace_bytes, L.total);
+    if (opts.workspace && ((uintptr_t)opts.workspace % kAlign))
+        return fail_thread(LBMFVM_ERR_ARG, "workspace must be %zu-byte aligned", kAlign);
+
+    lbmfvm_t *h = new (std::nothrow) lbmfvm_t();
+    if (!h) return fail_thread(LBMFVM_ERR_NOMEM, "host allocation failed");
+    h->grid = *grid;
+    h->prec = opts.store;
+    h->tile_y = opts.tile_y ? opts.tile_y : 8;
+    h->L = L;
+    h->nu = nu;
+    h->alpha = alpha;
+    h->gbeta = gbeta;
+    h->tau = tau;
+    h->t_ref = std::isnan(opts.t_ref) ? grid->t_wall[LBMFVM_SIDE_E] : opts.t_ref;
+    h->force[0] = force ? force[0] : 0.0;
+    h->force[1] = force ? force[1] : 0.0;
+    h->user = (cudaStream_t)opts.cuda_stream;
+    auto bail = [&](int code) {
+        lbmfvm_destroy(h);
+        return code;
+    };
+    cudaError_t e = cudaStreamCreateWithFlags(&h->s, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        h->s = nullptr;
+        fail(h, LBMFVM_ERR_CUDA, "cudaStreamCreateWithFlags failed: %s", cudaGetErrorString(e));
+        return bail(LBMFVM_ERR_CUDA);
+    }
+    if (cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming) != cudaSuccess) {
+        fail(h, LBMFVM_ERR_CUDA, "cudaEventCreate failed");
+        return bail(LBMFVM_ERR_CUDA);
+    }
+    if (opts.workspace) {
+        h->base = static_cast<unsigned char *>(opts.workspace);
+        h->owns = false;
+    } else {
+        e = cudaMalloc(&h->base, L.total);
+        if (e != cudaSuccess) {
+            h->base = nullptr;
+            fail(h, LBMFVM_ERR_NOMEM, "cudaMalloc of %zu bytes failed: %s", L.total, cudaGetErrorString(e));
+            return bail(LBMFVM_ERR_NOMEM);
+        }
+        h->owns = true;
+    }
+    std::vector<uint8_t> code = classify(*grid, mask, L.pitch);
+    if (join_in(h)) return bail(LBMFVM_ERR_CUDA);
+    if (cudaMemsetAsync(h->base, 0, L.total, h->s) != cudaSuccess ||
+        cudaMemcpyAsync(h->base + L.code, code.data(), code.size(), cudaMemcpyHostToDevice, h->s) != cudaSuccess) {
+        fail(h, LBMFVM_ERR_CUDA, "device initialisation failed");
+        return bail(LBMFVM_ERR_CUDA);
+    }
+    if (int r = set_state_impl(h, nullptr, nullptr, nullptr)) return bail(r);
+    *out = h;
+    return LBMFVM_OK;
+}
+
+template <class O>
+int fields_impl(lbmfvm_t *h, O *rho, O *u, O *v, O *T) {
+    if (!h) return fail_thread(LBMFVM_ERR_ARG, "handle is NULL");
+    const size_t n = (size_t)h->grid.nx * h->grid.ny;
+    O *st = reinterpret_cast<O *>(h->base + h->L.stage);
+    if (int r = join_in(h)) return r;
+    O *outs[2][2] = {{rho, u}, {v, T}};
+    for (int which = 0; which < 2; which++) {
+        if (!outs[which][0] && !outs[which][1]) continue;
+        DISPATCH(h, launch_fields, h, which, st, st + n);
+        CU(h, cudaGetLastError());
+        for (int i = 0; i < 2; i++)
+            if (outs[which][i])
+                CU(h, cudaMemcpyAsync(outs[which][i], st + i * n, n * sizeof(O), cudaMemcpyDefault, h->s));
+    }
+    CU(h, cudaStreamSynchronize(h->s));
+    return join_out(h);
+}
+
+}  // namespace
+
+extern "C" {
+
+void lbmfvm_opts_default(lbmfvm_opts_t *o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->store = LBMFVM_F32;
+    o->tile_y = 0;
+    o->t_ref = NAN;
+}
+
+int lbmfvm_workspace_bytes(const lbmfvm_grid_t *grid, const lbmfvm_opts_t *opts, size_t *bytes) {
+    if (!bytes) return fail_thread(LBMFVM_ERR_ARG, "bytes is NULL");
+    if (int r = check_grid(grid)) return r;
+    const int prec = opts ? opts->store : LBMFVM_F32;
+    if (prec < LBMFVM_F64 || prec > LBMFVM_BF16) return fail_thread(LBMFVM_ERR_ARG, "invalid store precision");
+    *bytes = make_layout(*grid, prec).total;
+    return LBMFVM_OK;
+}
+
+int lbmfvm_create(const lbmfvm_grid_t *grid, const uint8_t *mask, double Ra, double Pr, double Ma,
+                  const lbmfvm_opts_t *opts, lbmfvm_t **out) {
+    if (out) *out = nullptr;
+    if (int r = check_grid(grid)) return r;
+    if (!(Ra > 0.0) || !(Pr > 0.0) || !(Ma > 0.0) || !std::isfinite(Ra) || !std::isfinite(Pr) || !std::isfinite(Ma))
+        return fail_thread(LBMFVM_ERR_ARG, "Ra, Pr and Ma must be positive and finite");
+    const double dT = grid->t_wall[LBMFVM_SIDE_W] - grid->t_wall[LBMFVM_SIDE_E];
+    if (dT == 0.0 || !std::isfinite(dT))
+        return fail_thread(LBMFVM_ERR_ARG, "t_wall[W] - t_wall[E] must be non-zero");
+    if (Ma > 0.3) return fail_thread(LBMFVM_ERR_UNSTABLE, "Ma = %.6g exceeds 0.3", Ma);
+    const double H = grid->ny - 1;
+    const double U0 = Ma / std::sqrt(3.0);
+    const double nu = U0 * H * std::sqrt(Pr / Ra);
+    const double alpha = U0 * H / std::sqrt(Ra * Pr);
+    const double gbeta = U0 * U0 / (H * dT);
+    if (U0 * U0 > 2.0 * alpha)
+        return fail_thread(LBMFVM_ERR_UNSTABLE,
+                           "U0^2 = %.6g exceeds 2 alpha = %.6g (explicit central advection limit)", U0 * U0, 2 * alpha);
+    return create_impl(grid, mask, nu, alpha, gbeta, nullptr, opts, out);
+}
+
+int lbmfvm_create_lattice(const lbmfvm_grid_t *grid, const uint8_t *mask, double nu, double alpha, double gbeta,
+                          const double *force, const lbmfvm_opts_t *opts, lbmfvm_t **out) {
+    return create_impl(grid, mask, nu, alpha, gbeta, force, opts, out);
+}
+
+int lbmfvm_set_state(lbmfvm_t *h, const float *u, const float *v, const float *T) {
+    if (!h) return fail_thread(LBMFVM_ERR_ARG, "handle is NULL");
+    return set_state_impl(h, u, v, T);
+}
+
+int lbmfvm_step(lbmfvm_t *h, int64_t n) {
+    if (!h) return fail_thread(LBMFVM_ERR_ARG, "handle is NULL");
+    if (n < 0) return fail(h, LBMFVM_ERR_ARG, "n = %lld is negative", (long long)n);
+    if (n == 0) return LBMFVM_OK;
+    if (int r = join_in(h)) return r;
+    if (n >= kGraphSteps && !h->graph)
+        if (int r = build_graph(h)) return r;
+    while (n > 0) {
+        if (h->parity == 0 && n >= kGraphSteps && h->graph) {
+            CU(h, cudaGraphLaunch(h->graph, h->s));
+            n -= kGraphSteps;
+            h->steps += kGraphSteps;
+        } else {
+            launch_one(h, h->parity, h->s);
+            CU(h, cudaGetLastError());
+            h->parity ^= 1;
+            n--;
+            h->steps++;
+        }
+    }
+    return join_out(h);
+}
+
+int lbmfvm_step_count(const lbmfvm_t *h, int64_t *steps) {
+    if (!h || !steps) return fail_thread(LBMFVM_ERR_ARG, "handle or steps is NULL");
+    *steps = h->steps;
+    return LBMFVM_OK;
+}
+
+int lbmfvm_fields(lbmfvm_t *h, double *rho, double *u, double *v, double *T) {
+    return fields_impl<double>(h, rho, u, v, T);
+}
+
+int lbmfvm_fields_f32(lbmfvm_t *h, float *rho, float *u, float *v, float *T) {
+    return fields_impl<float>(h, rho, u, v, T);
+}
+
+int lbmfvm_nusselt(lbmfvm_t *h, double *mean_hot, double *local_hot, double *mean_cold) {
+    if (!h) return fail_thread(LBMFVM_ERR_ARG, "handle is NULL");
+    if (h->grid.t_wall[LBMFVM_SIDE_W] == h->grid.t_wall[LBMFVM_SIDE_E])
+        return fail(h, LBMFVM_ERR_ARG, "Nusselt number needs t_wall[W] != t_wall[E]");
+    if (int r = join_in(h)) return r;
+    DISPATCH(h, launch_nusselt, h);
+    CU(h, cudaGetLastError());
+    double *red = reinterpret_cast<double *>(h->base + h->L.red);
+    double means[2];
+    CU(h, cudaMemcpyAsync(means, red + 2 * kResidualBlocks + 6, sizeof(means), cudaMemcpyDeviceToHost, h->s));
+    if (local_hot)
+        CU(h, cudaMemcpyAsync(local_hot, red + 2 * kResidualBlocks + 8, h->grid.ny * sizeof(double),
+                              cudaMemcpyDefault, h->s));
+    CU(h, cudaStreamSynchronize(h->s));
+    if (mean_hot) *mean_hot = means[0];
+    if (mean_cold) *mean_cold = means[1];
+    if (!std::isfinite(means[0]) || !std::isfinite(means[1]))
+        return fail(h, LBMFVM_ERR_DIVERGED, "non-finite Nusselt number");
+    return join_out(h);
+}
+
+int lbmfvm_residual(lbmfvm_t *h, double *r) {
+    if (!h || !r) return fail_thread(LBMFVM_ERR_ARG, "handle or r is NULL");
+    if (int e = join_in(h)) return e;
+    DISPATCH(h, launch_residual, h, 0);
+    CU(h, cudaGetLastError());
+    double sums[2];
+    double *red = reinterpret_cast<double *>(h->base + h->L.red);
+    CU(h, cudaMemcpyAsync(sums, red + 2 * kResidualBlocks, sizeof(sums), cudaMemcpyDeviceToHost, h->s));
+    CU(h, cudaStreamSynchronize(h->s));
+    if (!std::isfinite(sums[0]) || !std::isfinite(sums[1])) {
+        *r = NAN;
+        return fail(h, LBMFVM_ERR_DIVERGED, "non-finite velocity in the residual");
+    }
+    *r = sums[1] > 0.0 ? std::sqrt(sums[0]) / std::sqrt(sums[1]) : (sums[0] == 0.0 ? 0.0 : INFINITY);
+    return join_out(h);
+}
+
+int lbmfvm_run_to_steady(lbmfvm_t *h, double tol, int64_t check_every, int64_t max_steps, int64_t *steps_done,
+                         double *r_final) {
+    if (!h) return fail_thread(LBMFVM_ERR_ARG, "handle is NULL");
+    if (check_every <= 0 || max_steps < 0) return fail(h, LBMFVM_ERR_ARG, "check_every must be > 0, max_steps >= 0");
+    int64_t done = 0;
+    double r = INFINITY;
+    while (done < max_steps) {
+        const int64_t n = check_every < max_steps - done ? check_every : max_steps - done;
+        if (int e = lbmfvm_step(h, n)) return e;
+        done += n;
+        if (int e = lbmfvm_residual(h, &r)) {
+            if (steps_done) *steps_done = done;
+            if (r_final) *r_final = r;
+            return e;
+        }
+        if (r < tol) break;
+    }
+    if (steps_done) *steps_done = done;
+    if (r_final) *r_final = r;
+    return LBMFVM_OK;
+}
+
+int lbmfvm_params(const lbmfvm_t *h, double *nu, double *alpha, double *gbeta, double *tau) {
+    if (!h) return fail_thread(LBMFVM_ERR_ARG, "handle is NULL");
+    if (nu) *nu = h->nu;
+    if (alpha) *alpha = h->alpha;
+    if (gbeta) *gbeta = h->gbeta;
+    if (tau) *tau = h->tau;
+    return LBMFVM_OK;
+}
+
+void lbmfvm_destroy(lbmfvm_t *h) {
+    if (!h) return;
+    if (h->s) cudaStreamSynchronize(h->s);
+    if (h->graph) cudaGraphExecDestroy(h->graph);
+    if (h->owns && h->base) cudaFree(h->base);
+    if (h->ev_in) cudaEventDestroy(h->ev_in);
+    if (h->ev_out) cudaEventDestroy(h->ev_out);
+    if (h->s) cudaStreamDestroy(h->s);
+    delete h;
+}
+
+const char *lbmfvm_last_error(const lbmfvm_t *h) { return h ? h->err : g_err; }
+
+}  // extern "C"

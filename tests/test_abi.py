@@ -1,0 +1,96 @@
+"""The C-ABI library loads without a GPU, exports every entry point its header
+declares, and rejects invalid arguments before touching the device."""
+
+import os
+import re
+
+import pytest
+
+import paper_1908_08386_gb300 as L
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(__file__)), "include", "lbmfvm.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(lbmfvm_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_header_declares_what_the_binding_lists():
+    assert declared_functions() == sorted(L.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol():
+    lib = L.lib()
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_opts_defaults():
+    o = L.lbmfvm_opts_default()
+    assert o.store == L.LBMFVM_F32 and o.tile_y == 0 and o.workspace is None
+    assert o.t_ref != o.t_ref  # NaN selects T_l
+
+
+def test_workspace_size_grows_with_precision():
+    g = L.make_grid(100, 70)
+    sizes = {}
+    for name, p in L.PRECISIONS.items():
+        o = L.lbmfvm_opts_default()
+        o.store = p
+        sizes[name] = L.lbmfvm_workspace_bytes(g, o)
+    assert sizes["f16"] == sizes["bf16"] < sizes["f32"] < sizes["f64"]
+    # two f planes of 9 populations, pitch rounded to 64 nodes
+    assert sizes["f32"] >= 2 * 9 * 70 * 128 * 4
+
+
+@pytest.mark.parametrize("nx,ny", [(2, 10), (10, 2), (0, 0)])
+def test_rejects_tiny_grids(nx, ny):
+    with pytest.raises(L.LbmfvmError) as e:
+        L.lbmfvm_workspace_bytes(L.make_grid(nx, ny))
+    assert e.value.code == L.LBMFVM_ERR_ARG
+
+
+def test_rejects_half_periodic():
+    g = L.make_grid(10, 10, bc=(L.LBMFVM_BC_PERIODIC, L.LBMFVM_BC_DIRICHLET, 1, 1))
+    with pytest.raises(L.LbmfvmError) as e:
+        L.lbmfvm_create_lattice(g, None, 0.1, 0.1, 0.0)
+    assert e.value.code == L.LBMFVM_ERR_ARG
+
+
+def test_stability_limits_are_checked_before_any_device_work():
+    g = L.make_grid(64, 64)
+    with pytest.raises(L.LbmfvmError) as e:  # tau = 3 nu + 1/2 < 0.51
+        L.lbmfvm_create_lattice(g, None, 0.001, 0.1, 0.0)
+    assert e.value.code == L.LBMFVM_ERR_UNSTABLE
+    with pytest.raises(L.LbmfvmError) as e:  # explicit diffusion limit
+        L.lbmfvm_create_lattice(g, None, 0.1, 0.3, 0.0)
+    assert e.value.code == L.LBMFVM_ERR_UNSTABLE
+    with pytest.raises(L.LbmfvmError) as e:  # Ma > 0.3
+        L.lbmfvm_create(g, None, 1e4, 0.71, 0.5)
+    assert e.value.code == L.LBMFVM_ERR_UNSTABLE
+    with pytest.raises(L.LbmfvmError) as e:  # alpha = U0 H / sqrt(Ra Pr) > 0.25
+        L.lbmfvm_create(L.make_grid(512, 512), None, 1e3, 0.71, 0.1 * 3**0.5)
+    assert e.value.code == L.LBMFVM_ERR_UNSTABLE
+    with pytest.raises(L.LbmfvmError) as e:  # no temperature difference
+        L.lbmfvm_create(L.make_grid(64, 64, t_wall=(1, 1, 0, 0)), None, 1e4, 0.71, 0.1)
+    assert e.value.code == L.LBMFVM_ERR_ARG
+    assert "t_wall" in L.lbmfvm_last_error()
+
+
+def test_workspace_too_small_is_rejected():
+    g = L.make_grid(64, 64)
+    o = L.lbmfvm_opts_default()
+    o.workspace = 256
+    o.workspace_bytes = 1024
+    with pytest.raises(L.LbmfvmError) as e:
+        L.lbmfvm_create_lattice(g, None, 0.1, 0.1, 0.0, None, o)
+    assert e.value.code == L.LBMFVM_ERR_NOMEM
+
+
+def test_null_handle_calls_fail_cleanly():
+    lib = L.lib()
+    assert lib.lbmfvm_step(None, 1) == L.LBMFVM_ERR_ARG
+    assert lib.lbmfvm_set_state(None, None, None, None) == L.LBMFVM_ERR_ARG
+    lib.lbmfvm_destroy(None)
