@@ -216,9 +216,10 @@ def run_ours(args):
         cpu = {"value": v, "unit": "MLUPS", "cores": cores, "kind": "oracle",
                "sample": f"{steps} coupled steps of the {args.size}x{args.size} Ra 1e6 cavity in {dt:.1f} s"}
 
-    case = WL.config_large(args.size)
+    case = WL.config_large(args.size, args.ra)
     n_nodes = case.nx * case.ny
-    cav = L.Cavity(case.nx, case.ny, Ra=case.Ra, Pr=case.Pr, Ma=case.Ma, store=args.store, device=dev)
+    cav = L.Cavity(case.nx, case.ny, Ra=case.Ra, Pr=case.Pr, Ma=case.Ma, store=args.store, device=dev,
+                   kernel=args.kernel, tma_config=args.tma_config)
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
 
@@ -307,14 +308,14 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": args.store, "data": "synthetic",
-        "config": {"workload": f"cavity {case.nx}x{case.ny}, Ra 1e6, Pr 0.71, U0 0.1, {args.store} storage",
+        "config": {"workload": f"cavity {case.nx}x{case.ny}, Ra {case.Ra:.0e}, Pr 0.71, U0 0.1, {args.store} storage",
                    "coupled_steps_per_step": args.chunk, "total_coupled_steps": args.chunk * args.steps,
                    "parallelism": f"replicas x{world} (one cavity per GPU)",
                    "l2": "512 MB buffer written between timed steps; the state is re-read every coupled step",
                    "wall_s": wall_s, "final_residual": last[0] if last else None,
                    "final_nusselt": last[1] if last else None},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": traffic, "kernel": "step_kernel", "peak_kind": peak_kind,
+                     "traffic": traffic, "kernel": "step_tma_kernel" if args.store != "f64" else "step_kernel", "peak_kind": peak_kind,
                      "algorithmic_bytes_per_launch": bytes_per_launch, "avg_launch_us": launch_s * 1e6},
         "cpu_baseline": cpu,
         "e2e": e2e,
@@ -331,8 +332,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--size", type=int, default=1024)
+    ap.add_argument("--ra", type=float, default=1e6, help="Rayleigh number (1e7 keeps 4096^2 stable)")
     ap.add_argument("--chunk", type=int, default=1000, help="coupled steps per benchmark step")
     ap.add_argument("--store", choices=["f32", "f16", "bf16", "f64"], default="f32")
+    ap.add_argument("--kernel", choices=["auto", "tma", "generic"], default="auto")
+    ap.add_argument("--tma-config", type=int, default=0)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-e2e", action="store_true")

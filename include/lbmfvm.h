@@ -66,6 +66,13 @@ extern "C" {
 #define LBMFVM_BC_PERIODIC 2
 #define LBMFVM_BC_MOVING 3
 
+/* Step kernel selection.  AUTO takes the persistent TMA kernel whenever it
+ * applies (walls on every side, F32/F16/BF16 storage) and the generic kernel
+ * otherwise; both compute the same arithmetic. */
+#define LBMFVM_KERNEL_AUTO 0
+#define LBMFVM_KERNEL_GENERIC 1
+#define LBMFVM_KERNEL_TMA 2
+
 /* Storage precision of the distributions.  F32/F16/BF16 store f - w_i and
  * compute in FP32 with FP32 temperature; F64 stores and computes in FP64. */
 #define LBMFVM_F64 0
@@ -87,8 +94,13 @@ typedef struct {
 /* Options; fill with lbmfvm_opts_default() first. */
 typedef struct {
     int32_t store;          /* LBMFVM_F64/F32/F16/BF16; default LBMFVM_F32 */
-    int32_t tile_y;         /* rows per thread block of the step kernel: 0 = default,
-                               else one of 4, 8, 16 */
+    int32_t tile_y;         /* rows per thread block of the generic step kernel:
+                               0 = default, else one of 4, 8, 16 */
+    int32_t kernel;         /* LBMFVM_KERNEL_*; default AUTO */
+    int32_t tma_config;     /* tile shape of the TMA kernel (width x height, stages,
+                               threads): 0 = 64x16, 3 stages (4 at 16 bit), 512;
+                               1 = the same with 1024 threads; 2 = 64x8, 4, 512;
+                               3 = 128x8, 2 stages (4 at 16 bit), 512 */
     double t_ref;           /* reference temperature of the buoyancy term; NaN (the
                                default) selects T_l = t_wall[E] as in Eq. 81 */
     void *cuda_stream;      /* cudaStream_t the handle orders its work on; NULL =
@@ -137,6 +149,17 @@ int lbmfvm_set_state(lbmfvm_t *h, const float *u, const float *v, const float *T
 
 /* Enqueue n coupled time steps (n >= 0) on the handle's stream and return. */
 int lbmfvm_step(lbmfvm_t *h, int64_t n);
+
+/* Fault-injection hook for testing the bounded device-side waits: the next
+ * single step launched by lbmfvm_step makes block 0 of the TMA kernel wait for
+ * a staged load that is never issued.  That wait gives up after about one
+ * second, the kernel records the failure in the handle's device status word
+ * and the block returns; the next synchronising call (fields, Nusselt,
+ * residual) returns LBMFVM_ERR_TIMEOUT and clears the word.  The state of that
+ * step is then incomplete: call lbmfvm_set_state before trusting it again.
+ * Nothing faults and the CUDA context stays usable.  Returns LBMFVM_ERR_ARG if
+ * the handle runs the generic kernel, which has no such waits. */
+int lbmfvm_inject_stall(lbmfvm_t *h);
 
 /* Number of time steps taken since the last set_state. */
 int lbmfvm_step_count(const lbmfvm_t *h, int64_t *steps);

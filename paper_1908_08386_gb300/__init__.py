@@ -30,6 +30,9 @@ LBMFVM_ERR_NOMEM = -6
 LBMFVM_SIDE_W, LBMFVM_SIDE_E, LBMFVM_SIDE_S, LBMFVM_SIDE_N = 0, 1, 2, 3
 # Boundary kinds
 LBMFVM_BC_DIRICHLET, LBMFVM_BC_ADIABATIC, LBMFVM_BC_PERIODIC, LBMFVM_BC_MOVING = 0, 1, 2, 3
+# Step kernels
+LBMFVM_KERNEL_AUTO, LBMFVM_KERNEL_GENERIC, LBMFVM_KERNEL_TMA = 0, 1, 2
+KERNELS = {"auto": LBMFVM_KERNEL_AUTO, "generic": LBMFVM_KERNEL_GENERIC, "tma": LBMFVM_KERNEL_TMA}
 # Storage precisions
 LBMFVM_F64, LBMFVM_F32, LBMFVM_F16, LBMFVM_BF16 = 0, 1, 2, 3
 PRECISIONS = {"f64": LBMFVM_F64, "f32": LBMFVM_F32, "f16": LBMFVM_F16, "bf16": LBMFVM_BF16}
@@ -37,7 +40,7 @@ PRECISIONS = {"f64": LBMFVM_F64, "f32": LBMFVM_F32, "f16": LBMFVM_F16, "bf16": L
 # Every entry point the header declares (checked by the test-suite).
 EXPORTS = (
     "lbmfvm_opts_default", "lbmfvm_workspace_bytes", "lbmfvm_create", "lbmfvm_create_lattice",
-    "lbmfvm_set_state", "lbmfvm_step", "lbmfvm_step_count", "lbmfvm_fields", "lbmfvm_fields_f32",
+    "lbmfvm_set_state", "lbmfvm_step", "lbmfvm_inject_stall", "lbmfvm_step_count", "lbmfvm_fields", "lbmfvm_fields_f32",
     "lbmfvm_nusselt", "lbmfvm_residual", "lbmfvm_run_to_steady", "lbmfvm_params", "lbmfvm_destroy",
     "lbmfvm_last_error",
 )
@@ -49,7 +52,8 @@ class lbmfvm_grid_t(ctypes.Structure):
 
 
 class lbmfvm_opts_t(ctypes.Structure):
-    _fields_ = [("store", ctypes.c_int32), ("tile_y", ctypes.c_int32), ("t_ref", ctypes.c_double),
+    _fields_ = [("store", ctypes.c_int32), ("tile_y", ctypes.c_int32), ("kernel", ctypes.c_int32),
+                ("tma_config", ctypes.c_int32), ("t_ref", ctypes.c_double),
                 ("cuda_stream", ctypes.c_void_p), ("workspace", ctypes.c_void_p),
                 ("workspace_bytes", ctypes.c_size_t)]
 
@@ -84,6 +88,7 @@ def lib() -> ctypes.CDLL:
                 "lbmfvm_create_lattice": (ctypes.c_int, [G, vp, d, d, d, vp, O, pp]),
                 "lbmfvm_set_state": (ctypes.c_int, [vp, vp, vp, vp]),
                 "lbmfvm_step": (ctypes.c_int, [vp, i64]),
+                "lbmfvm_inject_stall": (ctypes.c_int, [vp]),
                 "lbmfvm_step_count": (ctypes.c_int, [vp, i64p]),
                 "lbmfvm_fields": (ctypes.c_int, [vp, vp, vp, vp, vp]),
                 "lbmfvm_fields_f32": (ctypes.c_int, [vp, vp, vp, vp, vp]),
@@ -165,6 +170,10 @@ def lbmfvm_step(h, n):
     _check(lib().lbmfvm_step(h, int(n)), h)
 
 
+def lbmfvm_inject_stall(h):
+    _check(lib().lbmfvm_inject_stall(h), h)
+
+
 def lbmfvm_step_count(h) -> int:
     out = ctypes.c_int64()
     _check(lib().lbmfvm_step_count(h, ctypes.byref(out)), h)
@@ -225,7 +234,8 @@ class Cavity:
     def __init__(self, nx, ny, *, Ra=None, Pr=None, Ma=None, nu=None, alpha=None, gbeta=0.0, force=None,
                  mask=None, store="f32", bc=(LBMFVM_BC_DIRICHLET, LBMFVM_BC_DIRICHLET, LBMFVM_BC_ADIABATIC,
                                              LBMFVM_BC_ADIABATIC),
-                 t_wall=(1.0, 0.0, 0.0, 0.0), u_lid=0.0, t_init=0.5, t_ref=None, tile_y=0, device=None):
+                 t_wall=(1.0, 0.0, 0.0, 0.0), u_lid=0.0, t_init=0.5, t_ref=None, tile_y=0, kernel="auto",
+                 tma_config=0, device=None):
         import torch
 
         self.nx, self.ny = int(nx), int(ny)
@@ -233,6 +243,8 @@ class Cavity:
         self.opts = lbmfvm_opts_default()
         self.opts.store = PRECISIONS[store] if isinstance(store, str) else int(store)
         self.opts.tile_y = int(tile_y)
+        self.opts.kernel = KERNELS[kernel] if isinstance(kernel, str) else int(kernel)
+        self.opts.tma_config = int(tma_config)
         self.opts.t_ref = math.nan if t_ref is None else float(t_ref)
         dev = torch.device("cuda" if device is None else device)
         self.device = dev

@@ -2,8 +2,8 @@
 //
 // State between launches: the post-collision populations f* of the last step
 // (structure of arrays [9][ny][pitch], stored as f* - w_i) and the temperature
-// T (plane [ny][pitch]).  One launch of step_kernel takes the state from step
-// n to n+1:
+// T (plane [ny][pitch]).  One launch of a step kernel takes the state from
+// step n to n+1:
 //   1. pull f^{n+1}_i(x) = f*_i(x - e_i)                         (Eq. 5)
 //   2. wall nodes: f_b = f_eq(rho_f, u_wall) + f(x_f) - f_eq(x_f) (Eqs. 94, 96)
 //   3. rho^{n+1}, u^{n+1}                                         (Eqs. 16-17)
@@ -12,10 +12,19 @@
 //   5. f* = f - (f - f_eq)/tau + F with the Boussinesq force of T^{n+1}
 //                                                        (Eqs. 5, 8, 18, 81)
 // Step 4 needs u^{n+1} of the four neighbours, so each block first computes
-// rho, u for its tile plus a one-node ring (stored in shared memory), then
+// rho, u for its tile plus a one-node ring (kept in shared memory), then
 // updates T and collides its own nodes.
+//
+// Two kernels share this arithmetic:
+//   step_tma_kernel  persistent, one block per SM, each tile's populations,
+//                    temperature and node codes staged in shared memory by
+//                    TMA through a multi-stage mbarrier pipeline (walled
+//                    domains, FP32/FP16/BF16 storage);
+//   step_kernel      one block per tile, gathers straight from global memory
+//                    (periodic sides, FP64 storage).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -24,7 +33,8 @@
 namespace lbmfvm_dev {
 
 // Node codes: bits 0-1 kind, bits 2-5 partner direction of wall nodes,
-// bits 6-7 thermal role.
+// bits 6-7 thermal role.  Memory holds code ^ CODE_OUTSIDE, so that the zero
+// fill of a TMA box beyond the grid decodes as "outside".
 enum : uint8_t { KIND_FLUID = 0, KIND_WALL = 1, KIND_SOLID = 2 };
 enum : uint8_t { TH_FV = 0, TH_DIRICHLET = 1, TH_OBSTACLE = 2, TH_INERT = 3 };
 constexpr uint8_t CODE_OUTSIDE = KIND_SOLID | (TH_INERT << 6);
@@ -32,6 +42,8 @@ constexpr uint8_t CODE_OUTSIDE = KIND_SOLID | (TH_INERT << 6);
 __host__ __device__ __forceinline__ uint8_t make_code(int kind, int dir, int therm) {
     return (uint8_t)(kind | (dir << 2) | (therm << 6));
 }
+__host__ __device__ __forceinline__ uint8_t stored_code(uint8_t code) { return code ^ CODE_OUTSIDE; }
+__host__ __device__ __forceinline__ uint8_t decode(uint8_t stored) { return stored ^ CODE_OUTSIDE; }
 
 // D2Q9 velocities (Eq. 4): 0 rest, 1 E, 2 N, 3 W, 4 S, 5 NE, 6 NW, 7 SW, 8 SE.
 __host__ __device__ constexpr int cx(int q) {
@@ -69,6 +81,9 @@ __device__ __forceinline__ void st(double *p, double v) { *p = v; }
 __device__ __forceinline__ void st(__half *p, float v) { *p = __float2half_rn(v); }
 __device__ __forceinline__ void st(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
 
+__device__ __forceinline__ float recip(float r) { return __frcp_rn(r); }
+__device__ __forceinline__ double recip(double r) { return 1.0 / r; }
+
 template <class S>
 struct StepArgs {
     using C = typename Compute<S>::type;
@@ -76,20 +91,107 @@ struct StepArgs {
     S *fout;
     const C *Tin;
     C *Tout;
-    const uint8_t *code;
+    const uint8_t *code;  // stored codes (code ^ CODE_OUTSIDE)
     int nx, ny, pitch, perx, pery;
     long long plane;  // ny * pitch
     C omega, alpha, gbeta, t_ref, fx, fy;
     C wall_u[4], wall_v[4];  // velocity of box walls per side W, E, S, N
+    int *err;                // device status word (bounded waits that ran out)
+    int stall;               // test hook: block 0 skips its first staged load
 };
 
-// Second-order part of Eq. 8 divided by rho w_q:
-// 3 e.u + 4.5 (e.u)^2 - 1.5 u.u  (c_s^2 = 1/3).
+// ---------------------------------------------------------------------------
+// Arithmetic shared by both step kernels and the export kernels.
+// ---------------------------------------------------------------------------
+
+// Second-order part of Eq. 8 divided by rho w_q: 3 e.u + 4.5 (e.u)^2 - 1.5 u.u.
 template <class C>
 __device__ __forceinline__ C eq_poly(int q, C ux, C uy, C usq) {
     C eu = C(cx(q)) * ux + C(cy(q)) * uy;
     return C(3) * eu + C(4.5) * eu * eu - C(1.5) * usq;
 }
+
+// Eqs. 16-17 on shifted populations g = f - w: rho = 1 + sum g, rho u = sum e g.
+template <class C>
+__device__ __forceinline__ void moments(const C g[9], C &drho, C &ux, C &uy) {
+    const C s = (((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + (g[6] + g[7]))) + g[8];
+    const C jx = ((g[1] + g[5]) + g[8]) - ((g[3] + g[6]) + g[7]);
+    const C jy = ((g[2] + g[5]) + g[6]) - ((g[4] + g[7]) + g[8]);
+    const C inv = recip(C(1) + s);
+    drho = s;
+    ux = jx * inv;
+    uy = jy * inv;
+}
+
+// Non-equilibrium extrapolation (Eq. 94): g holds the partner's populations
+// and moments on entry; on exit the wall node's, with rho_b = rho_f (Eq. 96)
+// and the wall velocity (uw, vw).
+template <class C>
+__device__ __forceinline__ void nee(C g[9], C &drho, C &ux, C &uy, C uw, C vw) {
+    const C rho = C(1) + drho;
+    const C usw = uw * uw + vw * vw, usf = ux * ux + uy * uy;
+#pragma unroll
+    for (int q = 0; q < 9; q++)
+        g[q] += rho * wq<C>(q) * (eq_poly<C>(q, uw, vw, usw) - eq_poly<C>(q, ux, uy, usf));
+    moments<C>(g, drho, ux, uy);
+}
+
+// BGK relaxation with the buoyancy force (Eqs. 5, 8, 18) on shifted storage.
+// The force's pressure is the reference pressure rho0 c_s^2 with rho0 = 1, so
+// its momentum source is rho G (the force density of Eq. 75).  With
+// P_q = 3 e.u + 4.5 (e.u)^2 - 1.5 u.u and h_q = G.(e_q - u):
+//   f_eq - w = w (drho + rho P),  F = 3 h f_eq = 3 h w rho (1 + P),
+//   g* = (1 - omega) g + w [omega drho + 3 rho h + P (omega rho + 3 rho h)].
+template <class C, class Store>
+__device__ __forceinline__ void collide(const C g[9], C drho, C ux, C uy, C omega, C Gx, C Gy, Store store) {
+    const C rho = C(1) + drho;
+    const C usq = ux * ux + uy * uy;
+    const C Gu = Gx * ux + Gy * uy;
+    const C a = omega * drho, b = omega * rho, c = C(3) * rho, om1 = C(1) - omega;
+    const C P0 = C(-1.5) * usq;
+#pragma unroll
+    for (int q = 0; q < 9; q++) {
+        const C eu = C(cx(q)) * ux + C(cy(q)) * uy;
+        const C P = C(3) * eu + C(4.5) * eu * eu + P0;
+        const C ch = c * (C(cx(q)) * Gx + C(cy(q)) * Gy - Gu);
+        store(q, om1 * g[q] + wq<C>(q) * ((a + ch) + P * (b + ch)));
+    }
+}
+
+// Explicit finite-volume update (forward Euler, dt = 1) of a node-centred
+// control volume of extents ex x ey: central face temperatures, face
+// velocities the mean of the two node velocities, closed faces carry nothing.
+template <class C>
+__device__ __forceinline__ C fv_update(C TP, C uP, C vP, C ex, C ey, C alpha, bool oE, C TE, C uE, bool oN, C TN,
+                                       C vN, bool oW, C TW, C uW, bool oS, C TS, C vS) {
+    const C q = C(0.25);
+    const C fe = oE ? alpha * (TE - TP) - q * (uP + uE) * (TP + TE) : C(0);
+    const C fw = oW ? alpha * (TW - TP) + q * (uP + uW) * (TP + TW) : C(0);
+    const C fn = oN ? alpha * (TN - TP) - q * (vP + vN) * (TP + TN) : C(0);
+    const C fs = oS ? alpha * (TS - TP) + q * (vP + vS) * (TP + TS) : C(0);
+    // 1/(ex ey) is a power of two (ex, ey in {1/2, 1}): the product is exact.
+    const C inv_v = (ex < C(1) ? C(2) : C(1)) * (ey < C(1) ? C(2) : C(1));
+    return TP + (ey * (fe + fw) + ex * (fn + fs)) * inv_v;
+}
+
+__device__ __forceinline__ bool fv_open(uint8_t code) { return (code >> 6) <= TH_DIRICHLET; }
+
+// Velocity of a box wall node from its side (vertical sides own the corners).
+template <class S>
+__device__ __forceinline__ void wall_velocity(const StepArgs<S> &a, int x, int y, uint8_t code,
+                                              typename Compute<S>::type &uw, typename Compute<S>::type &vw) {
+    using C = typename Compute<S>::type;
+    uw = vw = C(0);
+    if ((code >> 6) != TH_OBSTACLE) {
+        const int side = (!a.perx && x == 0) ? 0 : (!a.perx && x == a.nx - 1) ? 1 : (!a.pery && y == 0) ? 2 : 3;
+        uw = a.wall_u[side];
+        vw = a.wall_v[side];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Generic path: gathers straight from global memory.
+// ---------------------------------------------------------------------------
 
 // Shifted populations g_q = f_q - w_q pulled into node (x, y) (Eq. 5).
 template <class S, class C>
@@ -109,24 +211,6 @@ __device__ __forceinline__ void gather(const S *__restrict__ fin, long long plan
     g[6] = ld(rm + 6 * plane + xp);
     g[7] = ld(rp + 7 * plane + xp);
     g[8] = ld(rp + 8 * plane + xm);
-}
-
-// Eqs. 16-17 on shifted populations: rho = 1 + sum g, rho u = sum e g.
-template <class C>
-__device__ __forceinline__ void moments(const C g[9], C &drho, C &ux, C &uy) {
-    C s = C(0), jx = C(0), jy = C(0);
-#pragma unroll
-    for (int q = 0; q < 9; q++) {
-        s += g[q];
-        if (cx(q) > 0) jx += g[q];
-        if (cx(q) < 0) jx -= g[q];
-        if (cy(q) > 0) jy += g[q];
-        if (cy(q) < 0) jy -= g[q];
-    }
-    drho = s;
-    const C rho = C(1) + s;
-    ux = jx / rho;
-    uy = jy / rho;
 }
 
 // Pre-collision populations and moments of node (x, y) at the new step:
@@ -154,37 +238,9 @@ __device__ __forceinline__ void node_state(const StepArgs<S> &a, const S *__rest
     gather<S, C>(fin, a.plane, a.pitch, a.nx, a.ny, sx, sy, g);
     moments<C>(g, drho, ux, uy);
     if (kind == KIND_WALL) {
-        C uw = C(0), vw = C(0);
-        if ((code >> 6) != TH_OBSTACLE) {
-            const int side = (!a.perx && x == 0) ? 0 : (!a.perx && x == a.nx - 1) ? 1 : (!a.pery && y == 0) ? 2 : 3;
-            uw = a.wall_u[side];
-            vw = a.wall_v[side];
-        }
-        const C rho = C(1) + drho;
-        const C usw = uw * uw + vw * vw, usf = ux * ux + uy * uy;
-#pragma unroll
-        for (int q = 0; q < 9; q++)
-            g[q] += rho * wq<C>(q) * (eq_poly<C>(q, uw, vw, usw) - eq_poly<C>(q, ux, uy, usf));
-        moments<C>(g, drho, ux, uy);
-    }
-}
-
-// BGK relaxation with the buoyancy force (Eqs. 5, 8, 18), shifted storage.
-// The force's pressure is the reference pressure rho0 c_s^2 with rho0 = 1, so
-// its momentum source is rho G (the force density of Eq. 75).
-template <class S, class C>
-__device__ __forceinline__ void collide_store(S *__restrict__ out, long long plane, const C g[9],
-                                              C drho, C ux, C uy, C omega, C Gx, C Gy) {
-    const C rho = C(1) + drho;
-    const C usq = ux * ux + uy * uy;
-#pragma unroll
-    for (int q = 0; q < 9; q++) {
-        const C P = eq_poly<C>(q, ux, uy, usq);
-        const C w = wq<C>(q);
-        const C feq = w * rho * (C(1) + P);
-        const C dfeq = w * (drho + rho * P);
-        const C F = C(3) * (Gx * (C(cx(q)) - ux) + Gy * (C(cy(q)) - uy)) * feq;
-        st(out + q * plane, g[q] + omega * (dfeq - g[q]) + F);
+        C uw, vw;
+        wall_velocity<S>(a, x, y, code, uw, vw);
+        nee<C>(g, drho, ux, uy, uw, vw);
     }
 }
 
@@ -209,7 +265,7 @@ __device__ __forceinline__ bool map_pos(const StepArgs<S> &a, int &x, int &y) {
     return true;
 }
 
-// Fused coupled step.  Block = 32 x TY threads, one per node of its tile.
+// Fused coupled step, generic path.  Block = 32 x TY threads, one per node.
 template <class S, int TY>
 __global__ void __launch_bounds__(32 * TY) step_kernel(const StepArgs<S> a) {
     using C = typename Compute<S>::type;
@@ -220,7 +276,7 @@ __global__ void __launch_bounds__(32 * TY) step_kernel(const StepArgs<S> a) {
     const S *__restrict__ fin = a.fin;
 
     C g[9], drho = C(-1), ux = C(0), uy = C(0);
-    bool own = x < a.nx && y < a.ny;
+    const bool own = x < a.nx && y < a.ny;
     {
         int mx = x, my = y;
         const bool in = map_pos(a, mx, my);
@@ -228,7 +284,7 @@ __global__ void __launch_bounds__(32 * TY) step_kernel(const StepArgs<S> a) {
         C T = C(0);
         if (in) {
             const long long k = (long long)my * a.pitch + mx;
-            c = a.code[k];
+            c = decode(a.code[k]);
             T = a.Tin[k];
             node_state<S, C>(a, fin, mx, my, c, g, drho, ux, uy);
         }
@@ -250,7 +306,7 @@ __global__ void __launch_bounds__(32 * TY) step_kernel(const StepArgs<S> a) {
         C T = C(0), hg[9], hd, hu = C(0), hv = C(0);
         if (in) {
             const long long k = (long long)my * a.pitch + mx;
-            c = a.code[k];
+            c = decode(a.code[k]);
             T = a.Tin[k];
             node_state<S, C>(a, fin, mx, my, c, hg, hd, hu, hv);
         }
@@ -267,46 +323,14 @@ __global__ void __launch_bounds__(32 * TY) step_kernel(const StepArgs<S> a) {
     const C TP = sm.T[ty + 1][tx + 1];
     C Tn = TP;
     if (th == TH_FV) {
-        // Control volume [x-1/2, x+1/2] x [y-1/2, y+1/2] clipped to the box.
         const C ex = a.perx ? C(1) : C(0.5) * C(x > 0) + C(0.5) * C(x < a.nx - 1);
         const C ey = a.pery ? C(1) : C(0.5) * C(y > 0) + C(0.5) * C(y < a.ny - 1);
-        const C uP = sm.u[ty + 1][tx + 1], vP = sm.v[ty + 1][tx + 1];
-        C acc = C(0);
-        // faces E, N, W, S; a face is open when the neighbour takes part in
-        // the balance (FV or Dirichlet node).
-        {
-            const int nx_ = tx + 2, ny_ = ty + 1;
-            if ((sm.c[ny_][nx_] >> 6) <= TH_DIRICHLET) {
-                const C Tn_ = sm.T[ny_][nx_];
-                const C Fl = ey * (C(0.5) * (uP + sm.u[ny_][nx_]));
-                acc += -Fl * (C(0.5) * (TP + Tn_)) + a.alpha * ey * (Tn_ - TP);
-            }
-        }
-        {
-            const int nx_ = tx + 1, ny_ = ty + 2;
-            if ((sm.c[ny_][nx_] >> 6) <= TH_DIRICHLET) {
-                const C Tn_ = sm.T[ny_][nx_];
-                const C Fl = ex * (C(0.5) * (vP + sm.v[ny_][nx_]));
-                acc += -Fl * (C(0.5) * (TP + Tn_)) + a.alpha * ex * (Tn_ - TP);
-            }
-        }
-        {
-            const int nx_ = tx, ny_ = ty + 1;
-            if ((sm.c[ny_][nx_] >> 6) <= TH_DIRICHLET) {
-                const C Tn_ = sm.T[ny_][nx_];
-                const C Fl = ey * (C(-0.5) * (uP + sm.u[ny_][nx_]));
-                acc += -Fl * (C(0.5) * (TP + Tn_)) + a.alpha * ey * (Tn_ - TP);
-            }
-        }
-        {
-            const int nx_ = tx + 1, ny_ = ty;
-            if ((sm.c[ny_][nx_] >> 6) <= TH_DIRICHLET) {
-                const C Tn_ = sm.T[ny_][nx_];
-                const C Fl = ex * (C(-0.5) * (vP + sm.v[ny_][nx_]));
-                acc += -Fl * (C(0.5) * (TP + Tn_)) + a.alpha * ex * (Tn_ - TP);
-            }
-        }
-        Tn = TP + acc / (ex * ey);
+        const int i = tx + 1, j = ty + 1;
+        Tn = fv_update<C>(TP, sm.u[j][i], sm.v[j][i], ex, ey, a.alpha,
+                          fv_open(sm.c[j][i + 1]), sm.T[j][i + 1], sm.u[j][i + 1],
+                          fv_open(sm.c[j + 1][i]), sm.T[j + 1][i], sm.v[j + 1][i],
+                          fv_open(sm.c[j][i - 1]), sm.T[j][i - 1], sm.u[j][i - 1],
+                          fv_open(sm.c[j - 1][i]), sm.T[j - 1][i], sm.v[j - 1][i]);
     } else if (th == TH_OBSTACLE) {
         const int d = partner_dir(c);
         Tn = sm.T[ty + 1 + cy_rt(d)][tx + 1 + cx_rt(d)];
@@ -314,7 +338,268 @@ __global__ void __launch_bounds__(32 * TY) step_kernel(const StepArgs<S> a) {
     const long long k = (long long)y * a.pitch + x;
     a.Tout[k] = Tn;
     const C Gy = a.fy + a.gbeta * (Tn - a.t_ref);
-    collide_store<S, C>(a.fout + k, a.plane, g, drho, ux, uy, a.omega, a.fx, Gy);
+    S *out = a.fout + k;
+    const long long plane = a.plane;
+    collide<C>(g, drho, ux, uy, a.omega, a.fx, Gy, [&](int q, C v) { st(out + q * plane, v); });
+}
+
+// ---------------------------------------------------------------------------
+// TMA path.
+// ---------------------------------------------------------------------------
+namespace tma {
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+// Orders this thread's earlier generic-proxy shared-memory accesses (made
+// visible to it by a block barrier) before later async-proxy (TMA) writes.
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n"
+        " .reg .pred p;\n"
+        " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n"
+        "}\n"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t globaltimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for phase `parity` of the barrier; false once `limit_ns` has passed.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, uint64_t limit_ns) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = globaltimer();
+    for (uint32_t it = 0;; it++) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 63u) == 63u && globaltimer() - t0 > limit_ns) return false;
+    }
+}
+
+__device__ __forceinline__ void load_3d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y, int z) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
+            smem_addr(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_addr(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            smem_addr(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_addr(bar))
+        : "memory");
+}
+
+}  // namespace tma
+
+// Tile geometry of the TMA path.  A tile is TW x TH output nodes at (x0, y0);
+// the staged box reaches 3 nodes beyond it in y and XOFF (>= 4, one 16-byte
+// TMA granule) in x, enough for the pull stencil of the one-node ring and of
+// any wall partner on that ring.
+template <class S, int TW_, int TH_, int STAGES_, int THREADS_>
+struct TmaTile {
+    static constexpr int TW = TW_, TH = TH_, STAGES = STAGES_, THREADS = THREADS_;
+    static constexpr int XOFF = 16 / (int)sizeof(S) < 4 ? 4 : 16 / (int)sizeof(S);
+    static constexpr int FW = TW + 2 * XOFF, FH = TH + 6;  // population box
+    static constexpr int TWD = TW + 8, THT = TH + 2;       // temperature box (x0-4, y0-1)
+    static constexpr int CWD = TW + 32, CHT = TH + 2;      // code box (x0-16, y0-1)
+    static constexpr int RW = TW + 2, RH = TH + 2;         // tile + ring
+    static constexpr uint32_t F_BYTES = 9u * FH * FW * sizeof(S);
+    static constexpr uint32_t T_BYTES = (uint32_t)THT * TWD * 4u;
+    static constexpr uint32_t C_BYTES = (uint32_t)CHT * CWD;
+    static constexpr uint32_t align128(uint32_t v) { return (v + 127u) & ~127u; }
+    static constexpr uint32_t F_OFF = 0, T_OFF = align128(F_BYTES), C_OFF = T_OFF + align128(T_BYTES);
+    static constexpr uint32_t STAGE_BYTES = C_OFF + align128(C_BYTES);
+    static constexpr uint32_t TX_BYTES = F_BYTES + T_BYTES + C_BYTES;
+    static constexpr uint32_t RING_OFF = STAGES * STAGE_BYTES;
+    static constexpr uint32_t RING_BYTES = align128(3u * RH * RW * 4u);
+    static constexpr uint32_t BAR_OFF = RING_OFF + RING_BYTES;
+    static constexpr uint32_t SMEM_BYTES = BAR_OFF + 8u * STAGES + 16u;
+    static_assert(SMEM_BYTES <= 232448u, "tile configuration exceeds 227 KB of shared memory");
+    static_assert((FW * sizeof(S)) % 16 == 0 && (TWD * 4) % 16 == 0 && CWD % 16 == 0,
+                  "TMA boxes need 16-byte inner extents");
+    static_assert(TW % 16 == 0, "tile origins must stay 16-byte aligned for every box");
+};
+
+constexpr uint64_t kWaitLimitNs = 1000000000ull;  // 1 s per wait
+constexpr int kErrTimeout = 1;
+
+// Persistent fused step for walled domains (no periodic sides).
+template <class S, class G>
+__global__ void __launch_bounds__(G::THREADS, 1)
+    step_tma_kernel(const StepArgs<S> a, const __grid_constant__ CUtensorMap map_f,
+                    const __grid_constant__ CUtensorMap map_T, const __grid_constant__ CUtensorMap map_c) {
+    using C = float;
+    constexpr int TW = G::TW, TH = G::TH, FW = G::FW, FH = G::FH, RW = G::RW, RH = G::RH;
+    constexpr int XOFF = G::XOFF;
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + G::BAR_OFF);
+    int *status = reinterpret_cast<int *>(smem + G::BAR_OFF + 8 * G::STAGES);
+    C *ring = reinterpret_cast<C *>(smem + G::RING_OFF);
+    C *RU = ring, *RV = ring + RH * RW, *RD = ring + 2 * RH * RW;
+
+    const int tid = threadIdx.x;
+    const int ntx = (a.nx + TW - 1) / TW, nty = (a.ny + TH - 1) / TH;
+    const int ntiles = ntx * nty;
+    const int my_count = (int)blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    auto tile_xy = [&](int k, int &x0, int &y0) {
+        const int t = (int)blockIdx.x + k * (int)gridDim.x;
+        const int ty = t / ntx;
+        x0 = (t - ty * ntx) * TW;
+        y0 = ty * TH;
+    };
+    auto issue = [&](int k) {
+        const int s = k % G::STAGES;
+        int x0, y0;
+        tile_xy(k, x0, y0);
+        unsigned char *stg = smem + s * G::STAGE_BYTES;
+        tma::mbar_arrive_expect_tx(&bars[s], G::TX_BYTES);
+        tma::load_3d(stg + G::F_OFF, &map_f, &bars[s], x0 - XOFF, y0 - 3, 0);
+        tma::load_2d(stg + G::T_OFF, &map_T, &bars[s], x0 - 4, y0 - 1);
+        tma::load_2d(stg + G::C_OFF, &map_c, &bars[s], x0 - 16, y0 - 1);
+    };
+
+    if (tid == 0) {
+        for (int s = 0; s < G::STAGES; s++) tma::mbar_init(&bars[s], 1);
+        tma::fence_mbar_init();
+    }
+    __syncthreads();
+    if (tid == 0)
+        for (int k = 0; k < G::STAGES && k < my_count; k++)
+            if (!(a.stall && blockIdx.x == 0 && k == 0)) issue(k);
+
+    const C alpha = a.alpha, omega = a.omega, gbeta = a.gbeta, t_ref = a.t_ref, fx = a.fx, fy = a.fy;
+    const long long plane = a.plane;
+
+    for (int k = 0; k < my_count; k++) {
+        const int s = k % G::STAGES;
+        if (k > 0) __syncthreads();  // every thread is done with tile k-1
+        if (tid == 0) {
+            if (k > 0 && k - 1 + G::STAGES < my_count) {
+                tma::fence_proxy_async();
+                issue(k - 1 + G::STAGES);
+            }
+            const bool ok = tma::mbar_wait_bounded(&bars[s], (uint32_t)(k / G::STAGES) & 1u, kWaitLimitNs);
+            *status = ok ? 1 : 0;
+            if (!ok) {
+                atomicOr(a.err, kErrTimeout);
+                // let the copies already in flight land before the block exits
+                for (int j = k + 1; j < my_count && j < k + G::STAGES; j++)
+                    tma::mbar_wait_bounded(&bars[j % G::STAGES], (uint32_t)(j / G::STAGES) & 1u, kWaitLimitNs / 2);
+            }
+        }
+        __syncthreads();
+        if (*status == 0) return;
+
+        int x0, y0;
+        tile_xy(k, x0, y0);
+        const unsigned char *stg = smem + s * G::STAGE_BYTES;
+        const S *F = reinterpret_cast<const S *>(stg + G::F_OFF);
+        const float *TT = reinterpret_cast<const float *>(stg + G::T_OFF);
+        const uint8_t *CC = reinterpret_cast<const uint8_t *>(stg + G::C_OFF);
+        // staged-box index of node (lx, ly) relative to the tile origin
+        auto fidx = [&](int lx, int ly) { return (ly + 3) * FW + (lx + XOFF); };
+        auto tidx = [&](int lx, int ly) { return (ly + 1) * G::TWD + (lx + 4); };
+        auto cidx = [&](int lx, int ly) { return (ly + 1) * G::CWD + (lx + 16); };
+        auto pull = [&](int lx, int ly, C g[9]) {
+            const int o = fidx(lx, ly);
+#pragma unroll
+            for (int q = 0; q < 9; q++) g[q] = ld(F + q * (FH * FW) + o - cy(q) * FW - cx(q));
+        };
+        auto state = [&](int lx, int ly, uint8_t c, C g[9], C &drho, C &ux, C &uy) {
+            const int kind = c & 3;
+            if (kind == KIND_SOLID) {
+#pragma unroll
+                for (int q = 0; q < 9; q++) g[q] = C(0);
+                drho = C(-1);
+                ux = uy = C(0);
+                return;
+            }
+            if (kind == KIND_FLUID) {
+                pull(lx, ly, g);
+                moments<C>(g, drho, ux, uy);
+                return;
+            }
+            const int d = partner_dir(c);
+            pull(lx + cx_rt(d), ly + cy_rt(d), g);
+            moments<C>(g, drho, ux, uy);
+            C uw, vw;
+            wall_velocity<S>(a, x0 + lx, y0 + ly, c, uw, vw);
+            nee<C>(g, drho, ux, uy, uw, vw);
+        };
+
+        // Phase A: moments of the tile and its one-node ring.
+        for (int i = tid; i < RH * RW; i += G::THREADS) {
+            const int ry = i / RW, rx = i - ry * RW;
+            const uint8_t c = decode(CC[cidx(rx - 1, ry - 1)]);
+            C g[9], drho, ux, uy;
+            state(rx - 1, ry - 1, c, g, drho, ux, uy);
+            RU[i] = ux;
+            RV[i] = uy;
+            RD[i] = drho;
+        }
+        __syncthreads();
+
+        // Phase B: energy balance and collision of the tile's own nodes.
+        for (int i = tid; i < TW * TH; i += G::THREADS) {
+            const int ly = i / TW, lx = i - ly * TW;
+            const int x = x0 + lx, y = y0 + ly;
+            if (x >= a.nx || y >= a.ny) continue;
+            const uint8_t c = decode(CC[cidx(lx, ly)]);
+            const int kind = c & 3;
+            if (kind == KIND_SOLID) continue;
+            const int r = (ly + 1) * RW + (lx + 1);
+            C g[9];
+            const C drho = RD[r], ux = RU[r], uy = RV[r];
+            if (kind == KIND_FLUID) {
+                pull(lx, ly, g);
+            } else {
+                C d2, u2, v2;
+                state(lx, ly, c, g, d2, u2, v2);
+            }
+            const int th = c >> 6;
+            const int t = tidx(lx, ly);
+            const C TP = TT[t];
+            C Tn = TP;
+            if (th == TH_FV) {
+                const C ex = C(0.5) * C(x > 0) + C(0.5) * C(x < a.nx - 1);
+                const C ey = C(0.5) * C(y > 0) + C(0.5) * C(y < a.ny - 1);
+                Tn = fv_update<C>(TP, ux, uy, ex, ey, alpha,
+                                  fv_open(decode(CC[cidx(lx + 1, ly)])), TT[t + 1], RU[r + 1],
+                                  fv_open(decode(CC[cidx(lx, ly + 1)])), TT[t + G::TWD], RV[r + RW],
+                                  fv_open(decode(CC[cidx(lx - 1, ly)])), TT[t - 1], RU[r - 1],
+                                  fv_open(decode(CC[cidx(lx, ly - 1)])), TT[t - G::TWD], RV[r - RW]);
+            } else if (th == TH_OBSTACLE) {
+                const int d = partner_dir(c);
+                Tn = TT[tidx(lx + cx_rt(d), ly + cy_rt(d))];
+            }
+            const long long kg = (long long)y * a.pitch + x;
+            a.Tout[kg] = Tn;
+            const C Gy = fy + gbeta * (Tn - t_ref);
+            S *out = a.fout + kg;
+            collide<C>(g, drho, ux, uy, omega, fx, Gy, [&](int q, C v) { st(out + q * plane, v); });
+        }
+    }
 }
 
 // Initial state: f^0 = f_eq(1, u0) (kept unrelaxed in f0_out for the step-0
@@ -330,7 +615,7 @@ __global__ void init_kernel(const StepArgs<S> a, S *f0_out, S *fstar_out, const 
     if (x >= a.nx || y >= a.ny) return;
     const long long k = (long long)y * a.pitch + x;
     const long long kin = (long long)y * a.nx + x;
-    const uint8_t c = a.code[k];
+    const uint8_t c = decode(a.code[k]);
     C T = T0 ? C(T0[kin]) : C(t_init);
     if ((c >> 6) == TH_DIRICHLET) {
         // Vertical sides own the corners.
@@ -360,7 +645,9 @@ __global__ void init_kernel(const StepArgs<S> a, S *f0_out, S *fstar_out, const 
     C drho, ux, uy;
     moments<C>(g, drho, ux, uy);
     const C Gy = a.fy + a.gbeta * (T - a.t_ref);
-    collide_store<S, C>(fstar_out + k, a.plane, g, drho, ux, uy, a.omega, a.fx, Gy);
+    S *out = fstar_out + k;
+    const long long plane = a.plane;
+    collide<C>(g, drho, ux, uy, a.omega, a.fx, Gy, [&](int q, C v2) { st(out + q * plane, v2); });
 }
 
 // Pre-collision moments of the current step: re-pulled from the previous
@@ -398,7 +685,7 @@ __global__ void fields_kernel(const StepArgs<S> a, int direct, int which, O *out
     if (x >= a.nx || y >= a.ny) return;
     const long long k = (long long)y * a.pitch + x;
     const long long ko = (long long)y * a.nx + x;
-    const uint8_t c = a.code[k];
+    const uint8_t c = decode(a.code[k]);
     C drho, ux, uy;
     current_moments<S>(a, direct, x, y, c, drho, ux, uy);
     const bool inert = (c & 3) == KIND_SOLID;
@@ -413,28 +700,28 @@ __global__ void fields_kernel(const StepArgs<S> a, int direct, int which, O *out
 
 // Residual, pass 1: per-block FP64 sums of |u - u_snap|^2 and |u|^2 over
 // fluid nodes, snapshot update; partials[2*b], partials[2*b+1].
-// Fixed assignment of nodes to threads and a fixed reduction tree make the
+// A fixed assignment of rows to blocks and a fixed reduction tree make the
 // result independent of scheduling.
 template <class S>
 __global__ void __launch_bounds__(256) residual_kernel(const StepArgs<S> a, int direct, double *su,
                                                        double *sv, double *partials, int update_only) {
     using C = typename Compute<S>::type;
     __shared__ double red[2][8];
-    const long long n = (long long)a.nx * a.ny;
     double num = 0.0, den = 0.0;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x) {
-        const int y = (int)(i / a.nx), x = (int)(i - (long long)y * a.nx);
-        const long long k = (long long)y * a.pitch + x;
-        const uint8_t c = a.code[k];
-        if ((c & 3) != KIND_FLUID) continue;
-        C drho, ux, uy;
-        current_moments<S>(a, direct, x, y, c, drho, ux, uy);
-        const double du = (double)ux - su[i], dv = (double)uy - sv[i];
-        num += du * du + dv * dv;
-        den += (double)ux * (double)ux + (double)uy * (double)uy;
-        su[i] = (double)ux;
-        sv[i] = (double)uy;
+    for (int y = blockIdx.x; y < a.ny; y += gridDim.x) {
+        for (int x = threadIdx.x; x < a.nx; x += blockDim.x) {
+            const long long k = (long long)y * a.pitch + x;
+            const uint8_t c = decode(a.code[k]);
+            if ((c & 3) != KIND_FLUID) continue;
+            C drho, ux, uy;
+            current_moments<S>(a, direct, x, y, c, drho, ux, uy);
+            const long long i = (long long)y * a.nx + x;
+            const double du = (double)ux - su[i], dv = (double)uy - sv[i];
+            num += du * du + dv * dv;
+            den += (double)ux * (double)ux + (double)uy * (double)uy;
+            su[i] = (double)ux;
+            sv[i] = (double)uy;
+        }
     }
     if (update_only) return;
 #pragma unroll

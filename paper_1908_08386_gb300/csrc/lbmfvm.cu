@@ -12,6 +12,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <type_traits>
 #include <vector>
 
 #include "kernels.cuh"
@@ -50,7 +51,7 @@ size_t store_size(int prec) {
 struct Layout {
     int pitch;
     long long plane;
-    size_t f[2], T[2], code, snap, stage, red, total;
+    size_t f[2], T[2], code, snap, stage, red, err, total;
 };
 
 Layout make_layout(const lbmfvm_grid_t &g, int prec) {
@@ -72,6 +73,7 @@ Layout make_layout(const lbmfvm_grid_t &g, int prec) {
     L.snap = take(2 * (size_t)g.nx * g.ny * sizeof(double));
     L.stage = take(2 * (size_t)g.nx * g.ny * sizeof(double));
     L.red = take((2 * kResidualBlocks + 8 + (size_t)g.ny) * sizeof(double));
+    L.err = take(16);
     L.total = off;
     return L;
 }
@@ -170,6 +172,7 @@ std::vector<uint8_t> classify(const lbmfvm_grid_t &g, const uint8_t *mask, int p
             }
             code[(size_t)j * pitch + i] = make_code(kd, kd == KIND_WALL ? dir[k] : 0, th);
         }
+    for (auto &c : code) c = stored_code(c);
     return code;
 }
 
@@ -189,6 +192,11 @@ struct lbmfvm {
     int parity;       // buffer holding the current post-collision state
     int64_t steps;    // steps since set_state
     cudaGraphExec_t graph;
+    bool use_tma;     // persistent TMA kernel (walled domains, 32/16-bit storage)
+    bool stall_next;  // test hook armed by lbmfvm_inject_stall
+    int tma_config;   // tile shape of the TMA kernel
+    int num_sms;
+    CUtensorMap map_f[2], map_T[2], map_c;
     char err[512];
 };
 
@@ -219,6 +227,7 @@ StepArgs<S> args_for(const lbmfvm_t *h, int cur) {
     a.Tin = reinterpret_cast<const C *>(h->base + h->L.T[cur]);
     a.Tout = reinterpret_cast<C *>(h->base + h->L.T[cur ^ 1]);
     a.code = h->base + h->L.code;
+    a.err = reinterpret_cast<int *>(h->base + h->L.err);
     a.nx = h->grid.nx;
     a.ny = h->grid.ny;
     a.pitch = h->L.pitch;
@@ -247,8 +256,45 @@ void launch_step_ty(const lbmfvm_t *h, int cur, cudaStream_t s) {
     step_kernel<S, TY><<<grid, block, 0, s>>>(a);
 }
 
+// Tile shapes of the TMA kernel (tile width x height, pipeline stages,
+// threads), selected by lbmfvm_opts_t.tma_config.  Stages are as many as the
+// 227 KB of shared memory allow for 32-bit storage; 16-bit storage halves the
+// population box and takes one more stage where it fits.
+template <class S, int CFG> struct TmaConfig;
+template <class S> struct TmaConfig<S, 0> { using G = TmaTile<S, 64, 16, sizeof(S) == 4 ? 3 : 4, 512>; };
+template <class S> struct TmaConfig<S, 1> { using G = TmaTile<S, 64, 16, sizeof(S) == 4 ? 3 : 4, 1024>; };
+template <class S> struct TmaConfig<S, 2> { using G = TmaTile<S, 64, 8, 4, 512>; };
+template <class S> struct TmaConfig<S, 3> { using G = TmaTile<S, 128, 8, sizeof(S) == 4 ? 2 : 4, 512>; };
+constexpr int kTmaConfigs = 4;
+
+template <class S, int CFG>
+void launch_tma_cfg(const lbmfvm_t *h, int cur, cudaStream_t s, bool stall) {
+    using G = typename TmaConfig<S, CFG>::G;
+    StepArgs<S> a = args_for<S>(h, cur);
+    a.stall = stall ? 1 : 0;
+    const int ntiles = ((h->grid.nx + G::TW - 1) / G::TW) * ((h->grid.ny + G::TH - 1) / G::TH);
+    const int blocks = ntiles < h->num_sms ? ntiles : h->num_sms;
+    step_tma_kernel<S, G><<<blocks, G::THREADS, G::SMEM_BYTES, s>>>(a, h->map_f[cur], h->map_T[cur], h->map_c);
+}
+
 template <class S>
-void launch_step(const lbmfvm_t *h, int cur, cudaStream_t s) {
+void launch_step_tma(const lbmfvm_t *h, int cur, cudaStream_t s, bool stall) {
+    switch (h->tma_config) {
+        case 1: launch_tma_cfg<S, 1>(h, cur, s, stall); break;
+        case 2: launch_tma_cfg<S, 2>(h, cur, s, stall); break;
+        case 3: launch_tma_cfg<S, 3>(h, cur, s, stall); break;
+        default: launch_tma_cfg<S, 0>(h, cur, s, stall); break;
+    }
+}
+
+template <class S>
+void launch_step(const lbmfvm_t *h, int cur, cudaStream_t s, bool stall) {
+    if constexpr (!std::is_same<S, double>::value) {
+        if (h->use_tma) {
+            launch_step_tma<S>(h, cur, s, stall);
+            return;
+        }
+    }
     switch (h->tile_y) {
         case 4: launch_step_ty<S, 4>(h, cur, s); break;
         case 16: launch_step_ty<S, 16>(h, cur, s); break;
@@ -256,12 +302,12 @@ void launch_step(const lbmfvm_t *h, int cur, cudaStream_t s) {
     }
 }
 
-void launch_one(const lbmfvm_t *h, int cur, cudaStream_t s) {
+void launch_one(const lbmfvm_t *h, int cur, cudaStream_t s, bool stall = false) {
     switch (h->prec) {
-        case LBMFVM_F64: launch_step<double>(h, cur, s); break;
-        case LBMFVM_F32: launch_step<float>(h, cur, s); break;
-        case LBMFVM_F16: launch_step<__half>(h, cur, s); break;
-        case LBMFVM_BF16: launch_step<__nv_bfloat16>(h, cur, s); break;
+        case LBMFVM_F64: launch_step<double>(h, cur, s, stall); break;
+        case LBMFVM_F32: launch_step<float>(h, cur, s, stall); break;
+        case LBMFVM_F16: launch_step<__half>(h, cur, s, stall); break;
+        case LBMFVM_BF16: launch_step<__nv_bfloat16>(h, cur, s, stall); break;
     }
 }
 
@@ -380,6 +426,101 @@ int set_state_impl(lbmfvm_t *h, const float *u, const float *v, const float *T) 
     return join_out(h);
 }
 
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no
+// link-time dependency on the driver library).
+using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_tiled() {
+    static EncodeTiledFn fn = []() -> EncodeTiledFn {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            return nullptr;
+        return reinterpret_cast<EncodeTiledFn>(p);
+    }();
+    return fn;
+}
+
+template <class S> constexpr CUtensorMapDataType tmap_type() { return CU_TENSOR_MAP_DATA_TYPE_FLOAT32; }
+template <> constexpr CUtensorMapDataType tmap_type<__half>() { return CU_TENSOR_MAP_DATA_TYPE_FLOAT16; }
+template <> constexpr CUtensorMapDataType tmap_type<__nv_bfloat16>() { return CU_TENSOR_MAP_DATA_TYPE_BFLOAT16; }
+
+// Tensor maps of both population buffers, both temperature planes and the
+// node codes; the grid's x extent is nx, so boxes reaching past it (or below
+// zero) are zero-filled.
+template <class S, int CFG>
+int setup_tma_cfg(lbmfvm_t *h) {
+    using G = typename TmaConfig<S, CFG>::G;
+    EncodeTiledFn enc = encode_tiled();
+    if (!enc) return fail(h, LBMFVM_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+    const cuuint64_t nx = (cuuint64_t)h->grid.nx, ny = (cuuint64_t)h->grid.ny, pitch = (cuuint64_t)h->L.pitch;
+    const cuuint32_t one[3] = {1, 1, 1};
+    for (int b = 0; b < 2; b++) {
+        const cuuint64_t dims[3] = {nx, ny, 9};
+        const cuuint64_t strides[2] = {pitch * sizeof(S), (cuuint64_t)h->L.plane * sizeof(S)};
+        const cuuint32_t box[3] = {(cuuint32_t)G::FW, (cuuint32_t)G::FH, 9};
+        CUresult r = enc(&h->map_f[b], tmap_type<S>(), 3, h->base + h->L.f[b], dims, strides, box, one,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return fail(h, LBMFVM_ERR_CUDA, "tensor map of the populations failed (%d)", (int)r);
+        const cuuint64_t dims2[2] = {nx, ny};
+        const cuuint64_t strides2[1] = {pitch * sizeof(float)};
+        const cuuint32_t box2[2] = {(cuuint32_t)G::TWD, (cuuint32_t)G::THT};
+        r = enc(&h->map_T[b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, h->base + h->L.T[b], dims2, strides2, box2, one,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return fail(h, LBMFVM_ERR_CUDA, "tensor map of the temperature failed (%d)", (int)r);
+    }
+    const cuuint64_t dims2[2] = {nx, ny};
+    const cuuint64_t strides2[1] = {pitch};
+    const cuuint32_t box2[2] = {(cuuint32_t)G::CWD, (cuuint32_t)G::CHT};
+    CUresult r = enc(&h->map_c, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, h->base + h->L.code, dims2, strides2, box2, one,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(h, LBMFVM_ERR_CUDA, "tensor map of the node codes failed (%d)", (int)r);
+    CU(h, cudaFuncSetAttribute(step_tma_kernel<S, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM_BYTES));
+    int dev = 0;
+    CU(h, cudaGetDevice(&dev));
+    CU(h, cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev));
+    return LBMFVM_OK;
+}
+
+template <class S>
+int setup_tma(lbmfvm_t *h) {
+    switch (h->tma_config) {
+        case 1: return setup_tma_cfg<S, 1>(h);
+        case 2: return setup_tma_cfg<S, 2>(h);
+        case 3: return setup_tma_cfg<S, 3>(h);
+        default: return setup_tma_cfg<S, 0>(h);
+    }
+}
+
+int setup_kernels(lbmfvm_t *h) {
+    if (!h->use_tma) return LBMFVM_OK;
+    switch (h->prec) {
+        case LBMFVM_F32: return setup_tma<float>(h);
+        case LBMFVM_F16: return setup_tma<__half>(h);
+        case LBMFVM_BF16: return setup_tma<__nv_bfloat16>(h);
+    }
+    return LBMFVM_OK;
+}
+
+// A bounded device-side wait that ran out leaves a non-zero status word.
+int check_device_status(lbmfvm_t *h) {
+    int word = 0;
+    int *dev = reinterpret_cast<int *>(h->base + h->L.err);
+    CU(h, cudaMemcpyAsync(&word, dev, sizeof(int), cudaMemcpyDeviceToHost, h->s));
+    CU(h, cudaStreamSynchronize(h->s));
+    if (word) {
+        CU(h, cudaMemsetAsync(dev, 0, sizeof(int), h->s));
+        return fail(h, LBMFVM_ERR_TIMEOUT, "a device-side wait for staged data ran out (status %d)", word);
+    }
+    return LBMFVM_OK;
+}
+
 int create_impl(const lbmfvm_grid_t *grid, const uint8_t *mask, double nu, double alpha, double gbeta,
                 const double *force, const lbmfvm_opts_t *opts_in, lbmfvm_t **out) {
     if (!out) return fail_thread(LBMFVM_ERR_ARG, "out is NULL");
@@ -392,6 +533,14 @@ int create_impl(const lbmfvm_grid_t *grid, const uint8_t *mask, double nu, doubl
         return fail_thread(LBMFVM_ERR_ARG, "store = %d is not a LBMFVM_F* value", opts.store);
     if (opts.tile_y != 0 && opts.tile_y != 4 && opts.tile_y != 8 && opts.tile_y != 16)
         return fail_thread(LBMFVM_ERR_ARG, "tile_y must be 0, 4, 8 or 16 (got %d)", opts.tile_y);
+    const bool periodic = grid->bc[LBMFVM_SIDE_W] == LBMFVM_BC_PERIODIC || grid->bc[LBMFVM_SIDE_S] == LBMFVM_BC_PERIODIC;
+    const bool tma_ok = !periodic && opts.store != LBMFVM_F64;
+    if (opts.kernel < LBMFVM_KERNEL_AUTO || opts.kernel > LBMFVM_KERNEL_TMA)
+        return fail_thread(LBMFVM_ERR_ARG, "kernel = %d is not a LBMFVM_KERNEL_* value", opts.kernel);
+    if (opts.tma_config < 0 || opts.tma_config >= kTmaConfigs)
+        return fail_thread(LBMFVM_ERR_ARG, "tma_config must be in [0, %d) (got %d)", kTmaConfigs, opts.tma_config);
+    if (opts.kernel == LBMFVM_KERNEL_TMA && !tma_ok)
+        return fail_thread(LBMFVM_ERR_ARG, "the TMA kernel needs walls on every side and 32- or 16-bit storage");
     if (!(nu > 0.0) || !std::isfinite(nu) || !(alpha > 0.0) || !std::isfinite(alpha) || !std::isfinite(gbeta))
         return fail_thread(LBMFVM_ERR_ARG, "nu and alpha must be positive and finite, gbeta finite");
     const double tau = 3.0 * nu + 0.5;
@@ -410,6 +559,8 @@ int create_impl(const lbmfvm_grid_t *grid, const uint8_t *mask, double nu, doubl
     h->grid = *grid;
     h->prec = opts.store;
     h->tile_y = opts.tile_y ? opts.tile_y : 8;
+    h->use_tma = tma_ok && opts.kernel != LBMFVM_KERNEL_GENERIC;
+    h->tma_config = opts.tma_config;
     h->L = L;
     h->nu = nu;
     h->alpha = alpha;
@@ -446,6 +597,7 @@ int create_impl(const lbmfvm_grid_t *grid, const uint8_t *mask, double nu, doubl
         }
         h->owns = true;
     }
+    if (int r = setup_kernels(h)) return bail(r);
     std::vector<uint8_t> code = classify(*grid, mask, L.pitch);
     if (join_in(h)) return bail(LBMFVM_ERR_CUDA);
     if (cudaMemsetAsync(h->base, 0, L.total, h->s) != cudaSuccess ||
@@ -474,6 +626,7 @@ int fields_impl(lbmfvm_t *h, O *rho, O *u, O *v, O *T) {
                 CU(h, cudaMemcpyAsync(outs[which][i], st + i * n, n * sizeof(O), cudaMemcpyDefault, h->s));
     }
     CU(h, cudaStreamSynchronize(h->s));
+    if (int r = check_device_status(h)) return r;
     return join_out(h);
 }
 
@@ -486,6 +639,7 @@ void lbmfvm_opts_default(lbmfvm_opts_t *o) {
     std::memset(o, 0, sizeof(*o));
     o->store = LBMFVM_F32;
     o->tile_y = 0;
+    o->kernel = LBMFVM_KERNEL_AUTO;
     o->t_ref = NAN;
 }
 
@@ -537,12 +691,13 @@ int lbmfvm_step(lbmfvm_t *h, int64_t n) {
     if (n >= kGraphSteps && !h->graph)
         if (int r = build_graph(h)) return r;
     while (n > 0) {
-        if (h->parity == 0 && n >= kGraphSteps && h->graph) {
+        if (h->parity == 0 && n >= kGraphSteps && h->graph && !h->stall_next) {
             CU(h, cudaGraphLaunch(h->graph, h->s));
             n -= kGraphSteps;
             h->steps += kGraphSteps;
         } else {
-            launch_one(h, h->parity, h->s);
+            launch_one(h, h->parity, h->s, h->stall_next);
+            h->stall_next = false;
             CU(h, cudaGetLastError());
             h->parity ^= 1;
             n--;
@@ -550,6 +705,13 @@ int lbmfvm_step(lbmfvm_t *h, int64_t n) {
         }
     }
     return join_out(h);
+}
+
+int lbmfvm_inject_stall(lbmfvm_t *h) {
+    if (!h) return fail_thread(LBMFVM_ERR_ARG, "handle is NULL");
+    if (!h->use_tma) return fail(h, LBMFVM_ERR_ARG, "the generic step kernel has no staged loads to stall");
+    h->stall_next = true;
+    return LBMFVM_OK;
 }
 
 int lbmfvm_step_count(const lbmfvm_t *h, int64_t *steps) {
@@ -582,6 +744,7 @@ int lbmfvm_nusselt(lbmfvm_t *h, double *mean_hot, double *local_hot, double *mea
     CU(h, cudaStreamSynchronize(h->s));
     if (mean_hot) *mean_hot = means[0];
     if (mean_cold) *mean_cold = means[1];
+    if (int r = check_device_status(h)) return r;
     if (!std::isfinite(means[0]) || !std::isfinite(means[1]))
         return fail(h, LBMFVM_ERR_DIVERGED, "non-finite Nusselt number");
     return join_out(h);
@@ -596,6 +759,10 @@ int lbmfvm_residual(lbmfvm_t *h, double *r) {
     double *red = reinterpret_cast<double *>(h->base + h->L.red);
     CU(h, cudaMemcpyAsync(sums, red + 2 * kResidualBlocks, sizeof(sums), cudaMemcpyDeviceToHost, h->s));
     CU(h, cudaStreamSynchronize(h->s));
+    if (int e = check_device_status(h)) {
+        *r = NAN;
+        return e;
+    }
     if (!std::isfinite(sums[0]) || !std::isfinite(sums[1])) {
         *r = NAN;
         return fail(h, LBMFVM_ERR_DIVERGED, "non-finite velocity in the residual");

@@ -43,9 +43,11 @@ def config_small() -> CavityCase:
     return CavityCase(64, 64, 1e3, 0.71, MA_DEFAULT, 10_000, name="cavity64_Ra1e3")
 
 
-def config_large(n: int = 1024) -> CavityCase:
-    """n x n nodes (1024 by default), Ra = 1e6, Pr = 0.71, U0 = 0.1, 100,000 steps."""
-    return CavityCase(n, n, 1e6, 0.71, MA_DEFAULT, 100_000, name=f"cavity{n}_Ra1e6")
+def config_large(n: int = 1024, Ra: float = 1e6) -> CavityCase:
+    """n x n nodes (1024 by default), Ra = 1e6, Pr = 0.71, U0 = 0.1, 100,000 steps.
+    Larger cavities need a larger Ra to keep the thermal diffusivity
+    U0 H / sqrt(Ra Pr) inside the explicit limit (e.g. Ra = 1e7 at 4096^2)."""
+    return CavityCase(n, n, Ra, 0.71, MA_DEFAULT, 100_000, name=f"cavity{n}_Ra{Ra:.0e}")
 
 
 def random_temperature(ny: int, nx: int, seed: int, lo: float = 0.0, hi: float = 1.0) -> np.ndarray:

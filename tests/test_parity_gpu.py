@@ -21,15 +21,15 @@ U0 = 0.1
 MA = U0 * math.sqrt(3.0)
 
 
-def pair(nx, ny, *, Ra=None, Pr=0.71, Ma=MA, store="f32", tile_y=0, mask=None, **kw):
+def pair(nx, ny, *, Ra=None, Pr=0.71, Ma=MA, store="f32", tile_y=0, mask=None, kernel="auto", **kw):
     """The same case on the GPU (Cavity) and on the oracle."""
     if Ra is not None:
-        gpu = L.Cavity(nx, ny, Ra=Ra, Pr=Pr, Ma=Ma, store=store, tile_y=tile_y, mask=mask, **kw)
+        gpu = L.Cavity(nx, ny, Ra=Ra, Pr=Pr, Ma=Ma, store=store, tile_y=tile_y, mask=mask, kernel=kernel, **kw)
         orc = oracle.Oracle.from_groups(nx, ny, Ra, Pr, Ma, mask=mask, **kw)
     else:
         lat = {k: kw.pop(k) for k in ("nu", "alpha", "gbeta") if k in kw}
         force = kw.pop("force", None)
-        gpu = L.Cavity(nx, ny, store=store, tile_y=tile_y, mask=mask, force=force, **lat, **kw)
+        gpu = L.Cavity(nx, ny, store=store, tile_y=tile_y, mask=mask, force=force, kernel=kernel, **lat, **kw)
         fx, fy = force if force is not None else (0.0, 0.0)
         orc = oracle.Oracle(nx, ny, mask=mask, fx=fx, fy=fy, **lat, **kw)
     return gpu, orc
@@ -54,9 +54,10 @@ def test_config_small_f64_matches_oracle():
     assert d["du"] <= 1e-9 and d["dT"] <= 1e-9 and d["drho"] <= 1e-9, d
 
 
-def test_config_small_f32_matches_oracle():
+@pytest.mark.parametrize("kernel", ["tma", "generic"])
+def test_config_small_f32_matches_oracle(kernel):
     case = WL.config_small()
-    gpu, orc = pair(case.nx, case.ny, Ra=case.Ra, Pr=case.Pr, store="f32")
+    gpu, orc = pair(case.nx, case.ny, Ra=case.Ra, Pr=case.Pr, store="f32", kernel=kernel)
     gpu.step(case.steps)
     orc.step(case.steps)
     d = compare(gpu, orc)
@@ -71,23 +72,67 @@ def obstacle_mask(nx, ny):
                          ("circle", 0.68 * nx, 0.6 * ny, 0.22 * ny)], nx, ny)
 
 
-@pytest.mark.parametrize("store,tol", [("f64", 1e-9), ("f32", 1e-5)])
+@pytest.mark.parametrize("store,tol,kernel", [("f64", 1e-9, "generic"), ("f32", 1e-5, "generic"),
+                                              ("f32", 1e-5, "tma")])
 @pytest.mark.parametrize("tile_y", [4, 8, 16])
-def test_ragged_grid_with_obstacles(store, tol, tile_y):
+def test_ragged_grid_with_obstacles(store, tol, kernel, tile_y):
     nx, ny = 77, 45  # ragged in both directions for every tile shape
     mask = obstacle_mask(nx, ny)
-    gpu, orc = pair(nx, ny, Ra=1e5, store=store, tile_y=tile_y, mask=mask)
+    gpu, orc = pair(nx, ny, Ra=1e5, store=store, tile_y=tile_y, mask=mask, kernel=kernel)
     gpu.step(1500)
     orc.step(1500)
     d = compare(gpu, orc)
     assert d["du"] <= tol and d["dT"] <= tol, d
 
 
+@pytest.mark.parametrize("cfg", [0, 1, 2, 3])
+@pytest.mark.parametrize("store", ["f32", "f16", "bf16"])
+@pytest.mark.parametrize("shape", [(130, 67), (64, 16), (200, 150)])
+def test_tma_and_generic_kernels_agree(store, shape, cfg):
+    """The persistent TMA kernel (every tile shape) and the global-gather
+    kernel compute the same arithmetic; across tile-aligned and ragged grids
+    with obstacles touching several tiles their fields agree to the last few
+    rounding steps."""
+    nx, ny = shape
+    out = {}
+    for kernel in ("tma", "generic"):
+        g = L.Cavity(nx, ny, Ra=1e5, Pr=0.71, Ma=MA, store=store, kernel=kernel, tma_config=cfg,
+                     mask=obstacle_mask(nx, ny))
+        g.step(500)
+        out[kernel] = np.stack(g.fields())
+    d = np.abs(out["tma"] - out["generic"])
+    assert d[1:3].max() <= 1e-6 * U0 and d[3].max() <= 1e-6, d.reshape(4, -1).max(axis=1)
+
+
+def test_bounded_wait_reports_timeout_and_context_survives():
+    case = WL.config_small()
+    gpu, orc = pair(case.nx, case.ny, Ra=case.Ra, Pr=case.Pr, store="f32", kernel="tma")
+    L.lbmfvm_inject_stall(gpu.h)
+    gpu.step(1)
+    with pytest.raises(L.LbmfvmError) as e:
+        gpu.residual()
+    assert e.value.code == L.LBMFVM_ERR_TIMEOUT
+    # the context is still usable: restart and match the oracle again
+    gpu.set_state()
+    gpu.step(500)
+    orc.step(500)
+    d = compare(gpu, orc)
+    assert d["du"] <= 1e-5 and d["dT"] <= 1e-5, d
+
+
+def test_inject_stall_needs_the_tma_kernel():
+    g = L.Cavity(40, 40, Ra=1e4, Pr=0.71, Ma=MA, store="f64")
+    with pytest.raises(L.LbmfvmError) as e:
+        L.lbmfvm_inject_stall(g.h)
+    assert e.value.code == L.LBMFVM_ERR_ARG
+
+
 def test_tile_shapes_agree_bitwise():
     nx, ny = 130, 67
     outs = []
     for ty in (4, 8, 16):
-        g = L.Cavity(nx, ny, Ra=1e5, Pr=0.71, Ma=MA, store="f32", tile_y=ty, mask=obstacle_mask(nx, ny))
+        g = L.Cavity(nx, ny, Ra=1e5, Pr=0.71, Ma=MA, store="f32", tile_y=ty, kernel="generic",
+                     mask=obstacle_mask(nx, ny))
         g.step(300)
         outs.append(np.stack(g.fields()))
     assert (outs[0] == outs[1]).all() and (outs[0] == outs[2]).all()
@@ -192,10 +237,11 @@ def test_full_size_cavity_sampled_against_oracle(store):
     assert d["du"] <= tol and d["dT"] <= tol, d
 
 
+@pytest.mark.parametrize("kernel", ["tma", "generic"])
 @pytest.mark.parametrize("store", ["f16", "bf16"])
-def test_reduced_precision_steady_nusselt(store):
+def test_reduced_precision_steady_nusselt(store, kernel):
     case = WL.config_small()
-    gpu, orc = pair(case.nx, case.ny, Ra=case.Ra, Pr=case.Pr, store=store)
+    gpu, orc = pair(case.nx, case.ny, Ra=case.Ra, Pr=case.Pr, store=store, kernel=kernel)
     steps = 40000
     gpu.step(steps)
     orc.step(steps)
@@ -208,6 +254,11 @@ def test_reduced_precision_steady_nusselt(store):
 
 def test_smallest_grid_and_zero_steps():
     gpu, orc = pair(3, 3, store="f64", nu=0.1, alpha=0.2, gbeta=0.01)
+    tiny, orc2 = pair(3, 3, store="f32", kernel="tma", nu=0.1, alpha=0.2, gbeta=0.01)
+    tiny.step(50)
+    orc2.step(50)
+    d = compare(tiny, orc2)
+    assert d["du"] <= 1e-6 and d["dT"] <= 1e-6
     gpu.step(0)
     assert gpu.steps == 0
     gpu.step(50)
