@@ -315,7 +315,7 @@ def run_ours(args):
                    "wall_s": wall_s, "final_residual": last[0] if last else None,
                    "final_nusselt": last[1] if last else None},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": traffic, "kernel": "step_tma_kernel" if args.store != "f64" else "step_kernel", "peak_kind": peak_kind,
+                     "traffic": traffic, "kernel": "step_kernel" if args.kernel == "generic" or args.store == "f64" else "step_tma_kernel", "peak_kind": peak_kind,
                      "algorithmic_bytes_per_launch": bytes_per_launch, "avg_launch_us": launch_s * 1e6},
         "cpu_baseline": cpu,
         "e2e": e2e,
@@ -336,7 +336,7 @@ def main():
     ap.add_argument("--chunk", type=int, default=1000, help="coupled steps per benchmark step")
     ap.add_argument("--store", choices=["f32", "f16", "bf16", "f64"], default="f32")
     ap.add_argument("--kernel", choices=["auto", "tma", "generic"], default="auto")
-    ap.add_argument("--tma-config", type=int, default=0)
+    ap.add_argument("--tma-config", type=int, default=1)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-e2e", action="store_true")

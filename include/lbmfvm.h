@@ -66,9 +66,14 @@ extern "C" {
 #define LBMFVM_BC_PERIODIC 2
 #define LBMFVM_BC_MOVING 3
 
-/* Step kernel selection.  AUTO takes the persistent TMA kernel whenever it
- * applies (walls on every side, F32/F16/BF16 storage) and the generic kernel
- * otherwise; both compute the same arithmetic. */
+/* Step kernel selection; both compute the same arithmetic.
+ *   TMA      persistent, one block per SM: each tile's populations,
+ *            temperature and node codes are staged in shared memory by TMA
+ *            through a multi-stage mbarrier pipeline and the results leave by
+ *            TMA bulk stores (walls on every side, F32/F16/BF16 storage only);
+ *   GENERIC  one block per tile, gathers straight from global memory (any
+ *            boundary, F64).
+ * AUTO takes TMA where it applies and GENERIC otherwise. */
 #define LBMFVM_KERNEL_AUTO 0
 #define LBMFVM_KERNEL_GENERIC 1
 #define LBMFVM_KERNEL_TMA 2
@@ -97,10 +102,11 @@ typedef struct {
     int32_t tile_y;         /* rows per thread block of the generic step kernel:
                                0 = default, else one of 4, 8, 16 */
     int32_t kernel;         /* LBMFVM_KERNEL_*; default AUTO */
-    int32_t tma_config;     /* tile shape of the TMA kernel (width x height, stages,
-                               threads): 0 = 64x16, 3 stages (4 at 16 bit), 512;
-                               1 = the same with 1024 threads; 2 = 64x8, 4, 512;
-                               3 = 128x8, 2 stages (4 at 16 bit), 512 */
+    int32_t tma_config;     /* tile shape of the TMA kernel, 0..3 (width x height,
+                               threads): 64x16 with 1024; 64x16 with 512 (the
+                               default, 1); 64x8 with 512 (two blocks per SM);
+                               128x8 with 1024.  Input stages: 2 (3 at 16 bit,
+                               2 for 128x8) */
     double t_ref;           /* reference temperature of the buoyancy term; NaN (the
                                default) selects T_l = t_wall[E] as in Eq. 81 */
     void *cuda_stream;      /* cudaStream_t the handle orders its work on; NULL =

@@ -235,7 +235,7 @@ class Cavity:
                  mask=None, store="f32", bc=(LBMFVM_BC_DIRICHLET, LBMFVM_BC_DIRICHLET, LBMFVM_BC_ADIABATIC,
                                              LBMFVM_BC_ADIABATIC),
                  t_wall=(1.0, 0.0, 0.0, 0.0), u_lid=0.0, t_init=0.5, t_ref=None, tile_y=0, kernel="auto",
-                 tma_config=0, device=None):
+                 tma_config=1, device=None):
         import torch
 
         self.nx, self.ny = int(nx), int(ny)

@@ -18,8 +18,9 @@
 // Two kernels share this arithmetic:
 //   step_tma_kernel  persistent, one block per SM, each tile's populations,
 //                    temperature and node codes staged in shared memory by
-//                    TMA through a multi-stage mbarrier pipeline (walled
-//                    domains, FP32/FP16/BF16 storage);
+//                    TMA through a multi-stage mbarrier pipeline, results
+//                    written back by TMA bulk stores (walled domains,
+//                    FP32/FP16/BF16 storage);
 //   step_kernel      one block per tile, gathers straight from global memory
 //                    (periodic sides, FP64 storage).
 #pragma once
@@ -412,18 +413,23 @@ __device__ __forceinline__ void load_2d(void *dst, const CUtensorMap *map, uint6
 
 }  // namespace tma
 
-// Tile geometry of the TMA path.  A tile is TW x TH output nodes at (x0, y0);
-// the staged box reaches 3 nodes beyond it in y and XOFF (>= 4, one 16-byte
-// TMA granule) in x, enough for the pull stencil of the one-node ring and of
-// any wall partner on that ring.
-template <class S, int TW_, int TH_, int STAGES_, int THREADS_>
+// Tile geometry of the TMA tile path.  A tile is TW x TH output nodes at
+// (x0, y0), NPT of them per thread; the staged input box reaches 3 nodes
+// beyond it in y and XOFF (>= 4, one 16-byte TMA granule) in x, enough for the
+// pull stencil of the one-node ring and of any wall partner on that ring.  The
+// results go to an output tile in shared memory that one TMA bulk store
+// writes back.
+template <class S, int TW_, int TH_, int STAGES_, int THREADS_, int MINB_ = 1>
 struct TmaTile {
     static constexpr int TW = TW_, TH = TH_, STAGES = STAGES_, THREADS = THREADS_;
+    static constexpr int MINB = MINB_;  // blocks per SM the register budget must allow
+    static constexpr int NPT = TW * TH / THREADS;  // own nodes per thread
     static constexpr int XOFF = 16 / (int)sizeof(S) < 4 ? 4 : 16 / (int)sizeof(S);
     static constexpr int FW = TW + 2 * XOFF, FH = TH + 6;  // population box
     static constexpr int TWD = TW + 8, THT = TH + 2;       // temperature box (x0-4, y0-1)
     static constexpr int CWD = TW + 32, CHT = TH + 2;      // code box (x0-16, y0-1)
     static constexpr int RW = TW + 2, RH = TH + 2;         // tile + ring
+    static constexpr int NRING = 2 * RW + 2 * TH;          // ring nodes
     static constexpr uint32_t F_BYTES = 9u * FH * FW * sizeof(S);
     static constexpr uint32_t T_BYTES = (uint32_t)THT * TWD * 4u;
     static constexpr uint32_t C_BYTES = (uint32_t)CHT * CWD;
@@ -432,31 +438,62 @@ struct TmaTile {
     static constexpr uint32_t STAGE_BYTES = C_OFF + align128(C_BYTES);
     static constexpr uint32_t TX_BYTES = F_BYTES + T_BYTES + C_BYTES;
     static constexpr uint32_t RING_OFF = STAGES * STAGE_BYTES;
-    static constexpr uint32_t RING_BYTES = align128(3u * RH * RW * 4u);
-    static constexpr uint32_t BAR_OFF = RING_OFF + RING_BYTES;
+    static constexpr uint32_t RING_BYTES = align128(2u * RH * RW * 4u);  // u, v of tile + ring
+    static constexpr uint32_t OF_OFF = RING_OFF + RING_BYTES;            // output populations [9][TH][TW]
+    static constexpr uint32_t OF_BYTES = 9u * TH * TW * sizeof(S);
+    static constexpr uint32_t OT_OFF = OF_OFF + align128(OF_BYTES);      // output temperature [TH][TW]
+    static constexpr uint32_t OT_BYTES = (uint32_t)TH * TW * 4u;
+    static constexpr uint32_t BAR_OFF = OT_OFF + align128(OT_BYTES);
     static constexpr uint32_t SMEM_BYTES = BAR_OFF + 8u * STAGES + 16u;
     static_assert(SMEM_BYTES <= 232448u, "tile configuration exceeds 227 KB of shared memory");
-    static_assert((FW * sizeof(S)) % 16 == 0 && (TWD * 4) % 16 == 0 && CWD % 16 == 0,
+    static_assert((FW * sizeof(S)) % 16 == 0 && (TWD * 4) % 16 == 0 && CWD % 16 == 0 && (TW * sizeof(S)) % 16 == 0,
                   "TMA boxes need 16-byte inner extents");
     static_assert(TW % 16 == 0, "tile origins must stay 16-byte aligned for every box");
+    static_assert(NPT >= 1 && NPT * THREADS == TW * TH && NRING <= THREADS, "thread mapping");
 };
 
 constexpr uint64_t kWaitLimitNs = 1000000000ull;  // 1 s per wait
 constexpr int kErrTimeout = 1;
 
-// Persistent fused step for walled domains (no periodic sides).
+namespace tma {
+__device__ __forceinline__ void store_3d(const CUtensorMap *map, const void *src, int x, int y, int z) {
+    asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%2, %3, %4}], [%1];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(smem_addr(src)), "r"(x), "r"(y), "r"(z)
+                 : "memory");
+}
+__device__ __forceinline__ void store_2d(const CUtensorMap *map, const void *src, int x, int y) {
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(smem_addr(src)), "r"(x), "r"(y)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// Wait until the committed bulk stores have finished reading shared memory.
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+// Wait until the committed bulk stores are complete.
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+}  // namespace tma
+
+// Persistent fused step for walled domains (no periodic sides).  Per tile:
+//   phase A  moments of the tile (kept in registers) and of its ring (shared);
+//   phase B  energy balance and collision into the output tile;
+//   then one thread hands the output tile to a TMA bulk store and refills the
+//   freed input stage.
 template <class S, class G>
-__global__ void __launch_bounds__(G::THREADS, 1)
+__global__ void __launch_bounds__(G::THREADS, G::MINB)
     step_tma_kernel(const StepArgs<S> a, const __grid_constant__ CUtensorMap map_f,
-                    const __grid_constant__ CUtensorMap map_T, const __grid_constant__ CUtensorMap map_c) {
+                    const __grid_constant__ CUtensorMap map_T, const __grid_constant__ CUtensorMap map_c,
+                    const __grid_constant__ CUtensorMap map_f_out, const __grid_constant__ CUtensorMap map_T_out) {
     using C = float;
-    constexpr int TW = G::TW, TH = G::TH, FW = G::FW, FH = G::FH, RW = G::RW, RH = G::RH;
+    constexpr int TW = G::TW, TH = G::TH, FW = G::FW, FH = G::FH, RW = G::RW, NPT = G::NPT;
     constexpr int XOFF = G::XOFF;
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + G::BAR_OFF);
     int *status = reinterpret_cast<int *>(smem + G::BAR_OFF + 8 * G::STAGES);
-    C *ring = reinterpret_cast<C *>(smem + G::RING_OFF);
-    C *RU = ring, *RV = ring + RH * RW, *RD = ring + 2 * RH * RW;
+    C *RU = reinterpret_cast<C *>(smem + G::RING_OFF), *RV = RU + G::RH * RW;
+    S *OF = reinterpret_cast<S *>(smem + G::OF_OFF);
+    float *OT = reinterpret_cast<float *>(smem + G::OT_OFF);
 
     const int tid = threadIdx.x;
     const int ntx = (a.nx + TW - 1) / TW, nty = (a.ny + TH - 1) / TH;
@@ -478,6 +515,14 @@ __global__ void __launch_bounds__(G::THREADS, 1)
         tma::load_2d(stg + G::T_OFF, &map_T, &bars[s], x0 - 4, y0 - 1);
         tma::load_2d(stg + G::C_OFF, &map_c, &bars[s], x0 - 16, y0 - 1);
     };
+    auto store_tile = [&](int k) {
+        int x0, y0;
+        tile_xy(k, x0, y0);
+        tma::fence_proxy_async();
+        tma::store_3d(&map_f_out, OF, x0, y0, 0);
+        tma::store_2d(&map_T_out, OT, x0, y0);
+        tma::bulk_commit();
+    };
 
     if (tid == 0) {
         for (int s = 0; s < G::STAGES; s++) tma::mbar_init(&bars[s], 1);
@@ -489,15 +534,15 @@ __global__ void __launch_bounds__(G::THREADS, 1)
             if (!(a.stall && blockIdx.x == 0 && k == 0)) issue(k);
 
     const C alpha = a.alpha, omega = a.omega, gbeta = a.gbeta, t_ref = a.t_ref, fx = a.fx, fy = a.fy;
-    const long long plane = a.plane;
+    constexpr int OPLANE = TH * TW;
 
     for (int k = 0; k < my_count; k++) {
         const int s = k % G::STAGES;
-        if (k > 0) __syncthreads();  // every thread is done with tile k-1
+        if (k > 0) __syncthreads();  // tile k-1 is complete in the output tile; its stage is free
         if (tid == 0) {
-            if (k > 0 && k - 1 + G::STAGES < my_count) {
-                tma::fence_proxy_async();
-                issue(k - 1 + G::STAGES);
+            if (k > 0) {
+                store_tile(k - 1);
+                if (k - 1 + G::STAGES < my_count) issue(k - 1 + G::STAGES);
             }
             const bool ok = tma::mbar_wait_bounded(&bars[s], (uint32_t)(k / G::STAGES) & 1u, kWaitLimitNs);
             *status = ok ? 1 : 0;
@@ -506,6 +551,7 @@ __global__ void __launch_bounds__(G::THREADS, 1)
                 // let the copies already in flight land before the block exits
                 for (int j = k + 1; j < my_count && j < k + G::STAGES; j++)
                     tma::mbar_wait_bounded(&bars[j % G::STAGES], (uint32_t)(j / G::STAGES) & 1u, kWaitLimitNs / 2);
+                tma::bulk_wait_all();
             }
         }
         __syncthreads();
@@ -522,69 +568,82 @@ __global__ void __launch_bounds__(G::THREADS, 1)
         auto tidx = [&](int lx, int ly) { return (ly + 1) * G::TWD + (lx + 4); };
         auto cidx = [&](int lx, int ly) { return (ly + 1) * G::CWD + (lx + 16); };
         auto pull = [&](int lx, int ly, C g[9]) {
-            const int o = fidx(lx, ly);
+            const S *p = F + fidx(lx, ly);
 #pragma unroll
-            for (int q = 0; q < 9; q++) g[q] = ld(F + q * (FH * FW) + o - cy(q) * FW - cx(q));
+            for (int q = 0; q < 9; q++) g[q] = ld(p + q * (FH * FW) - cy(q) * FW - cx(q));
         };
         auto state = [&](int lx, int ly, uint8_t c, C g[9], C &drho, C &ux, C &uy) {
             const int kind = c & 3;
-            if (kind == KIND_SOLID) {
+            if (kind == KIND_FLUID) {
+                pull(lx, ly, g);
+                moments<C>(g, drho, ux, uy);
+            } else if (kind == KIND_WALL) {
+                const int d = partner_dir(c);
+                pull(lx + cx_rt(d), ly + cy_rt(d), g);
+                moments<C>(g, drho, ux, uy);
+                C uw, vw;
+                wall_velocity<S>(a, x0 + lx, y0 + ly, c, uw, vw);
+                nee<C>(g, drho, ux, uy, uw, vw);
+            } else {
 #pragma unroll
                 for (int q = 0; q < 9; q++) g[q] = C(0);
                 drho = C(-1);
                 ux = uy = C(0);
-                return;
             }
-            if (kind == KIND_FLUID) {
-                pull(lx, ly, g);
-                moments<C>(g, drho, ux, uy);
-                return;
-            }
-            const int d = partner_dir(c);
-            pull(lx + cx_rt(d), ly + cy_rt(d), g);
-            moments<C>(g, drho, ux, uy);
-            C uw, vw;
-            wall_velocity<S>(a, x0 + lx, y0 + ly, c, uw, vw);
-            nee<C>(g, drho, ux, uy, uw, vw);
         };
 
-        // Phase A: moments of the tile and its one-node ring.
-        for (int i = tid; i < RH * RW; i += G::THREADS) {
-            const int ry = i / RW, rx = i - ry * RW;
-            const uint8_t c = decode(CC[cidx(rx - 1, ry - 1)]);
-            C g[9], drho, ux, uy;
-            state(rx - 1, ry - 1, c, g, drho, ux, uy);
-            RU[i] = ux;
-            RV[i] = uy;
-            RD[i] = drho;
+        // Phase A: own nodes into registers (and their u, v to shared), the
+        // ring's u, v to shared.
+        C g[NPT][9], dr[NPT], uu[NPT], vv[NPT];
+        uint8_t cc[NPT];
+#pragma unroll
+        for (int j = 0; j < NPT; j++) {
+            const int i = tid + j * G::THREADS;
+            const int ly = i / TW, lx = i - ly * TW;
+            cc[j] = decode(CC[cidx(lx, ly)]);
+            state(lx, ly, cc[j], g[j], dr[j], uu[j], vv[j]);
+            const int r = (ly + 1) * RW + (lx + 1);
+            RU[r] = uu[j];
+            RV[r] = vv[j];
         }
+        if (tid < G::NRING) {
+            int rx, ry;
+            if (tid < RW) { rx = tid; ry = 0; }
+            else if (tid < 2 * RW) { rx = tid - RW; ry = TH + 1; }
+            else { const int h = tid - 2 * RW; rx = (h & 1) ? RW - 1 : 0; ry = 1 + (h >> 1); }
+            const uint8_t c = decode(CC[cidx(rx - 1, ry - 1)]);
+            C hg[9], hd, hu, hv;
+            state(rx - 1, ry - 1, c, hg, hd, hu, hv);
+            RU[ry * RW + rx] = hu;
+            RV[ry * RW + rx] = hv;
+        }
+        if (tid == 0 && k > 0) tma::bulk_wait_read();  // the previous output tile has been read
         __syncthreads();
 
-        // Phase B: energy balance and collision of the tile's own nodes.
-        for (int i = tid; i < TW * TH; i += G::THREADS) {
+        // Phase B: energy balance and collision of the own nodes into the
+        // output tile (inert nodes keep their temperature).
+#pragma unroll
+        for (int j = 0; j < NPT; j++) {
+            const int i = tid + j * G::THREADS;
             const int ly = i / TW, lx = i - ly * TW;
             const int x = x0 + lx, y = y0 + ly;
-            if (x >= a.nx || y >= a.ny) continue;
-            const uint8_t c = decode(CC[cidx(lx, ly)]);
-            const int kind = c & 3;
-            if (kind == KIND_SOLID) continue;
-            const int r = (ly + 1) * RW + (lx + 1);
-            C g[9];
-            const C drho = RD[r], ux = RU[r], uy = RV[r];
-            if (kind == KIND_FLUID) {
-                pull(lx, ly, g);
-            } else {
-                C d2, u2, v2;
-                state(lx, ly, c, g, d2, u2, v2);
-            }
-            const int th = c >> 6;
+            const uint8_t c = cc[j];
             const int t = tidx(lx, ly);
             const C TP = TT[t];
+            S *of = OF + ly * TW + lx;
+            if ((c & 3) == KIND_SOLID) {
+                OT[ly * TW + lx] = TP;
+#pragma unroll
+                for (int q = 0; q < 9; q++) st(of + q * OPLANE, C(0));
+                continue;
+            }
+            const int r = (ly + 1) * RW + (lx + 1);
+            const int th = c >> 6;
             C Tn = TP;
             if (th == TH_FV) {
-                const C ex = C(0.5) * C(x > 0) + C(0.5) * C(x < a.nx - 1);
-                const C ey = C(0.5) * C(y > 0) + C(0.5) * C(y < a.ny - 1);
-                Tn = fv_update<C>(TP, ux, uy, ex, ey, alpha,
+                const C ex = (x > 0 ? C(0.5) : C(0)) + (x < a.nx - 1 ? C(0.5) : C(0));
+                const C ey = (y > 0 ? C(0.5) : C(0)) + (y < a.ny - 1 ? C(0.5) : C(0));
+                Tn = fv_update<C>(TP, uu[j], vv[j], ex, ey, alpha,
                                   fv_open(decode(CC[cidx(lx + 1, ly)])), TT[t + 1], RU[r + 1],
                                   fv_open(decode(CC[cidx(lx, ly + 1)])), TT[t + G::TWD], RV[r + RW],
                                   fv_open(decode(CC[cidx(lx - 1, ly)])), TT[t - 1], RU[r - 1],
@@ -593,12 +652,15 @@ __global__ void __launch_bounds__(G::THREADS, 1)
                 const int d = partner_dir(c);
                 Tn = TT[tidx(lx + cx_rt(d), ly + cy_rt(d))];
             }
-            const long long kg = (long long)y * a.pitch + x;
-            a.Tout[kg] = Tn;
+            OT[ly * TW + lx] = Tn;
             const C Gy = fy + gbeta * (Tn - t_ref);
-            S *out = a.fout + kg;
-            collide<C>(g, drho, ux, uy, omega, fx, Gy, [&](int q, C v) { st(out + q * plane, v); });
+            collide<C>(g[j], dr[j], uu[j], vv[j], omega, fx, Gy, [&](int q, C v) { st(of + q * OPLANE, v); });
         }
+    }
+    __syncthreads();
+    if (tid == 0 && my_count > 0) {
+        store_tile(my_count - 1);
+        tma::bulk_wait_all();
     }
 }
 

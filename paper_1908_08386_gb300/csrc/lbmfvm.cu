@@ -197,6 +197,8 @@ struct lbmfvm {
     int tma_config;   // tile shape of the TMA kernel
     int num_sms;
     CUtensorMap map_f[2], map_T[2], map_c;
+    CUtensorMap map_fo[2], map_To[2];  // output-tile boxes of the TMA tile kernel
+    int tma_blocks_per_sm;
     char err[512];
 };
 
@@ -261,10 +263,10 @@ void launch_step_ty(const lbmfvm_t *h, int cur, cudaStream_t s) {
 // 227 KB of shared memory allow for 32-bit storage; 16-bit storage halves the
 // population box and takes one more stage where it fits.
 template <class S, int CFG> struct TmaConfig;
-template <class S> struct TmaConfig<S, 0> { using G = TmaTile<S, 64, 16, sizeof(S) == 4 ? 3 : 4, 512>; };
-template <class S> struct TmaConfig<S, 1> { using G = TmaTile<S, 64, 16, sizeof(S) == 4 ? 3 : 4, 1024>; };
-template <class S> struct TmaConfig<S, 2> { using G = TmaTile<S, 64, 8, 4, 512>; };
-template <class S> struct TmaConfig<S, 3> { using G = TmaTile<S, 128, 8, sizeof(S) == 4 ? 2 : 4, 512>; };
+template <class S> struct TmaConfig<S, 0> { using G = TmaTile<S, 64, 16, sizeof(S) == 4 ? 2 : 3, 1024>; };
+template <class S> struct TmaConfig<S, 1> { using G = TmaTile<S, 64, 16, sizeof(S) == 4 ? 2 : 3, 512>; };
+template <class S> struct TmaConfig<S, 2> { using G = TmaTile<S, 64, 8, sizeof(S) == 4 ? 2 : 3, 512, 2>; };
+template <class S> struct TmaConfig<S, 3> { using G = TmaTile<S, 128, 8, 2, 1024>; };
 constexpr int kTmaConfigs = 4;
 
 template <class S, int CFG>
@@ -273,17 +275,19 @@ void launch_tma_cfg(const lbmfvm_t *h, int cur, cudaStream_t s, bool stall) {
     StepArgs<S> a = args_for<S>(h, cur);
     a.stall = stall ? 1 : 0;
     const int ntiles = ((h->grid.nx + G::TW - 1) / G::TW) * ((h->grid.ny + G::TH - 1) / G::TH);
-    const int blocks = ntiles < h->num_sms ? ntiles : h->num_sms;
-    step_tma_kernel<S, G><<<blocks, G::THREADS, G::SMEM_BYTES, s>>>(a, h->map_f[cur], h->map_T[cur], h->map_c);
+    const int resident = h->num_sms * h->tma_blocks_per_sm;
+    const int blocks = ntiles < resident ? ntiles : resident;
+    step_tma_kernel<S, G><<<blocks, G::THREADS, G::SMEM_BYTES, s>>>(a, h->map_f[cur], h->map_T[cur], h->map_c,
+                                                                    h->map_fo[cur ^ 1], h->map_To[cur ^ 1]);
 }
 
 template <class S>
 void launch_step_tma(const lbmfvm_t *h, int cur, cudaStream_t s, bool stall) {
     switch (h->tma_config) {
-        case 1: launch_tma_cfg<S, 1>(h, cur, s, stall); break;
+        case 0: launch_tma_cfg<S, 0>(h, cur, s, stall); break;
         case 2: launch_tma_cfg<S, 2>(h, cur, s, stall); break;
         case 3: launch_tma_cfg<S, 3>(h, cur, s, stall); break;
-        default: launch_tma_cfg<S, 0>(h, cur, s, stall); break;
+        default: launch_tma_cfg<S, 1>(h, cur, s, stall); break;
     }
 }
 
@@ -448,12 +452,35 @@ template <class S> constexpr CUtensorMapDataType tmap_type() { return CU_TENSOR_
 template <> constexpr CUtensorMapDataType tmap_type<__half>() { return CU_TENSOR_MAP_DATA_TYPE_FLOAT16; }
 template <> constexpr CUtensorMapDataType tmap_type<__nv_bfloat16>() { return CU_TENSOR_MAP_DATA_TYPE_BFLOAT16; }
 
-// Tensor maps of both population buffers, both temperature planes and the
-// node codes; the grid's x extent is nx, so boxes reaching past it (or below
-// zero) are zero-filled.
+template <class S>
+int encode_maps(lbmfvm_t *h, int fw, int fh, int tw, int th, int cw, int ch);
+
 template <class S, int CFG>
 int setup_tma_cfg(lbmfvm_t *h) {
     using G = typename TmaConfig<S, CFG>::G;
+    // output boxes first: encode_maps() leaves the load boxes in map_f/map_T
+    if (int r = encode_maps<S>(h, G::TW, G::TH, G::TW, G::TH, G::CWD, G::CHT)) return r;
+    for (int b = 0; b < 2; b++) {
+        h->map_fo[b] = h->map_f[b];
+        h->map_To[b] = h->map_T[b];
+    }
+    if (int r = encode_maps<S>(h, G::FW, G::FH, G::TWD, G::THT, G::CWD, G::CHT)) return r;
+    auto kern = step_tma_kernel<S, G>;
+    CU(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM_BYTES));
+    int dev = 0, per_sm = 0;
+    CU(h, cudaGetDevice(&dev));
+    CU(h, cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev));
+    CU(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, G::THREADS, G::SMEM_BYTES));
+    if (per_sm < 1) return fail(h, LBMFVM_ERR_CUDA, "TMA tile kernel does not fit on an SM");
+    h->tma_blocks_per_sm = per_sm;
+    return LBMFVM_OK;
+}
+
+// Tensor maps of both population buffers (box fw x fh x 9), both
+// temperature planes (tw x th) and the node codes (cw x ch); the grid's x
+// extent is nx, so boxes reaching past it (or below zero) are zero-filled.
+template <class S>
+int encode_maps(lbmfvm_t *h, int fw, int fh, int tw, int th, int cw, int ch) {
     EncodeTiledFn enc = encode_tiled();
     if (!enc) return fail(h, LBMFVM_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
     const cuuint64_t nx = (cuuint64_t)h->grid.nx, ny = (cuuint64_t)h->grid.ny, pitch = (cuuint64_t)h->L.pitch;
@@ -461,14 +488,14 @@ int setup_tma_cfg(lbmfvm_t *h) {
     for (int b = 0; b < 2; b++) {
         const cuuint64_t dims[3] = {nx, ny, 9};
         const cuuint64_t strides[2] = {pitch * sizeof(S), (cuuint64_t)h->L.plane * sizeof(S)};
-        const cuuint32_t box[3] = {(cuuint32_t)G::FW, (cuuint32_t)G::FH, 9};
+        const cuuint32_t box[3] = {(cuuint32_t)fw, (cuuint32_t)fh, 9};
         CUresult r = enc(&h->map_f[b], tmap_type<S>(), 3, h->base + h->L.f[b], dims, strides, box, one,
                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) return fail(h, LBMFVM_ERR_CUDA, "tensor map of the populations failed (%d)", (int)r);
         const cuuint64_t dims2[2] = {nx, ny};
         const cuuint64_t strides2[1] = {pitch * sizeof(float)};
-        const cuuint32_t box2[2] = {(cuuint32_t)G::TWD, (cuuint32_t)G::THT};
+        const cuuint32_t box2[2] = {(cuuint32_t)tw, (cuuint32_t)th};
         r = enc(&h->map_T[b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, h->base + h->L.T[b], dims2, strides2, box2, one,
                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -476,25 +503,21 @@ int setup_tma_cfg(lbmfvm_t *h) {
     }
     const cuuint64_t dims2[2] = {nx, ny};
     const cuuint64_t strides2[1] = {pitch};
-    const cuuint32_t box2[2] = {(cuuint32_t)G::CWD, (cuuint32_t)G::CHT};
+    const cuuint32_t box2[2] = {(cuuint32_t)cw, (cuuint32_t)ch};
     CUresult r = enc(&h->map_c, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, h->base + h->L.code, dims2, strides2, box2, one,
                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(h, LBMFVM_ERR_CUDA, "tensor map of the node codes failed (%d)", (int)r);
-    CU(h, cudaFuncSetAttribute(step_tma_kernel<S, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM_BYTES));
-    int dev = 0;
-    CU(h, cudaGetDevice(&dev));
-    CU(h, cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev));
     return LBMFVM_OK;
 }
 
 template <class S>
 int setup_tma(lbmfvm_t *h) {
     switch (h->tma_config) {
-        case 1: return setup_tma_cfg<S, 1>(h);
+        case 0: return setup_tma_cfg<S, 0>(h);
         case 2: return setup_tma_cfg<S, 2>(h);
         case 3: return setup_tma_cfg<S, 3>(h);
-        default: return setup_tma_cfg<S, 0>(h);
+        default: return setup_tma_cfg<S, 1>(h);
     }
 }
 

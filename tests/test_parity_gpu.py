@@ -85,28 +85,34 @@ def test_ragged_grid_with_obstacles(store, tol, kernel, tile_y):
     assert d["du"] <= tol and d["dT"] <= tol, d
 
 
+@pytest.mark.parametrize("kernel", ["tma"])
 @pytest.mark.parametrize("cfg", [0, 1, 2, 3])
 @pytest.mark.parametrize("store", ["f32", "f16", "bf16"])
-@pytest.mark.parametrize("shape", [(130, 67), (64, 16), (200, 150)])
-def test_tma_and_generic_kernels_agree(store, shape, cfg):
-    """The persistent TMA kernel (every tile shape) and the global-gather
-    kernel compute the same arithmetic; across tile-aligned and ragged grids
-    with obstacles touching several tiles their fields agree to the last few
-    rounding steps."""
+@pytest.mark.parametrize("shape", [(130, 67), (64, 16), (200, 150), (31, 97)])
+def test_tma_kernels_agree_with_generic(store, shape, cfg, kernel):
+    """The TMA-staged kernels (every shape index) and the global-gather kernel
+    compute the same arithmetic; across aligned and ragged grids with
+    obstacles crossing tile borders their fields agree to
+    the last few rounding steps."""
     nx, ny = shape
     out = {}
-    for kernel in ("tma", "generic"):
-        g = L.Cavity(nx, ny, Ra=1e5, Pr=0.71, Ma=MA, store=store, kernel=kernel, tma_config=cfg,
+    for k in (kernel, "generic"):
+        g = L.Cavity(nx, ny, Ra=1e5, Pr=0.71, Ma=MA, store=store, kernel=k, tma_config=cfg,
                      mask=obstacle_mask(nx, ny))
         g.step(500)
-        out[kernel] = np.stack(g.fields())
-    d = np.abs(out["tma"] - out["generic"])
-    assert d[1:3].max() <= 1e-6 * U0 and d[3].max() <= 1e-6, d.reshape(4, -1).max(axis=1)
+        out[k] = np.stack(g.fields())
+    d = np.abs(out[kernel] - out["generic"])
+    # FP32 storage: a few rounding steps.  16-bit storage re-quantises every
+    # step, so one differently contracted FMA grows into storage-level noise;
+    # an indexing error would still show up at the scale of U0 and of dT = 1.
+    tol_u, tol_T = (1e-6 * U0, 1e-6) if store == "f32" else (2e-3 * U0, 2e-3)
+    assert d[1:3].max() <= tol_u and d[3].max() <= tol_T, d.reshape(4, -1).max(axis=1)
 
 
 def test_bounded_wait_reports_timeout_and_context_survives():
+    kernel = "tma"
     case = WL.config_small()
-    gpu, orc = pair(case.nx, case.ny, Ra=case.Ra, Pr=case.Pr, store="f32", kernel="tma")
+    gpu, orc = pair(case.nx, case.ny, Ra=case.Ra, Pr=case.Pr, store="f32", kernel=kernel)
     L.lbmfvm_inject_stall(gpu.h)
     gpu.step(1)
     with pytest.raises(L.LbmfvmError) as e:
@@ -254,11 +260,12 @@ def test_reduced_precision_steady_nusselt(store, kernel):
 
 def test_smallest_grid_and_zero_steps():
     gpu, orc = pair(3, 3, store="f64", nu=0.1, alpha=0.2, gbeta=0.01)
-    tiny, orc2 = pair(3, 3, store="f32", kernel="tma", nu=0.1, alpha=0.2, gbeta=0.01)
-    tiny.step(50)
-    orc2.step(50)
-    d = compare(tiny, orc2)
-    assert d["du"] <= 1e-6 and d["dT"] <= 1e-6
+    for kernel in ("tma",):
+        tiny, orc2 = pair(3, 3, store="f32", kernel=kernel, nu=0.1, alpha=0.2, gbeta=0.01)
+        tiny.step(50)
+        orc2.step(50)
+        d = compare(tiny, orc2)
+        assert d["du"] <= 1e-6 and d["dT"] <= 1e-6
     gpu.step(0)
     assert gpu.steps == 0
     gpu.step(50)
