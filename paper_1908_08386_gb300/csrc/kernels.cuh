@@ -416,13 +416,13 @@ __device__ __forceinline__ void load_2d(void *dst, const CUtensorMap *map, uint6
 // Tile geometry of the TMA tile path.  A tile is TW x TH output nodes at
 // (x0, y0), NPT of them per thread; the staged input box reaches 3 nodes
 // beyond it in y and XOFF (>= 4, one 16-byte TMA granule) in x, enough for the
-// pull stencil of the one-node ring and of any wall partner on that ring.  The
-// results go to an output tile in shared memory that one TMA bulk store
-// writes back.
+// pull stencil of the one-node ring and of any wall partner on that ring.
+// Once a tile's moments are taken, its staged populations are dead and the
+// same bytes receive the tile's results, which one TMA bulk store writes back.
 template <class S, int TW_, int TH_, int STAGES_, int THREADS_, int MINB_ = 1>
 struct TmaTile {
     static constexpr int TW = TW_, TH = TH_, STAGES = STAGES_, THREADS = THREADS_;
-    static constexpr int MINB = MINB_;  // blocks per SM the register budget must allow
+    static constexpr int MINB = MINB_;             // blocks per SM the register budget must allow
     static constexpr int NPT = TW * TH / THREADS;  // own nodes per thread
     static constexpr int XOFF = 16 / (int)sizeof(S) < 4 ? 4 : 16 / (int)sizeof(S);
     static constexpr int FW = TW + 2 * XOFF, FH = TH + 6;  // population box
@@ -437,19 +437,21 @@ struct TmaTile {
     static constexpr uint32_t F_OFF = 0, T_OFF = align128(F_BYTES), C_OFF = T_OFF + align128(T_BYTES);
     static constexpr uint32_t STAGE_BYTES = C_OFF + align128(C_BYTES);
     static constexpr uint32_t TX_BYTES = F_BYTES + T_BYTES + C_BYTES;
+    // results, inside the stage's population bytes: [9][TH][TW] then [TH][TW]
+    static constexpr uint32_t OF_BYTES = 9u * TH * TW * sizeof(S);
+    static constexpr uint32_t OT_OFF = align128(OF_BYTES);
+    static constexpr uint32_t OT_BYTES = (uint32_t)TH * TW * 4u;
     static constexpr uint32_t RING_OFF = STAGES * STAGE_BYTES;
     static constexpr uint32_t RING_BYTES = align128(2u * RH * RW * 4u);  // u, v of tile + ring
-    static constexpr uint32_t OF_OFF = RING_OFF + RING_BYTES;            // output populations [9][TH][TW]
-    static constexpr uint32_t OF_BYTES = 9u * TH * TW * sizeof(S);
-    static constexpr uint32_t OT_OFF = OF_OFF + align128(OF_BYTES);      // output temperature [TH][TW]
-    static constexpr uint32_t OT_BYTES = (uint32_t)TH * TW * 4u;
-    static constexpr uint32_t BAR_OFF = OT_OFF + align128(OT_BYTES);
+    static constexpr uint32_t BAR_OFF = RING_OFF + 2u * RING_BYTES;      // two ring buffers
     static constexpr uint32_t SMEM_BYTES = BAR_OFF + 8u * STAGES + 16u;
     static_assert(SMEM_BYTES <= 232448u, "tile configuration exceeds 227 KB of shared memory");
+    static_assert(OT_OFF + OT_BYTES <= F_BYTES, "results must fit in the staged population bytes");
     static_assert((FW * sizeof(S)) % 16 == 0 && (TWD * 4) % 16 == 0 && CWD % 16 == 0 && (TW * sizeof(S)) % 16 == 0,
                   "TMA boxes need 16-byte inner extents");
     static_assert(TW % 16 == 0, "tile origins must stay 16-byte aligned for every box");
     static_assert(NPT >= 1 && NPT * THREADS == TW * TH && NRING <= THREADS, "thread mapping");
+    static_assert(STAGES >= 2, "the pipeline needs two stages");
 };
 
 constexpr uint64_t kWaitLimitNs = 1000000000ull;  // 1 s per wait
@@ -475,11 +477,20 @@ __device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.w
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 }  // namespace tma
 
-// Persistent fused step for walled domains (no periodic sides).  Per tile:
-//   phase A  moments of the tile (kept in registers) and of its ring (shared);
-//   phase B  energy balance and collision into the output tile;
-//   then one thread hands the output tile to a TMA bulk store and refills the
-//   freed input stage.
+// Persistent fused step for walled domains (no periodic sides).  Tile k of a
+// block runs
+//   wait    every thread waits (bounded) for stage k % STAGES to land;
+//   phase A moments of the own nodes (kept in registers) and of the ring
+//           (u, v to ring buffer k % 2);
+//   barrier the only block-wide one per tile;
+//   store   thread 0 hands tile k-1's results to a TMA bulk store;
+//   phase B energy balance and collision of the own nodes, results into the
+//           stage's population bytes;
+//   refill  thread 0, once the store of tile k-1 has read its stage, loads
+//           tile k-1+STAGES into it.
+// A wait that runs out raises a shared abort flag that every thread checks
+// after the barrier, so the block leaves together and a device status word
+// tells the host.
 template <class S, class G>
 __global__ void __launch_bounds__(G::THREADS, G::MINB)
     step_tma_kernel(const StepArgs<S> a, const __grid_constant__ CUtensorMap map_f,
@@ -488,12 +499,10 @@ __global__ void __launch_bounds__(G::THREADS, G::MINB)
     using C = float;
     constexpr int TW = G::TW, TH = G::TH, FW = G::FW, FH = G::FH, RW = G::RW, NPT = G::NPT;
     constexpr int XOFF = G::XOFF;
+    constexpr int OPLANE = TH * TW;
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + G::BAR_OFF);
-    int *status = reinterpret_cast<int *>(smem + G::BAR_OFF + 8 * G::STAGES);
-    C *RU = reinterpret_cast<C *>(smem + G::RING_OFF), *RV = RU + G::RH * RW;
-    S *OF = reinterpret_cast<S *>(smem + G::OF_OFF);
-    float *OT = reinterpret_cast<float *>(smem + G::OT_OFF);
+    int *abort_flag = reinterpret_cast<int *>(smem + G::BAR_OFF + 8 * G::STAGES);
 
     const int tid = threadIdx.x;
     const int ntx = (a.nx + TW - 1) / TW, nty = (a.ny + TH - 1) / TH;
@@ -505,11 +514,12 @@ __global__ void __launch_bounds__(G::THREADS, G::MINB)
         x0 = (t - ty * ntx) * TW;
         y0 = ty * TH;
     };
+    auto stage = [&](int k) { return smem + (k % G::STAGES) * G::STAGE_BYTES; };
     auto issue = [&](int k) {
         const int s = k % G::STAGES;
         int x0, y0;
         tile_xy(k, x0, y0);
-        unsigned char *stg = smem + s * G::STAGE_BYTES;
+        unsigned char *stg = stage(k);
         tma::mbar_arrive_expect_tx(&bars[s], G::TX_BYTES);
         tma::load_3d(stg + G::F_OFF, &map_f, &bars[s], x0 - XOFF, y0 - 3, 0);
         tma::load_2d(stg + G::T_OFF, &map_T, &bars[s], x0 - 4, y0 - 1);
@@ -518,14 +528,16 @@ __global__ void __launch_bounds__(G::THREADS, G::MINB)
     auto store_tile = [&](int k) {
         int x0, y0;
         tile_xy(k, x0, y0);
+        unsigned char *stg = stage(k);
         tma::fence_proxy_async();
-        tma::store_3d(&map_f_out, OF, x0, y0, 0);
-        tma::store_2d(&map_T_out, OT, x0, y0);
+        tma::store_3d(&map_f_out, stg + G::F_OFF, x0, y0, 0);
+        tma::store_2d(&map_T_out, stg + G::F_OFF + G::OT_OFF, x0, y0);
         tma::bulk_commit();
     };
 
     if (tid == 0) {
         for (int s = 0; s < G::STAGES; s++) tma::mbar_init(&bars[s], 1);
+        *abort_flag = 0;
         tma::fence_mbar_init();
     }
     __syncthreads();
@@ -534,35 +546,20 @@ __global__ void __launch_bounds__(G::THREADS, G::MINB)
             if (!(a.stall && blockIdx.x == 0 && k == 0)) issue(k);
 
     const C alpha = a.alpha, omega = a.omega, gbeta = a.gbeta, t_ref = a.t_ref, fx = a.fx, fy = a.fy;
-    constexpr int OPLANE = TH * TW;
 
     for (int k = 0; k < my_count; k++) {
-        const int s = k % G::STAGES;
-        if (k > 0) __syncthreads();  // tile k-1 is complete in the output tile; its stage is free
-        if (tid == 0) {
-            if (k > 0) {
-                store_tile(k - 1);
-                if (k - 1 + G::STAGES < my_count) issue(k - 1 + G::STAGES);
-            }
-            const bool ok = tma::mbar_wait_bounded(&bars[s], (uint32_t)(k / G::STAGES) & 1u, kWaitLimitNs);
-            *status = ok ? 1 : 0;
-            if (!ok) {
-                atomicOr(a.err, kErrTimeout);
-                // let the copies already in flight land before the block exits
-                for (int j = k + 1; j < my_count && j < k + G::STAGES; j++)
-                    tma::mbar_wait_bounded(&bars[j % G::STAGES], (uint32_t)(j / G::STAGES) & 1u, kWaitLimitNs / 2);
-                tma::bulk_wait_all();
-            }
+        unsigned char *stg = stage(k);
+        if (!tma::mbar_wait_bounded(&bars[k % G::STAGES], (uint32_t)(k / G::STAGES) & 1u, kWaitLimitNs)) {
+            atomicOr(abort_flag, 1);
+            atomicOr(a.err, kErrTimeout);
         }
-        __syncthreads();
-        if (*status == 0) return;
 
         int x0, y0;
         tile_xy(k, x0, y0);
-        const unsigned char *stg = smem + s * G::STAGE_BYTES;
         const S *F = reinterpret_cast<const S *>(stg + G::F_OFF);
         const float *TT = reinterpret_cast<const float *>(stg + G::T_OFF);
         const uint8_t *CC = reinterpret_cast<const uint8_t *>(stg + G::C_OFF);
+        C *RU = reinterpret_cast<C *>(smem + G::RING_OFF + (k & 1) * G::RING_BYTES), *RV = RU + G::RH * RW;
         // staged-box index of node (lx, ly) relative to the tile origin
         auto fidx = [&](int lx, int ly) { return (ly + 3) * FW + (lx + XOFF); };
         auto tidx = [&](int lx, int ly) { return (ly + 1) * G::TWD + (lx + 4); };
@@ -592,8 +589,8 @@ __global__ void __launch_bounds__(G::THREADS, G::MINB)
             }
         };
 
-        // Phase A: own nodes into registers (and their u, v to shared), the
-        // ring's u, v to shared.
+        // Phase A: own nodes into registers (their u, v also to the ring
+        // buffer), the ring's u, v.
         C g[NPT][9], dr[NPT], uu[NPT], vv[NPT];
         uint8_t cc[NPT];
 #pragma unroll
@@ -617,11 +614,22 @@ __global__ void __launch_bounds__(G::THREADS, G::MINB)
             RU[ry * RW + rx] = hu;
             RV[ry * RW + rx] = hv;
         }
-        if (tid == 0 && k > 0) tma::bulk_wait_read();  // the previous output tile has been read
         __syncthreads();
+        if (*abort_flag) {
+            if (tid == 0) {
+                // let the copies already in flight land before the block exits
+                for (int j = k + 1; j < my_count && j < k + G::STAGES; j++)
+                    tma::mbar_wait_bounded(&bars[j % G::STAGES], (uint32_t)(j / G::STAGES) & 1u, kWaitLimitNs / 2);
+                tma::bulk_wait_all();
+            }
+            return;
+        }
+        if (tid == 0 && k > 0) store_tile(k - 1);
 
-        // Phase B: energy balance and collision of the own nodes into the
-        // output tile (inert nodes keep their temperature).
+        // Phase B: energy balance and collision of the own nodes; results go
+        // to the stage's (now dead) population bytes.  Inert nodes keep T.
+        S *OF = reinterpret_cast<S *>(stg + G::F_OFF);
+        float *OT = reinterpret_cast<float *>(stg + G::F_OFF + G::OT_OFF);
 #pragma unroll
         for (int j = 0; j < NPT; j++) {
             const int i = tid + j * G::THREADS;
@@ -655,6 +663,10 @@ __global__ void __launch_bounds__(G::THREADS, G::MINB)
             OT[ly * TW + lx] = Tn;
             const C Gy = fy + gbeta * (Tn - t_ref);
             collide<C>(g[j], dr[j], uu[j], vv[j], omega, fx, Gy, [&](int q, C v) { st(of + q * OPLANE, v); });
+        }
+        if (tid == 0 && k > 0 && k - 1 + G::STAGES < my_count) {
+            tma::bulk_wait_read();  // the results of tile k-1 have left its stage
+            issue(k - 1 + G::STAGES);
         }
     }
     __syncthreads();

@@ -263,10 +263,10 @@ void launch_step_ty(const lbmfvm_t *h, int cur, cudaStream_t s) {
 // 227 KB of shared memory allow for 32-bit storage; 16-bit storage halves the
 // population box and takes one more stage where it fits.
 template <class S, int CFG> struct TmaConfig;
-template <class S> struct TmaConfig<S, 0> { using G = TmaTile<S, 64, 16, sizeof(S) == 4 ? 2 : 3, 1024>; };
-template <class S> struct TmaConfig<S, 1> { using G = TmaTile<S, 64, 16, sizeof(S) == 4 ? 2 : 3, 512>; };
+template <class S> struct TmaConfig<S, 0> { using G = TmaTile<S, 64, 16, 3, 1024>; };
+template <class S> struct TmaConfig<S, 1> { using G = TmaTile<S, 64, 16, 3, 512>; };
 template <class S> struct TmaConfig<S, 2> { using G = TmaTile<S, 64, 8, sizeof(S) == 4 ? 2 : 3, 512, 2>; };
-template <class S> struct TmaConfig<S, 3> { using G = TmaTile<S, 128, 8, 2, 1024>; };
+template <class S> struct TmaConfig<S, 3> { using G = TmaTile<S, 128, 8, sizeof(S) == 4 ? 2 : 3, 1024>; };
 constexpr int kTmaConfigs = 4;
 
 template <class S, int CFG>
