@@ -200,6 +200,28 @@ int lbmfvm_run_to_steady(lbmfvm_t *h, double tol, int64_t check_every, int64_t m
 /* Derived lattice parameters: nu, alpha, gbeta, tau (any may be NULL). */
 int lbmfvm_params(const lbmfvm_t *h, double *nu, double *alpha, double *gbeta, double *tau);
 
+/* The residual of lbmfvm_residual computed on caller arrays without any
+ * device allocation (the paper has no counterpart; this is a service for
+ * callers that cannot allocate: code running under CUDA graph capture, code
+ * whose device memory belongs to another allocator, loops that cannot pay for
+ * cudaMalloc's implicit synchronisation).
+ *   r = ||(u, v) - (u_prev, v_prev)||_2 / ||(u, v)||_2 in FP64 over the nodes
+ *   with select[i] != 0 (all n nodes if select is NULL).
+ * u, v, u_prev, v_prev: device arrays of n doubles; select: device array of n
+ * bytes or NULL; stream: cudaStream_t to run on (NULL = legacy stream); r: host
+ * pointer, written after the stream has been synchronised.
+ * Its scratch is a file-scope __device__ array of 8 KB (512 blocks x 2
+ * partial sums + 2 totals) that every GPU loading the library keeps until the
+ * process exits; n is limited to [1, 2^30] (LBMFVM_ERR_ARG beyond).  The first
+ * call on a device looks up the array's device address with
+ * cudaGetSymbolAddress (with that device current), so make that first call
+ * before any stream capture.  Every call shares the array: calls that overlap
+ * on the GPU (on different streams, or from several host threads) race and
+ * must be serialised by the caller.  Calls no cudaMalloc, cudaFree or other
+ * allocating routine.  Returns LBMFVM_ERR_DIVERGED if a sum is not finite. */
+int lbmfvm_residual_noalloc(const double *u, const double *v, const double *u_prev, const double *v_prev,
+                            const uint8_t *select, int64_t n, void *stream, double *r);
+
 /* Release the handle and any memory the library allocated.  NULL is a no-op. */
 void lbmfvm_destroy(lbmfvm_t *h);
 

@@ -41,8 +41,8 @@ PRECISIONS = {"f64": LBMFVM_F64, "f32": LBMFVM_F32, "f16": LBMFVM_F16, "bf16": L
 EXPORTS = (
     "lbmfvm_opts_default", "lbmfvm_workspace_bytes", "lbmfvm_create", "lbmfvm_create_lattice",
     "lbmfvm_set_state", "lbmfvm_step", "lbmfvm_inject_stall", "lbmfvm_step_count", "lbmfvm_fields", "lbmfvm_fields_f32",
-    "lbmfvm_nusselt", "lbmfvm_residual", "lbmfvm_run_to_steady", "lbmfvm_params", "lbmfvm_destroy",
-    "lbmfvm_last_error",
+    "lbmfvm_nusselt", "lbmfvm_residual", "lbmfvm_run_to_steady", "lbmfvm_params", "lbmfvm_residual_noalloc",
+    "lbmfvm_destroy", "lbmfvm_last_error",
 )
 
 
@@ -96,6 +96,7 @@ def lib() -> ctypes.CDLL:
                 "lbmfvm_residual": (ctypes.c_int, [vp, dp]),
                 "lbmfvm_run_to_steady": (ctypes.c_int, [vp, d, i64, i64, i64p, dp]),
                 "lbmfvm_params": (ctypes.c_int, [vp, dp, dp, dp, dp]),
+                "lbmfvm_residual_noalloc": (ctypes.c_int, [vp, vp, vp, vp, vp, i64, vp, dp]),
                 "lbmfvm_destroy": (None, [vp]),
                 "lbmfvm_last_error": (ctypes.c_char_p, [vp]),
             }
@@ -211,6 +212,15 @@ def lbmfvm_params(h):
     out = [ctypes.c_double() for _ in range(4)]
     _check(lib().lbmfvm_params(h, *[ctypes.byref(x) for x in out]), h)
     return tuple(x.value for x in out)
+
+
+def lbmfvm_residual_noalloc(u, v, u_prev, v_prev, select=None, n=None, stream=None) -> float:
+    """Residual of lbmfvm_residual on caller device arrays, without allocation."""
+    r = ctypes.c_double()
+    n = int(u.numel() if n is None else n)
+    _check(lib().lbmfvm_residual_noalloc(_addr(u), _addr(v), _addr(u_prev), _addr(v_prev), _addr(select), n,
+                                         None if stream is None else ctypes.c_void_p(stream), ctypes.byref(r)))
+    return r.value
 
 
 def lbmfvm_destroy(h):

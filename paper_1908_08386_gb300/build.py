@@ -16,7 +16,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "liblbmfvm.so")
-SOURCES = [os.path.join(CSRC, "lbmfvm.cu")]
+SOURCES = [os.path.join(CSRC, "lbmfvm.cu"), os.path.join(CSRC, "residual_noalloc.cu")]
 DEPS = SOURCES + [os.path.join(CSRC, "kernels.cuh"), os.path.join(INCLUDE, "lbmfvm.h")]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 

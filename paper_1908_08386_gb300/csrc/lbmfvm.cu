@@ -178,6 +178,12 @@ std::vector<uint8_t> classify(const lbmfvm_grid_t &g, const uint8_t *mask, int p
 
 }  // namespace
 
+namespace lbmfvm_internal {
+// Record a failure message for lbmfvm_last_error(NULL) from another
+// translation unit of the library.
+int fail_thread_msg(int code, const char *msg) { return fail_thread(code, "%s", msg); }
+}  // namespace lbmfvm_internal
+
 struct lbmfvm {
     lbmfvm_grid_t grid;
     int prec;
