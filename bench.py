@@ -273,13 +273,6 @@ def run_ours(args):
     achieved = bytes_per_launch / launch_s / 1e9
     peak, peak_kind = measured_peak()
     traffic = NCU_TRAFFIC.get((args.store, args.size, kernel_hash()))
-    if traffic is None and args.store != "f64":
-        # The capture is of the 4096^2 case (1024^2 fits in L2, where DRAM
-        # counters say nothing about the kernel); per-node traffic scales with
-        # the node count.
-        ref = NCU_TRAFFIC.get((args.store, 4096, kernel_hash()))
-        if ref is not None:
-            traffic = ref * n_nodes / (4096 * 4096)
 
     # End to end through the C-ABI with host buffers: each step uploads the
     # initial (u, v, T) from pinned host memory, runs the chunk, reads back the
