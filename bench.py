@@ -114,34 +114,21 @@ class ClockSampler:
 
 
 def dist_setup(n_gpus: int):
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    if world > 1:
-        import torch
-        import torch.distributed as dist
+    from paper_1908_08386_gb300 import replicas
 
-        local = int(os.environ.get("LOCAL_RANK", "0"))
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
-        return dist.get_rank(), world, local
-    return 0, 1, 0
+    return replicas.init("nccl")
 
 
 def barrier(world):
-    if world > 1:
-        import torch.distributed as dist
+    from paper_1908_08386_gb300 import replicas
 
-        dist.barrier()
+    replicas.barrier(world)
 
 
 def max_over_ranks(x: float, world: int) -> float:
-    if world == 1:
-        return x
-    import torch
-    import torch.distributed as dist
+    from paper_1908_08386_gb300 import replicas
 
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
+    return replicas.max_over_ranks(x, world, "cuda")
 
 
 def oracle_mlups(n: int, seconds: float, chunk: int = 2):
@@ -255,7 +242,9 @@ def run_ours(args):
     wall_s = time.perf_counter() - t_wall0
     clocks = sampler.stop() if sampler else None
     total_ms = max_over_ranks(total_ms, world)
-    value = world * n_nodes * args.chunk * args.steps / (total_ms * 1e-3) / 1e6
+    from paper_1908_08386_gb300 import replicas
+
+    value = replicas.whole_job_rate(n_nodes * args.chunk * args.steps, world, total_ms * 1e-3) / 1e6
 
     # Dominant kernel: step_kernel.  Average launch duration over a run of
     # back-to-back launches (graph replays) on the same stream.
