@@ -222,6 +222,44 @@ int lbmfvm_params(const lbmfvm_t *h, double *nu, double *alpha, double *gbeta, d
 int lbmfvm_residual_noalloc(const double *u, const double *v, const double *u_prev, const double *v_prev,
                             const uint8_t *select, int64_t n, void *stream, double *r);
 
+/* ---- Batches: many cavities advanced by one persistent launch per step ----
+ * The cavities (each with its own size, obstacle mask, Ra, Pr and Ma) are
+ * packed into one grid, each in its own slot; every step is one launch of the
+ * TMA kernel over the tiles of the cavities still active, each tile with its
+ * cavity's lattice parameters.  Cavities converge independently: once a
+ * cavity's residual drops below the tolerance of lbmfvm_batch_run it leaves
+ * the launch and keeps its state.  F32, F16 or BF16 storage, walls on every
+ * side; the library allocates the memory (opts->workspace must be NULL); the
+ * other options apply to the whole batch. */
+typedef struct lbmfvm_batch lbmfvm_batch_t;
+
+/* n cavities: grids[i], masks[i] (ny*nx bytes, 1 = solid; masks or masks[i]
+ * may be NULL), Ra[i], Pr[i], Ma[i] with the parameter rules and limits of
+ * lbmfvm_create.  Every cavity starts at rest with T = grids[i].t_init. */
+int lbmfvm_batch_create(int32_t n, const lbmfvm_grid_t *grids, const uint8_t *const *masks, const double *Ra,
+                        const double *Pr, const double *Ma, const lbmfvm_opts_t *opts, lbmfvm_batch_t **out);
+/* lbmfvm_set_state for cavity i (which becomes active again). */
+int lbmfvm_batch_set_state(lbmfvm_batch_t *b, int32_t i, const float *u, const float *v, const float *T);
+/* n steps of every active cavity. */
+int lbmfvm_batch_step(lbmfvm_batch_t *b, int64_t n);
+/* Residual of lbmfvm_residual for every active cavity (snapshots advance);
+ * inactive cavities report their last value.  r: n doubles, host. */
+int lbmfvm_batch_residuals(lbmfvm_batch_t *b, double *r);
+/* Step in chunks of check_every until every cavity's residual is below tol
+ * (converged cavities leave the launch) or max_steps steps were taken.
+ * steps_out, r_out: n entries each (host, may be NULL): steps taken by each
+ * cavity since its set_state and its last residual. */
+int lbmfvm_batch_run(lbmfvm_batch_t *b, double tol, int64_t check_every, int64_t max_steps, int64_t *steps_out,
+                     double *r_out);
+/* lbmfvm_fields and lbmfvm_nusselt for cavity i. */
+int lbmfvm_batch_fields(lbmfvm_batch_t *b, int32_t i, double *rho, double *u, double *v, double *T);
+int lbmfvm_batch_nusselt(lbmfvm_batch_t *b, int32_t i, double *mean_hot, double *local_hot, double *mean_cold);
+/* Steps since set_state, whether cavity i is still stepped, and its lattice
+ * parameters nu, alpha, gbeta, tau (params: 4 doubles or NULL). */
+int lbmfvm_batch_info(const lbmfvm_batch_t *b, int32_t i, int64_t *steps, int32_t *active, double *params);
+void lbmfvm_batch_destroy(lbmfvm_batch_t *b);
+const char *lbmfvm_batch_last_error(const lbmfvm_batch_t *b);
+
 /* Release the handle and any memory the library allocated.  NULL is a no-op. */
 void lbmfvm_destroy(lbmfvm_t *h);
 

@@ -42,7 +42,9 @@ EXPORTS = (
     "lbmfvm_opts_default", "lbmfvm_workspace_bytes", "lbmfvm_create", "lbmfvm_create_lattice",
     "lbmfvm_set_state", "lbmfvm_step", "lbmfvm_inject_stall", "lbmfvm_step_count", "lbmfvm_fields", "lbmfvm_fields_f32",
     "lbmfvm_nusselt", "lbmfvm_residual", "lbmfvm_run_to_steady", "lbmfvm_params", "lbmfvm_residual_noalloc",
-    "lbmfvm_destroy", "lbmfvm_last_error",
+    "lbmfvm_destroy", "lbmfvm_last_error", "lbmfvm_batch_create", "lbmfvm_batch_set_state", "lbmfvm_batch_step",
+    "lbmfvm_batch_residuals", "lbmfvm_batch_run", "lbmfvm_batch_fields", "lbmfvm_batch_nusselt", "lbmfvm_batch_info",
+    "lbmfvm_batch_destroy", "lbmfvm_batch_last_error",
 )
 
 
@@ -99,6 +101,16 @@ def lib() -> ctypes.CDLL:
                 "lbmfvm_residual_noalloc": (ctypes.c_int, [vp, vp, vp, vp, vp, i64, vp, dp]),
                 "lbmfvm_destroy": (None, [vp]),
                 "lbmfvm_last_error": (ctypes.c_char_p, [vp]),
+                "lbmfvm_batch_create": (ctypes.c_int, [i32, G, vp, dp, dp, dp, O, pp]),
+                "lbmfvm_batch_set_state": (ctypes.c_int, [vp, i32, vp, vp, vp]),
+                "lbmfvm_batch_step": (ctypes.c_int, [vp, i64]),
+                "lbmfvm_batch_residuals": (ctypes.c_int, [vp, vp]),
+                "lbmfvm_batch_run": (ctypes.c_int, [vp, d, i64, i64, vp, vp]),
+                "lbmfvm_batch_fields": (ctypes.c_int, [vp, i32, vp, vp, vp, vp]),
+                "lbmfvm_batch_nusselt": (ctypes.c_int, [vp, i32, dp, vp, dp]),
+                "lbmfvm_batch_info": (ctypes.c_int, [vp, i32, i64p, ctypes.POINTER(i32), vp]),
+                "lbmfvm_batch_destroy": (None, [vp]),
+                "lbmfvm_batch_last_error": (ctypes.c_char_p, [vp]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -313,3 +325,93 @@ class Cavity:
 
     def run_to_steady(self, tol=1e-8, check_every=1000, max_steps=10**8):
         return lbmfvm_run_to_steady(self.h, tol, check_every, max_steps)
+
+
+def _bcheck(code: int, b):
+    if code != LBMFVM_OK:
+        msg = lib().lbmfvm_batch_last_error(b)
+        raise LbmfvmError(code, msg.decode() if msg else "")
+
+
+class Batch:
+    """Many cavities advanced together by one persistent launch per step.
+
+    ``cases``: sequence of objects with ``nx, ny, Ra, Pr, Ma`` and optional
+    ``mask`` (ny x nx, 1 = solid) and ``t_init`` attributes (for example
+    ``workloads.CavityCase``).  The library allocates the memory; work runs on
+    PyTorch's current stream.
+    """
+
+    def __init__(self, cases, store="f32", tma_config=1, device=None):
+        import torch
+
+        self.n = len(cases)
+        self.shapes = [(int(c.ny), int(c.nx)) for c in cases]
+        grids = (lbmfvm_grid_t * self.n)()
+        for k, c in enumerate(cases):
+            grids[k] = make_grid(c.nx, c.ny, t_init=getattr(c, "t_init", 0.5))
+        self._masks = [None if getattr(c, "mask", None) is None else
+                       np.ascontiguousarray(c.mask, dtype=np.uint8).reshape(c.ny, c.nx) for c in cases]
+        mptrs = (ctypes.c_void_p * self.n)(*[None if m is None else m.ctypes.data for m in self._masks])
+        arr = lambda xs: (ctypes.c_double * self.n)(*[float(x) for x in xs])
+        ra, pr, ma = arr([c.Ra for c in cases]), arr([c.Pr for c in cases]), arr([c.Ma for c in cases])
+        self.opts = lbmfvm_opts_default()
+        self.opts.store = PRECISIONS[store] if isinstance(store, str) else int(store)
+        self.opts.tma_config = int(tma_config)
+        dev = torch.device("cuda" if device is None else device)
+        self.opts.cuda_stream = torch.cuda.current_stream(dev).cuda_stream
+        self.b = ctypes.c_void_p()
+        with torch.cuda.device(dev):
+            _bcheck(lib().lbmfvm_batch_create(self.n, grids, ctypes.cast(mptrs, ctypes.c_void_p), ra, pr, ma,
+                                              ctypes.byref(self.opts), ctypes.byref(self.b)), None)
+
+    def close(self):
+        if getattr(self, "b", None):
+            lib().lbmfvm_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_state(self, i, u=None, v=None, T=None):
+        ny, nx = self.shapes[i]
+        conv = lambda a: None if a is None else np.ascontiguousarray(a, dtype=np.float32).reshape(ny, nx)
+        u, v, T = conv(u), conv(v), conv(T)
+        _bcheck(lib().lbmfvm_batch_set_state(self.b, int(i), _addr(u), _addr(v), _addr(T)), self.b)
+
+    def step(self, n=1):
+        _bcheck(lib().lbmfvm_batch_step(self.b, int(n)), self.b)
+
+    def residuals(self):
+        r = np.empty(self.n)
+        _bcheck(lib().lbmfvm_batch_residuals(self.b, _addr(r)), self.b)
+        return r
+
+    def run(self, tol=1e-8, check_every=1000, max_steps=10**8):
+        steps = np.empty(self.n, dtype=np.int64)
+        r = np.empty(self.n)
+        _bcheck(lib().lbmfvm_batch_run(self.b, float(tol), int(check_every), int(max_steps), _addr(steps), _addr(r)),
+                self.b)
+        return steps, r
+
+    def fields(self, i):
+        shp = self.shapes[i]
+        rho, u, v, T = (np.empty(shp) for _ in range(4))
+        _bcheck(lib().lbmfvm_batch_fields(self.b, int(i), _addr(rho), _addr(u), _addr(v), _addr(T)), self.b)
+        return rho, u, v, T
+
+    def nusselt(self, i):
+        loc = np.empty(self.shapes[i][0])
+        mh, mc = ctypes.c_double(), ctypes.c_double()
+        _bcheck(lib().lbmfvm_batch_nusselt(self.b, int(i), ctypes.byref(mh), _addr(loc), ctypes.byref(mc)), self.b)
+        return mh.value, loc, mc.value
+
+    def info(self, i):
+        steps, active = ctypes.c_int64(), ctypes.c_int32()
+        params = np.empty(4)
+        _bcheck(lib().lbmfvm_batch_info(self.b, int(i), ctypes.byref(steps), ctypes.byref(active), _addr(params)),
+                self.b)
+        return steps.value, bool(active.value), tuple(params)

@@ -101,6 +101,25 @@ struct StepArgs {
     int stall;               // test hook: block 0 skips its first staged load
 };
 
+// One cavity of the TMA path: its rectangle in the (possibly multi-cavity)
+// node arrays, which starts on a tile corner, and its lattice parameters.
+struct CavityDesc {
+    int x0, y0, nx, ny;
+    float omega, alpha, gbeta, t_ref, fx, fy;
+    float wall_u[4], wall_v[4];  // box-wall velocity per side W, E, S, N
+};
+
+// One tile of the TMA path: what a block needs to know about it.  A tile
+// holds nodes of one cavity only (plus unused padding beyond its rectangle).
+// The host writes the list; the issuing thread copies a tile's header next
+// to its stage with the same bulk-copy barrier as the tile's data.
+struct TileHeader {
+    int x0, y0, ox, oy, nx, ny, cav, pad;  // origin; origin relative to the cavity; cavity size
+    float omega, alpha, gbeta, t_ref, fx, fy, pad1, pad2;
+};
+static_assert(sizeof(TileHeader) == 64, "tile headers are 64-byte bulk copies");
+
+
 // ---------------------------------------------------------------------------
 // Arithmetic shared by both step kernels and the export kernels.
 // ---------------------------------------------------------------------------
@@ -403,6 +422,14 @@ __device__ __forceinline__ void load_3d(void *dst, const CUtensorMap *map, uint6
         : "memory");
 }
 
+// Untiled bulk copy (16-byte aligned addresses, size a multiple of 16).
+__device__ __forceinline__ void load_bytes(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+
 __device__ __forceinline__ void load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y) {
     asm volatile(
         "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
@@ -444,7 +471,8 @@ struct TmaTile {
     static constexpr uint32_t RING_OFF = STAGES * STAGE_BYTES;
     static constexpr uint32_t RING_BYTES = align128(2u * RH * RW * 4u);  // u, v of tile + ring
     static constexpr uint32_t BAR_OFF = RING_OFF + 2u * RING_BYTES;      // two ring buffers
-    static constexpr uint32_t SMEM_BYTES = BAR_OFF + 8u * STAGES + 16u;
+    static constexpr uint32_t HDR_OFF = BAR_OFF + align128(8u * STAGES + 16u);
+    static constexpr uint32_t SMEM_BYTES = HDR_OFF + STAGES * 64u;
     static_assert(SMEM_BYTES <= 232448u, "tile configuration exceeds 227 KB of shared memory");
     static_assert(OT_OFF + OT_BYTES <= F_BYTES, "results must fit in the staged population bytes");
     static_assert((FW * sizeof(S)) % 16 == 0 && (TWD * 4) % 16 == 0 && CWD % 16 == 0 && (TW * sizeof(S)) % 16 == 0,
@@ -493,7 +521,8 @@ __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wa
 // tells the host.
 template <class S, class G>
 __global__ void __launch_bounds__(G::THREADS, G::MINB)
-    step_tma_kernel(const StepArgs<S> a, const __grid_constant__ CUtensorMap map_f,
+    step_tma_kernel(const StepArgs<S> a, const CavityDesc *__restrict__ cavs, const TileHeader *__restrict__ tiles,
+                    const int *__restrict__ ntiles_p, const __grid_constant__ CUtensorMap map_f,
                     const __grid_constant__ CUtensorMap map_T, const __grid_constant__ CUtensorMap map_c,
                     const __grid_constant__ CUtensorMap map_f_out, const __grid_constant__ CUtensorMap map_T_out) {
     using C = float;
@@ -503,31 +532,43 @@ __global__ void __launch_bounds__(G::THREADS, G::MINB)
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + G::BAR_OFF);
     int *abort_flag = reinterpret_cast<int *>(smem + G::BAR_OFF + 8 * G::STAGES);
+    TileHeader *hdrs = reinterpret_cast<TileHeader *>(smem + G::HDR_OFF);
 
     const int tid = threadIdx.x;
-    const int ntx = (a.nx + TW - 1) / TW, nty = (a.ny + TH - 1) / TH;
-    const int ntiles = ntx * nty;
+    const int ntiles = *ntiles_p;
     const int my_count = (int)blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
-    auto tile_xy = [&](int k, int &x0, int &y0) {
-        const int t = (int)blockIdx.x + k * (int)gridDim.x;
-        const int ty = t / ntx;
-        x0 = (t - ty * ntx) * TW;
-        y0 = ty * TH;
-    };
     auto stage = [&](int k) { return smem + (k % G::STAGES) * G::STAGE_BYTES; };
-    auto issue = [&](int k) {
+    // Origin of the k-th tile of this block (the issuing thread loads it one
+    // issue ahead); the rest of the header travels with the tile's data.
+    auto origin = [&](int k) {
+        int2 o = make_int2(0, 0);
+        if (k < my_count) {
+            const TileHeader *t = tiles + (int)blockIdx.x + k * (int)gridDim.x;
+            o = make_int2(t->x0, t->y0);
+        }
+        return o;
+    };
+    // A tile origin off the 16-node grid would give a TMA box an unaligned
+    // x coordinate; such a tile is never loaded (its wait then runs out and
+    // the block leaves through the abort path with the status word set).
+    auto tile_ok = [&](int x0, int y0) { return (x0 & 15) == 0 && x0 >= 0 && y0 >= 0; };
+    auto issue = [&](int k, int2 o) {
         const int s = k % G::STAGES;
-        int x0, y0;
-        tile_xy(k, x0, y0);
+        const int x0 = o.x, y0 = o.y;
+        if (!tile_ok(x0, y0)) {
+            atomicOr(a.err, kErrTimeout);
+            return;
+        }
         unsigned char *stg = stage(k);
-        tma::mbar_arrive_expect_tx(&bars[s], G::TX_BYTES);
+        tma::mbar_arrive_expect_tx(&bars[s], G::TX_BYTES + (uint32_t)sizeof(TileHeader));
+        tma::load_bytes(&hdrs[s], tiles + (int)blockIdx.x + k * (int)gridDim.x, sizeof(TileHeader), &bars[s]);
         tma::load_3d(stg + G::F_OFF, &map_f, &bars[s], x0 - XOFF, y0 - 3, 0);
         tma::load_2d(stg + G::T_OFF, &map_T, &bars[s], x0 - 4, y0 - 1);
         tma::load_2d(stg + G::C_OFF, &map_c, &bars[s], x0 - 16, y0 - 1);
     };
     auto store_tile = [&](int k) {
-        int x0, y0;
-        tile_xy(k, x0, y0);
+        const int x0 = hdrs[k % G::STAGES].x0, y0 = hdrs[k % G::STAGES].y0;
+        if (!tile_ok(x0, y0)) return;
         unsigned char *stg = stage(k);
         tma::fence_proxy_async();
         tma::store_3d(&map_f_out, stg + G::F_OFF, x0, y0, 0);
@@ -541,21 +582,27 @@ __global__ void __launch_bounds__(G::THREADS, G::MINB)
         tma::fence_mbar_init();
     }
     __syncthreads();
-    if (tid == 0)
+    int2 pre = make_int2(0, 0);  // thread 0: origin of the next tile to issue
+    if (tid == 0) {
         for (int k = 0; k < G::STAGES && k < my_count; k++)
-            if (!(a.stall && blockIdx.x == 0 && k == 0)) issue(k);
-
-    const C alpha = a.alpha, omega = a.omega, gbeta = a.gbeta, t_ref = a.t_ref, fx = a.fx, fy = a.fy;
+            if (!(a.stall && blockIdx.x == 0 && k == 0)) issue(k, origin(k));
+        pre = origin(G::STAGES);
+    }
 
     for (int k = 0; k < my_count; k++) {
         unsigned char *stg = stage(k);
-        if (!tma::mbar_wait_bounded(&bars[k % G::STAGES], (uint32_t)(k / G::STAGES) & 1u, kWaitLimitNs)) {
+        const bool landed = tma::mbar_wait_bounded(&bars[k % G::STAGES], (uint32_t)(k / G::STAGES) & 1u, kWaitLimitNs);
+        if (!landed) {
             atomicOr(abort_flag, 1);
             atomicOr(a.err, kErrTimeout);
         }
-
-        int x0, y0;
-        tile_xy(k, x0, y0);
+        // a stage that never landed has no header: use a harmless one (the
+        // block leaves at the next barrier)
+        const TileHeader hd = landed ? hdrs[k % G::STAGES] : TileHeader{};
+        // node (lx, ly) of the tile sits at (ox + lx, oy + ly) of its cavity
+        const int ox = hd.ox, oy = hd.oy, cv_nx = hd.nx, cv_ny = hd.ny;
+        const CavityDesc *cvp = cavs + hd.cav;
+        const C alpha = hd.alpha, omega = hd.omega, gbeta = hd.gbeta, t_ref = hd.t_ref, fx = hd.fx, fy = hd.fy;
         const S *F = reinterpret_cast<const S *>(stg + G::F_OFF);
         const float *TT = reinterpret_cast<const float *>(stg + G::T_OFF);
         const uint8_t *CC = reinterpret_cast<const uint8_t *>(stg + G::C_OFF);
@@ -578,8 +625,14 @@ __global__ void __launch_bounds__(G::THREADS, G::MINB)
                 const int d = partner_dir(c);
                 pull(lx + cx_rt(d), ly + cy_rt(d), g);
                 moments<C>(g, drho, ux, uy);
-                C uw, vw;
-                wall_velocity<S>(a, x0 + lx, y0 + ly, c, uw, vw);
+                C uw = C(0), vw = C(0);
+                if ((c >> 6) != TH_OBSTACLE) {
+                    // box walls: vertical sides own the corners
+                    const int cx = ox + lx, cy = oy + ly;
+                    const int side = cx == 0 ? 0 : (cx == cv_nx - 1 ? 1 : (cy == 0 ? 2 : 3));
+                    uw = cvp->wall_u[side];
+                    vw = cvp->wall_v[side];
+                }
                 nee<C>(g, drho, ux, uy, uw, vw);
             } else {
 #pragma unroll
@@ -634,7 +687,7 @@ __global__ void __launch_bounds__(G::THREADS, G::MINB)
         for (int j = 0; j < NPT; j++) {
             const int i = tid + j * G::THREADS;
             const int ly = i / TW, lx = i - ly * TW;
-            const int x = x0 + lx, y = y0 + ly;
+            const int cx = ox + lx, cy = oy + ly;  // position in the cavity
             const uint8_t c = cc[j];
             const int t = tidx(lx, ly);
             const C TP = TT[t];
@@ -649,13 +702,17 @@ __global__ void __launch_bounds__(G::THREADS, G::MINB)
             const int th = c >> 6;
             C Tn = TP;
             if (th == TH_FV) {
-                const C ex = (x > 0 ? C(0.5) : C(0)) + (x < a.nx - 1 ? C(0.5) : C(0));
-                const C ey = (y > 0 ? C(0.5) : C(0)) + (y < a.ny - 1 ? C(0.5) : C(0));
-                Tn = fv_update<C>(TP, uu[j], vv[j], ex, ey, alpha,
-                                  fv_open(decode(CC[cidx(lx + 1, ly)])), TT[t + 1], RU[r + 1],
-                                  fv_open(decode(CC[cidx(lx, ly + 1)])), TT[t + G::TWD], RV[r + RW],
-                                  fv_open(decode(CC[cidx(lx - 1, ly)])), TT[t - 1], RU[r - 1],
-                                  fv_open(decode(CC[cidx(lx, ly - 1)])), TT[t - G::TWD], RV[r - RW]);
+                // control volume clipped to the cavity; faces beyond it are closed
+                const bool hw = cx > 0, he = cx < cv_nx - 1, hs = cy > 0, hn = cy < cv_ny - 1;
+                const C ex = (hw ? C(0.5) : C(0)) + (he ? C(0.5) : C(0));
+                const C ey = (hs ? C(0.5) : C(0)) + (hn ? C(0.5) : C(0));
+                // (bitwise &: no short circuit, so no branch around the loads)
+                const bool oE = he & fv_open(decode(CC[cidx(lx + 1, ly)]));
+                const bool oN = hn & fv_open(decode(CC[cidx(lx, ly + 1)]));
+                const bool oW = hw & fv_open(decode(CC[cidx(lx - 1, ly)]));
+                const bool oS = hs & fv_open(decode(CC[cidx(lx, ly - 1)]));
+                Tn = fv_update<C>(TP, uu[j], vv[j], ex, ey, alpha, oE, TT[t + 1], RU[r + 1], oN, TT[t + G::TWD],
+                                  RV[r + RW], oW, TT[t - 1], RU[r - 1], oS, TT[t - G::TWD], RV[r - RW]);
             } else if (th == TH_OBSTACLE) {
                 const int d = partner_dir(c);
                 Tn = TT[tidx(lx + cx_rt(d), ly + cy_rt(d))];
@@ -666,7 +723,8 @@ __global__ void __launch_bounds__(G::THREADS, G::MINB)
         }
         if (tid == 0 && k > 0 && k - 1 + G::STAGES < my_count) {
             tma::bulk_wait_read();  // the results of tile k-1 have left its stage
-            issue(k - 1 + G::STAGES);
+            issue(k - 1 + G::STAGES, pre);
+            pre = origin(k + G::STAGES);
         }
     }
     __syncthreads();

@@ -7,6 +7,7 @@
 // so that long runs can replay a captured CUDA graph of many launches.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -51,10 +52,10 @@ size_t store_size(int prec) {
 struct Layout {
     int pitch;
     long long plane;
-    size_t f[2], T[2], code, snap, stage, red, err, total;
+    size_t f[2], T[2], code, snap, stage, red, err, cav, tiles, cavres, twall, total;
 };
 
-Layout make_layout(const lbmfvm_grid_t &g, int prec) {
+Layout make_layout(const lbmfvm_grid_t &g, int prec, int ncav = 1) {
     Layout L{};
     L.pitch = (int)align_up((size_t)g.nx, 64);
     L.plane = (long long)g.ny * L.pitch;
@@ -74,6 +75,13 @@ Layout make_layout(const lbmfvm_grid_t &g, int prec) {
     L.stage = take(2 * (size_t)g.nx * g.ny * sizeof(double));
     L.red = take((2 * kResidualBlocks + 8 + (size_t)g.ny) * sizeof(double));
     L.err = take(16);
+    // cavity table (one entry) and tile list of the TMA kernel (tiles of at
+    // least 64 x 8 nodes), plus the tile count
+    L.cav = take(ncav * sizeof(CavityDesc));
+    L.cavres = take(ncav * 4 * sizeof(double));  // per cavity: residual sums, Nusselt means
+    L.twall = take(ncav * 4 * sizeof(double));   // per cavity: wall temperatures W, E, S, N
+    const size_t max_tiles = ((size_t)g.nx + 63) / 64 * (((size_t)g.ny + 7) / 8);
+    L.tiles = take((max_tiles + 1) * sizeof(TileHeader));  // count slot, then the headers
     L.total = off;
     return L;
 }
@@ -205,6 +213,11 @@ struct lbmfvm {
     CUtensorMap map_f[2], map_T[2], map_c;
     CUtensorMap map_fo[2], map_To[2];  // output-tile boxes of the TMA tile kernel
     int tma_blocks_per_sm;
+    int ntiles;       // tiles of the TMA kernel
+    int tile_w, tile_h;
+    // Several cavities packed in one grid (batch handles); empty for one cavity.
+    std::vector<CavityDesc> atlas_cavs;
+    std::vector<char> atlas_active;
     char err[512];
 };
 
@@ -280,11 +293,15 @@ void launch_tma_cfg(const lbmfvm_t *h, int cur, cudaStream_t s, bool stall) {
     using G = typename TmaConfig<S, CFG>::G;
     StepArgs<S> a = args_for<S>(h, cur);
     a.stall = stall ? 1 : 0;
-    const int ntiles = ((h->grid.nx + G::TW - 1) / G::TW) * ((h->grid.ny + G::TH - 1) / G::TH);
     const int resident = h->num_sms * h->tma_blocks_per_sm;
-    const int blocks = ntiles < resident ? ntiles : resident;
-    step_tma_kernel<S, G><<<blocks, G::THREADS, G::SMEM_BYTES, s>>>(a, h->map_f[cur], h->map_T[cur], h->map_c,
-                                                                    h->map_fo[cur ^ 1], h->map_To[cur ^ 1]);
+    const int blocks = h->ntiles < resident ? h->ntiles : resident;
+    const CavityDesc *cavs = reinterpret_cast<const CavityDesc *>(h->base + h->L.cav);
+    // the count sits at a fixed address in front of the list, so that a
+    // captured graph reads the current count after the list has changed
+    const int *count = reinterpret_cast<const int *>(h->base + h->L.tiles);
+    const TileHeader *tiles = reinterpret_cast<const TileHeader *>(h->base + h->L.tiles) + 1;
+    step_tma_kernel<S, G><<<blocks, G::THREADS, G::SMEM_BYTES, s>>>(a, cavs, tiles, count, h->map_f[cur], h->map_T[cur],
+                                                                    h->map_c, h->map_fo[cur ^ 1], h->map_To[cur ^ 1]);
 }
 
 template <class S>
@@ -460,6 +477,8 @@ template <> constexpr CUtensorMapDataType tmap_type<__nv_bfloat16>() { return CU
 
 template <class S>
 int encode_maps(lbmfvm_t *h, int fw, int fh, int tw, int th, int cw, int ch);
+int upload_tiles(lbmfvm_t *h, int tw, int th);
+CavityDesc single_cavity_desc(const lbmfvm_t *h);
 
 template <class S, int CFG>
 int setup_tma_cfg(lbmfvm_t *h) {
@@ -479,7 +498,70 @@ int setup_tma_cfg(lbmfvm_t *h) {
     CU(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, G::THREADS, G::SMEM_BYTES));
     if (per_sm < 1) return fail(h, LBMFVM_ERR_CUDA, "TMA tile kernel does not fit on an SM");
     h->tma_blocks_per_sm = per_sm;
+    h->tile_w = G::TW;
+    h->tile_h = G::TH;
+    return upload_tiles(h, G::TW, G::TH);
+}
+
+// Tile list of the TMA kernel (row by row over every active cavity) and the
+// cavity table, uploaded on the handle's stream.
+int upload_tiles(lbmfvm_t *h, int tw, int th) {
+    std::vector<TileHeader> tl;
+    std::vector<CavityDesc> table;
+    if (!h->atlas_cavs.empty()) table = h->atlas_cavs;
+    else table.push_back(single_cavity_desc(h));
+    tl.push_back(TileHeader{});  // the count, read by the kernel, in front of the list
+    for (size_t c = 0; c < table.size(); c++) {
+        if (!h->atlas_cavs.empty() && !h->atlas_active[c]) continue;
+        const CavityDesc &cd = table[c];
+        for (int y0 = cd.y0; y0 < cd.y0 + cd.ny; y0 += th)
+            for (int x0 = cd.x0; x0 < cd.x0 + cd.nx; x0 += tw) {
+                TileHeader t{};
+                t.x0 = x0;
+                t.y0 = y0;
+                t.ox = x0 - cd.x0;
+                t.oy = y0 - cd.y0;
+                t.nx = cd.nx;
+                t.ny = cd.ny;
+                t.cav = (int)c;
+                t.omega = cd.omega;
+                t.alpha = cd.alpha;
+                t.gbeta = cd.gbeta;
+                t.t_ref = cd.t_ref;
+                t.fx = cd.fx;
+                t.fy = cd.fy;
+                tl.push_back(t);
+            }
+    }
+    h->ntiles = (int)tl.size() - 1;
+    tl[0].x0 = h->ntiles;
+    // on the handle's stream, after the workspace has been cleared
+    CU(h, cudaMemcpyAsync(h->base + h->L.tiles, tl.data(), tl.size() * sizeof(TileHeader), cudaMemcpyHostToDevice,
+                          h->s));
+    CU(h, cudaMemcpyAsync(h->base + h->L.cav, table.data(), table.size() * sizeof(CavityDesc),
+                          cudaMemcpyHostToDevice, h->s));
+    CU(h, cudaStreamSynchronize(h->s));
     return LBMFVM_OK;
+}
+
+CavityDesc single_cavity_desc(const lbmfvm_t *h) {
+    CavityDesc cd{};
+    cd.x0 = 0;
+    cd.y0 = 0;
+    cd.nx = h->grid.nx;
+    cd.ny = h->grid.ny;
+    cd.omega = (float)(1.0 / h->tau);
+    cd.alpha = (float)h->alpha;
+    cd.gbeta = (float)h->gbeta;
+    cd.t_ref = (float)h->t_ref;
+    cd.fx = (float)h->force[0];
+    cd.fy = (float)h->force[1];
+    for (int sd = 0; sd < 4; sd++) {
+        const bool moving = h->grid.bc[sd] == LBMFVM_BC_MOVING;
+        cd.wall_u[sd] = (float)(moving && sd >= 2 ? h->grid.u_lid : 0.0);
+        cd.wall_v[sd] = (float)(moving && sd < 2 ? h->grid.u_lid : 0.0);
+    }
+    return cd;
 }
 
 // Tensor maps of both population buffers (box fw x fh x 9), both
@@ -550,8 +632,15 @@ int check_device_status(lbmfvm_t *h) {
     return LBMFVM_OK;
 }
 
+// Several cavities packed in one grid: their descriptors (rectangles starting
+// on 128 x 16 slot corners, lattice parameters) and the packed node codes.
+struct AtlasSpec {
+    std::vector<CavityDesc> cavs;
+    std::vector<uint8_t> codes;  // stored codes, ny * pitch of the packed grid
+};
+
 int create_impl(const lbmfvm_grid_t *grid, const uint8_t *mask, double nu, double alpha, double gbeta,
-                const double *force, const lbmfvm_opts_t *opts_in, lbmfvm_t **out) {
+                const double *force, const lbmfvm_opts_t *opts_in, lbmfvm_t **out, const AtlasSpec *atlas = nullptr) {
     if (!out) return fail_thread(LBMFVM_ERR_ARG, "out is NULL");
     *out = nullptr;
     if (int r = check_grid(grid)) return r;
@@ -576,7 +665,8 @@ int create_impl(const lbmfvm_grid_t *grid, const uint8_t *mask, double nu, doubl
     if (tau < 0.51) return fail_thread(LBMFVM_ERR_UNSTABLE, "tau = %.6g < 0.51", tau);
     if (alpha > 0.25)
         return fail_thread(LBMFVM_ERR_UNSTABLE, "alpha = %.6g exceeds the explicit diffusion limit 0.25", alpha);
-    const Layout L = make_layout(*grid, opts.store);
+    if (atlas && !tma_ok) return fail_thread(LBMFVM_ERR_ARG, "a batch needs 32- or 16-bit storage");
+    const Layout L = make_layout(*grid, opts.store, atlas ? (int)atlas->cavs.size() : 1);
     if (opts.workspace && opts.workspace_bytes < L.total)
         return fail_thread(LBMFVM_ERR_NOMEM, "workspace of %zu bytes is smaller than the %zu needed",
                            opts.workspace_bytes, L.total);
@@ -626,15 +716,21 @@ int create_impl(const lbmfvm_grid_t *grid, const uint8_t *mask, double nu, doubl
         }
         h->owns = true;
     }
-    if (int r = setup_kernels(h)) return bail(r);
-    std::vector<uint8_t> code = classify(*grid, mask, L.pitch);
+    std::vector<uint8_t> code = atlas ? atlas->codes : classify(*grid, mask, L.pitch);
+    if (atlas) {
+        h->atlas_cavs = atlas->cavs;
+        h->atlas_active.assign(atlas->cavs.size(), 1);
+        h->use_tma = true;
+    }
     if (join_in(h)) return bail(LBMFVM_ERR_CUDA);
     if (cudaMemsetAsync(h->base, 0, L.total, h->s) != cudaSuccess ||
         cudaMemcpyAsync(h->base + L.code, code.data(), code.size(), cudaMemcpyHostToDevice, h->s) != cudaSuccess) {
         fail(h, LBMFVM_ERR_CUDA, "device initialisation failed");
         return bail(LBMFVM_ERR_CUDA);
     }
-    if (int r = set_state_impl(h, nullptr, nullptr, nullptr)) return bail(r);
+    if (int r = setup_kernels(h)) return bail(r);
+    if (!atlas)
+        if (int r = set_state_impl(h, nullptr, nullptr, nullptr)) return bail(r);
     *out = h;
     return LBMFVM_OK;
 }
@@ -845,3 +941,5 @@ void lbmfvm_destroy(lbmfvm_t *h) {
 const char *lbmfvm_last_error(const lbmfvm_t *h) { return h ? h->err : g_err; }
 
 }  // extern "C"
+
+#include "batch.inl"

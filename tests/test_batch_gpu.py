@@ -1,0 +1,121 @@
+"""Batches: many cavities in one persistent launch per step (GPU).
+
+A cavity in a batch runs the same kernel and tile decomposition as a
+single-cavity handle, so its fields equal the single run bit for bit; the
+FP64 oracle checks a few cavities directly."""
+
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_1908_08386_gb300 as L
+from paper_1908_08386_gb300 import workloads as WL
+
+pytestmark = pytest.mark.gpu
+
+MA = 0.1 * math.sqrt(3.0)
+
+
+def small_cases():
+    """Uneven cavities: sizes that are and are not tile multiples, aspect 2,
+    obstacles, different Ra and Pr."""
+    cases = [
+        WL.CavityCase(64, 64, 1e4, 0.71, MA, name="a"),
+        WL.CavityCase(97, 49, 3e4, 7.0, MA, name="b"),
+        WL.CavityCase(129, 65, 1e5, 0.71, MA, name="c"),
+        WL.CavityCase(40, 40, 2e3, 0.71, 0.05 * math.sqrt(3.0), name="d"),
+        WL.CavityCase(150, 72, 1e5, 0.71, MA, name="e"),
+    ]
+    cases[2].mask = WL.rasterize([("circle", 60.0, 30.0, 14.0)], 129, 65)
+    cases[4].mask = WL.rasterize([("rect", 40.0, 36.0, 12.0, 20.0), ("circle", 110.0, 30.0, 10.0)], 150, 72)
+    return cases
+
+
+@pytest.mark.parametrize("store", ["f32", "f16"])
+def test_batch_equals_single_cavity_runs_bitwise(store):
+    cases = small_cases()
+    b = L.Batch(cases, store=store)
+    b.step(300)
+    for i, c in enumerate(cases):
+        single = L.Cavity(c.nx, c.ny, Ra=c.Ra, Pr=c.Pr, Ma=c.Ma, mask=c.mask, store=store, kernel="tma")
+        single.step(300)
+        got = np.stack(b.fields(i))
+        want = np.stack(single.fields())
+        assert np.array_equal(got, want), (c.name, np.abs(got - want).max())
+        assert b.info(i)[0] == 300
+
+
+def test_batch_cavities_match_the_oracle():
+    cases = small_cases()
+    b = L.Batch(cases, store="f32")
+    b.step(800)
+    for i in (1, 2, 4):
+        c = cases[i]
+        o = oracle.Oracle.from_groups(c.nx, c.ny, c.Ra, c.Pr, c.Ma, mask=c.mask)
+        o.step(800)
+        _, ug, vg, Tg = b.fields(i)
+        _, uo, vo, To = o.fields()
+        u_scale = c.Ma / math.sqrt(3.0)
+        assert max(np.abs(ug - uo).max(), np.abs(vg - vo).max()) / u_scale <= 1e-5
+        assert np.abs(Tg - To).max() <= 1e-5
+        nh_g, loc_g, nc_g = b.nusselt(i)
+        nh_o, loc_o, nc_o, _ = o.nusselt()
+        assert abs(nh_g - nh_o) <= 1e-4 * abs(nh_o) and abs(nc_g - nc_o) <= 1e-4 * abs(nc_o)
+
+
+def test_batch_residuals_match_single_handles():
+    cases = small_cases()[:3]
+    b = L.Batch(cases, store="f32")
+    singles = [L.Cavity(c.nx, c.ny, Ra=c.Ra, Pr=c.Pr, Ma=c.Ma, mask=c.mask, store="f32", kernel="tma") for c in cases]
+    for _ in range(2):
+        b.step(500)
+        rb = b.residuals()
+        for s, r in zip(singles, rb):
+            s.step(500)
+            assert r == pytest.approx(s.residual(), rel=1e-12)
+
+
+def test_converged_cavities_leave_the_launch_and_keep_their_state():
+    # a tiny conductive cavity converges long before a convective one
+    cases = [WL.CavityCase(24, 24, 1e3, 0.71, MA, name="fast"),
+             WL.CavityCase(96, 96, 1e5, 0.71, MA, name="slow")]
+    b = L.Batch(cases, store="f32")
+    steps, r = b.run(tol=1e-6, check_every=500, max_steps=20000)
+    assert r[0] < 1e-6 and not b.info(0)[1]
+    assert steps[0] < steps[1] or r[1] >= 1e-6
+    frozen = np.stack(b.fields(0))
+    b.step(1000)  # only the slow cavity, if still active, moves
+    assert np.array_equal(np.stack(b.fields(0)), frozen)
+    assert b.info(0)[0] == steps[0]
+
+
+def test_set_state_resets_one_cavity_only():
+    cases = small_cases()[:2]
+    b = L.Batch(cases, store="f32")
+    b.step(200)
+    other = np.stack(b.fields(1))
+    rng = np.random.default_rng(3)
+    T0 = rng.random((cases[0].ny, cases[0].nx)).astype(np.float32)
+    b.set_state(0, T=T0)
+    assert b.info(0)[0] == 0 and b.info(1)[0] == 200
+    assert np.array_equal(np.stack(b.fields(1)), other)
+    # the reset cavity now follows a fresh single run from the same state
+    single = L.Cavity(cases[0].nx, cases[0].ny, Ra=cases[0].Ra, Pr=cases[0].Pr, Ma=cases[0].Ma, store="f32",
+                      kernel="tma")
+    single.set_state(T=T0)
+    b.step(100)
+    single.step(100)
+    assert np.array_equal(np.stack(b.fields(0)), np.stack(single.fields()))
+
+
+def test_batch_rejects_what_it_cannot_run():
+    c = WL.CavityCase(64, 64, 1e4, 0.71, MA)
+    with pytest.raises(L.LbmfvmError) as e:
+        L.Batch([c], store="f64")
+    assert e.value.code == L.LBMFVM_ERR_ARG
+    bad = WL.CavityCase(512, 512, 1e3, 0.71, MA)  # alpha above the explicit limit
+    with pytest.raises(L.LbmfvmError) as e:
+        L.Batch([c, bad])
+    assert e.value.code == L.LBMFVM_ERR_UNSTABLE
