@@ -192,10 +192,23 @@ int lbmfvm_nusselt(lbmfvm_t *h, double *mean_hot, double *local_hot, double *mea
 int lbmfvm_residual(lbmfvm_t *h, double *r);
 
 /* Step in chunks of check_every, computing the residual after each chunk,
- * until it falls below tol or max_steps steps were taken.  steps_done and
- * r_final may be NULL. */
+ * until it falls below tol or max_steps steps were taken.  After each check
+ * that does not stop the run, the populations are rescaled so that the fluid
+ * nodes average rho = 1 (this changes neither u nor T; see the batch notes
+ * below).  steps_done and r_final may be NULL. */
 int lbmfvm_run_to_steady(lbmfvm_t *h, double tol, int64_t check_every, int64_t max_steps,
                          int64_t *steps_done, double *r_final);
+
+/* Copy the state of src into dst, converting the storage precision: the
+ * populations (stored as f - w_i in every precision, Eq. 9 weights), the
+ * temperature, the step count and the residual snapshot.  dst keeps its own
+ * lattice parameters and mask; the grids must have the same nx and ny
+ * (LBMFVM_ERR_ARG otherwise) and the caller keeps the masks equal.  The
+ * reduced-precision forms use it to finish a run in FP32 storage once their
+ * residual reaches their storage's floor: the iteration then continues
+ * exactly as an FP32 run from the converted state.  Runs on dst's stream
+ * after src's queued work. */
+int lbmfvm_copy_state(lbmfvm_t *dst, lbmfvm_t *src);
 
 /* Derived lattice parameters: nu, alpha, gbeta, tau (any may be NULL). */
 int lbmfvm_params(const lbmfvm_t *h, double *nu, double *alpha, double *gbeta, double *tau);
@@ -230,7 +243,24 @@ int lbmfvm_residual_noalloc(const double *u, const double *v, const double *u_pr
  * cavity's residual drops below the tolerance of lbmfvm_batch_run it leaves
  * the launch and keeps its state.  F32, F16 or BF16 storage, walls on every
  * side; the library allocates the memory (opts->workspace must be NULL); the
- * other options apply to the whole batch. */
+ * other options apply to the whole batch.
+ * Precision ladder: the rounding of the stored populations puts a floor under
+ * the residual, about 1e-3 for F16, 4e-3 for BF16 and 2e-7 to 2e-6 for F32.
+ * Above its storage precision a batch keeps packed grids in the wider
+ * precisions (F32, then F64), created when first needed.  During
+ * lbmfvm_batch_run a cavity moves one level up (lbmfvm_copy_state's
+ * conversion) when its residual falls below its level's switch value, or when
+ * it is within a factor 100 of that value and has not halved for a number of
+ * checks (lbmfvm_batch_set_polish; defaults: F16 2e-3, BF16 1e-2, 16 checks;
+ * F32 1e-6, 32 checks), and is stepped there until it meets the run's
+ * tolerance.  Each step is one launch per level with active cavities.
+ * lbmfvm_batch_run also rescales the populations of every active cavity after
+ * each residual check so that its fluid nodes average rho = 1: the step is
+ * homogeneous of degree one in f (Eq. 18 with the pressure rho0 cs^2,
+ * non-equilibrium extrapolation walls Eqs. 94, 96), so this changes neither u
+ * nor T, and it undoes the walls' steady mass loss, which would otherwise
+ * inflate the stored f - w_i and the rounding of u with it.
+ * lbmfvm_run_to_steady does the same for a single handle. */
 typedef struct lbmfvm_batch lbmfvm_batch_t;
 
 /* n cavities: grids[i], masks[i] (ny*nx bytes, 1 = solid; masks or masks[i]
@@ -257,6 +287,15 @@ int lbmfvm_batch_nusselt(lbmfvm_batch_t *b, int32_t i, double *mean_hot, double 
 /* Steps since set_state, whether cavity i is still stepped, and its lattice
  * parameters nu, alpha, gbeta, tau (params: 4 doubles or NULL). */
 int lbmfvm_batch_info(const lbmfvm_batch_t *b, int32_t i, int64_t *steps, int32_t *active, double *params);
+/* Ladder switch for cavities stepped in precision prec (a level below the
+ * top of this batch's ladder, LBMFVM_ERR_ARG otherwise): the residual below
+ * which lbmfvm_batch_run moves them one level up, and the number of checks
+ * without halving the residual that also moves them (within a factor 100 of
+ * r_switch).  r_switch <= 0 keeps them at prec; stall_checks <= 0 turns the
+ * second rule off. */
+int lbmfvm_batch_set_polish(lbmfvm_batch_t *b, int32_t prec, double r_switch, int32_t stall_checks);
+/* Storage precision cavity i is currently stepped in (lbmfvm_prec). */
+int lbmfvm_batch_precision(const lbmfvm_batch_t *b, int32_t i, int32_t *prec);
 void lbmfvm_batch_destroy(lbmfvm_batch_t *b);
 const char *lbmfvm_batch_last_error(const lbmfvm_batch_t *b);
 

@@ -85,6 +85,7 @@ def load_library(path: str):
     lib.orc_tau.argtypes = [vp]
     lib.orc_fields.argtypes = [vp, vp, vp, vp, vp]
     lib.orc_get_f.argtypes = [vp, vp]
+    lib.orc_set_f.argtypes = [vp, vp]
     lib.orc_classes.argtypes = [vp, vp, vp, vp]
     lib.orc_nusselt.argtypes = [vp, dp, vp, dp, vp]
     lib.orc_flux_nusselt.argtypes = [vp, vp]
@@ -183,6 +184,10 @@ class Oracle:
         out = np.empty((9, self.ny, self.nx))
         self._lib.orc_get_f(self._h, _ptr(out))
         return out
+
+    def set_f(self, f):
+        f = np.ascontiguousarray(f, dtype=np.float64).reshape(9, self.ny, self.nx)
+        self._lib.orc_set_f(self._h, _ptr(f))
 
     def classes(self):
         shp = (self.ny, self.nx)

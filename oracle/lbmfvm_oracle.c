@@ -448,6 +448,14 @@ void orc_fields(const orc_t *o, double *rho, double *u, double *v, double *T) {
 
 void orc_get_f(const orc_t *o, double *f) { memcpy(f, o->f, sizeof(double) * Q * o->nx * o->ny); }
 
+/* Replace the post-stream populations of the current state (Q planes of
+ * ny*nx, the layout of orc_get_f); T, the step count and the residual
+ * snapshot stay.  For tests of properties of the step as a map of f. */
+void orc_set_f(orc_t *o, const double *f) {
+    memcpy(o->f, f, sizeof(double) * Q * o->nx * o->ny);
+    compute_moments(o);
+}
+
 void orc_classes(const orc_t *o, unsigned char *kind, unsigned char *therm, int *partner) {
     long n = (long)o->nx * o->ny;
     for (long k = 0; k < n; k++) {

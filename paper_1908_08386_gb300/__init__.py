@@ -41,10 +41,10 @@ PRECISIONS = {"f64": LBMFVM_F64, "f32": LBMFVM_F32, "f16": LBMFVM_F16, "bf16": L
 EXPORTS = (
     "lbmfvm_opts_default", "lbmfvm_workspace_bytes", "lbmfvm_create", "lbmfvm_create_lattice",
     "lbmfvm_set_state", "lbmfvm_step", "lbmfvm_inject_stall", "lbmfvm_step_count", "lbmfvm_fields", "lbmfvm_fields_f32",
-    "lbmfvm_nusselt", "lbmfvm_residual", "lbmfvm_run_to_steady", "lbmfvm_params", "lbmfvm_residual_noalloc",
+    "lbmfvm_nusselt", "lbmfvm_residual", "lbmfvm_run_to_steady", "lbmfvm_copy_state", "lbmfvm_params", "lbmfvm_residual_noalloc",
     "lbmfvm_destroy", "lbmfvm_last_error", "lbmfvm_batch_create", "lbmfvm_batch_set_state", "lbmfvm_batch_step",
     "lbmfvm_batch_residuals", "lbmfvm_batch_run", "lbmfvm_batch_fields", "lbmfvm_batch_nusselt", "lbmfvm_batch_info",
-    "lbmfvm_batch_destroy", "lbmfvm_batch_last_error",
+    "lbmfvm_batch_set_polish", "lbmfvm_batch_precision", "lbmfvm_batch_destroy", "lbmfvm_batch_last_error",
 )
 
 
@@ -97,6 +97,7 @@ def lib() -> ctypes.CDLL:
                 "lbmfvm_nusselt": (ctypes.c_int, [vp, dp, vp, dp]),
                 "lbmfvm_residual": (ctypes.c_int, [vp, dp]),
                 "lbmfvm_run_to_steady": (ctypes.c_int, [vp, d, i64, i64, i64p, dp]),
+                "lbmfvm_copy_state": (ctypes.c_int, [vp, vp]),
                 "lbmfvm_params": (ctypes.c_int, [vp, dp, dp, dp, dp]),
                 "lbmfvm_residual_noalloc": (ctypes.c_int, [vp, vp, vp, vp, vp, i64, vp, dp]),
                 "lbmfvm_destroy": (None, [vp]),
@@ -109,6 +110,8 @@ def lib() -> ctypes.CDLL:
                 "lbmfvm_batch_fields": (ctypes.c_int, [vp, i32, vp, vp, vp, vp]),
                 "lbmfvm_batch_nusselt": (ctypes.c_int, [vp, i32, dp, vp, dp]),
                 "lbmfvm_batch_info": (ctypes.c_int, [vp, i32, i64p, ctypes.POINTER(i32), vp]),
+                "lbmfvm_batch_set_polish": (ctypes.c_int, [vp, i32, d, i32]),
+                "lbmfvm_batch_precision": (ctypes.c_int, [vp, i32, ctypes.POINTER(i32)]),
                 "lbmfvm_batch_destroy": (None, [vp]),
                 "lbmfvm_batch_last_error": (ctypes.c_char_p, [vp]),
             }
@@ -220,6 +223,10 @@ def lbmfvm_run_to_steady(h, tol=1e-8, check_every=1000, max_steps=10**8):
     return done.value, r.value
 
 
+def lbmfvm_copy_state(dst, src):
+    _check(lib().lbmfvm_copy_state(dst, src), dst)
+
+
 def lbmfvm_params(h):
     out = [ctypes.c_double() for _ in range(4)]
     _check(lib().lbmfvm_params(h, *[ctypes.byref(x) for x in out]), h)
@@ -326,6 +333,11 @@ class Cavity:
     def run_to_steady(self, tol=1e-8, check_every=1000, max_steps=10**8):
         return lbmfvm_run_to_steady(self.h, tol, check_every, max_steps)
 
+    def copy_state_from(self, other: "Cavity"):
+        """Take ``other``'s state (populations, temperature, step count,
+        residual snapshot), converted to this cavity's storage precision."""
+        lbmfvm_copy_state(self.h, other.h)
+
 
 def _bcheck(code: int, b):
     if code != LBMFVM_OK:
@@ -415,3 +427,16 @@ class Batch:
         _bcheck(lib().lbmfvm_batch_info(self.b, int(i), ctypes.byref(steps), ctypes.byref(active), _addr(params)),
                 self.b)
         return steps.value, bool(active.value), tuple(params)
+
+    def set_polish(self, prec, r_switch, stall_checks=0):
+        """Ladder switch of the cavities stepped in ``prec``: the residual
+        below which ``run`` moves them one precision up (<= 0: never), and the
+        checks without halving that also do (<= 0: off)."""
+        p = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
+        _bcheck(lib().lbmfvm_batch_set_polish(self.b, p, float(r_switch), int(stall_checks)), self.b)
+
+    def precision(self, i):
+        """Storage precision cavity i is stepped in ("f32", "f16" or "bf16")."""
+        p = ctypes.c_int32()
+        _bcheck(lib().lbmfvm_batch_precision(self.b, int(i), ctypes.byref(p)), self.b)
+        return {v: k for k, v in PRECISIONS.items()}[p.value]

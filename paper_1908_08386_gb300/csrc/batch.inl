@@ -9,9 +9,24 @@
 // kernels on a view of the cavity: base pointers moved to the cavity's origin,
 // the packed grid's row pitch and plane stride, the cavity's own sizes.
 // Converged cavities leave the tile list and keep their state where it was.
+//
+// Precision ladder: the rounding of the stored populations puts a floor under
+// the residual (about 1e-3 for 16-bit storage, 1e-7 for FP32).  Above the
+// storage grid the batch keeps packed grids of the wider precisions with the
+// same slots (FP32, then FP64), created when first needed; a cavity whose
+// residual reaches its level's switch value, or stops falling, is converted
+// into the next grid and stepped there from then on.
 
 struct lbmfvm_batch {
-    lbmfvm_t *a = nullptr;  // the packed grid (memory, stream, kernels)
+    lbmfvm_t *a = nullptr;          // the storage grid (memory, stream, kernels); lv[0]
+    lbmfvm_t *lv[3] = {};           // packed grids of the ladder; upper ones created when first needed
+    int prec[3] = {};               // their storage precisions
+    int nlv = 1;                    // levels of the ladder
+    double switch_r[3] = {};        // residual that moves a cavity from level l to l + 1 (0: never)
+    int stall_checks[3] = {};       // checks without halving the residual that also move it (0: never)
+    lbmfvm_grid_t atlas_grid;       // what the upper grids are created from
+    AtlasSpec spec;
+    lbmfvm_opts_t opts;
     struct Cav {
         lbmfvm_grid_t grid;
         int x0, y0;
@@ -19,6 +34,9 @@ struct lbmfvm_batch {
         int64_t steps;    // steps since this cavity's last set_state
         int parity;       // buffer of the state while frozen
         bool active;
+        int level;        // ladder level holding the state
+        double best_r;    // smallest residual at this level, and the checks since it halved
+        int since_best;
         size_t snap_off;  // first node of the cavity's residual snapshot
         double last_r;
     };
@@ -45,12 +63,15 @@ int bcheck(lbmfvm_batch_t *b, int code) {
     return code;
 }
 
-int cav_parity(const lbmfvm_batch_t *b, int i) { return b->cav[i].active ? b->a->parity : b->cav[i].parity; }
+// The packed grid that holds cavity i's state.
+lbmfvm_t *hnd(const lbmfvm_batch_t *b, int i) { return b->lv[b->cav[i].level]; }
+
+int cav_parity(const lbmfvm_batch_t *b, int i) { return b->cav[i].active ? hnd(b, i)->parity : b->cav[i].parity; }
 
 template <class S>
 StepArgs<S> cav_view(const lbmfvm_batch_t *b, int i, int cur) {
     using C = typename Compute<S>::type;
-    StepArgs<S> v = args_for<S>(b->a, cur);
+    StepArgs<S> v = args_for<S>(hnd(b, i), cur);
     const auto &c = b->cav[i];
     const long long off = (long long)c.y0 * v.pitch + c.x0;
     v.fin += off;
@@ -83,7 +104,7 @@ StepArgs<S> cav_read_view(const lbmfvm_batch_t *b, int i, int &direct) {
     StepArgs<S> v = cav_view<S>(b, i, par);
     const auto &c = b->cav[i];
     const long long off = (long long)c.y0 * v.pitch + c.x0;
-    v.fin = reinterpret_cast<const S *>(b->a->base + b->a->L.f[par ^ 1]) + off;
+    v.fin = reinterpret_cast<const S *>(hnd(b, i)->base + hnd(b, i)->L.f[par ^ 1]) + off;
     direct = c.steps == 0;
     return v;
 }
@@ -108,7 +129,7 @@ void launch_cav_init(lbmfvm_batch_t *b, int i, const float *u0, const float *v0,
 
 template <class S>
 void launch_cav_residual(lbmfvm_batch_t *b, int i, int update_only) {
-    lbmfvm_t *h = b->a;
+    lbmfvm_t *h = hnd(b, i);
     int direct;
     StepArgs<S> v = cav_read_view<S>(b, i, direct);
     double *su = reinterpret_cast<double *>(h->base + h->L.snap) + b->cav[i].snap_off;
@@ -117,19 +138,33 @@ void launch_cav_residual(lbmfvm_batch_t *b, int i, int update_only) {
     const int blocks = v.ny < kResidualBlocks ? v.ny : kResidualBlocks;
     residual_kernel<S><<<blocks, 256, 0, h->s>>>(v, direct, su, sv, red, update_only);
     if (!update_only)
-        residual_finish_kernel<<<1, 32, 0, h->s>>>(red, blocks, reinterpret_cast<double *>(h->base + h->L.cavres) + 4 * i);
+        residual_finish_kernel<<<1, 32, 0, h->s>>>(red, blocks,
+                                                   reinterpret_cast<double *>(h->base + h->L.cavres) + kCavRes * i);
 }
 
 template <class S>
 void launch_cav_nusselt(lbmfvm_batch_t *b, int i) {
-    lbmfvm_t *h = b->a;
+    lbmfvm_t *h = hnd(b, i);
     int direct;
     StepArgs<S> v = cav_read_view<S>(b, i, direct);
     const auto &g = b->cav[i].grid;
     double *red = reinterpret_cast<double *>(h->base + h->L.red);
     nusselt_kernel<S><<<1, 256, 0, h->s>>>(v, (double)(g.ny - 1), g.t_wall[LBMFVM_SIDE_W] - g.t_wall[LBMFVM_SIDE_E],
-                                           red + 2 * kResidualBlocks + 8,
-                                           reinterpret_cast<double *>(h->base + h->L.cavres) + 4 * i + 2);
+                                           red + kRedLocal,
+                                           reinterpret_cast<double *>(h->base + h->L.cavres) + kCavRes * i + kCavNu);
+}
+
+template <class S>
+void launch_cav_rescale(lbmfvm_batch_t *b, int i) {
+    lbmfvm_t *h = hnd(b, i);
+    const auto &c = b->cav[i];
+    StepArgs<S> v = cav_view<S>(b, i, cav_parity(b, i));
+    const long long off = (long long)c.y0 * v.pitch + c.x0;
+    S *f0 = reinterpret_cast<S *>(h->base + h->L.f[0]) + off;
+    S *f1 = reinterpret_cast<S *>(h->base + h->L.f[1]) + off;
+    const double *tot = reinterpret_cast<const double *>(h->base + h->L.cavres) + kCavRes * i;
+    dim3 block(32, 8), grid((c.grid.nx + 31) / 32, (c.grid.ny + 7) / 8, 2);
+    rescale_kernel<S><<<grid, block, 0, h->s>>>(v, f0, f1, tot);
 }
 
 template <class S, class O>
@@ -137,12 +172,14 @@ void launch_cav_fields(lbmfvm_batch_t *b, int i, int which, O *o0, O *o1) {
     int direct;
     StepArgs<S> v = cav_read_view<S>(b, i, direct);
     dim3 block(32, 8), grid((v.nx + 31) / 32, (v.ny + 7) / 8);
-    fields_kernel<S, O><<<grid, block, 0, b->a->s>>>(v, direct, which, o0, o1);
+    fields_kernel<S, O><<<grid, block, 0, hnd(b, i)->s>>>(v, direct, which, o0, o1);
 }
 
-#define BDISPATCH(b, FN, ...)                                         \
+// FN<storage type>(...) for the precision of packed grid h.
+#define BDISPATCH(h, FN, ...)                                         \
     do {                                                              \
-        switch ((b)->a->prec) {                                       \
+        switch ((h)->prec) {                                          \
+            case LBMFVM_F64: FN<double>(__VA_ARGS__); break;          \
             case LBMFVM_F32: FN<float>(__VA_ARGS__); break;           \
             case LBMFVM_F16: FN<__half>(__VA_ARGS__); break;          \
             case LBMFVM_BF16: FN<__nv_bfloat16>(__VA_ARGS__); break;  \
@@ -156,16 +193,113 @@ int check_index(lbmfvm_batch_t *b, int32_t i) {
     return LBMFVM_OK;
 }
 
+int bcheck_h(lbmfvm_batch_t *b, lbmfvm_t *h, int code) {
+    if (code != LBMFVM_OK) snprintf(b->err, sizeof(b->err), "%s", h->err);
+    return code;
+}
+
 int set_active(lbmfvm_batch_t *b, int i, bool active) {
     if (b->cav[i].active == active) return LBMFVM_OK;
-    if (!active) b->cav[i].parity = b->a->parity;
+    lbmfvm_t *h = hnd(b, i);
+    if (!active) b->cav[i].parity = h->parity;
     b->cav[i].active = active;
-    b->a->atlas_active[i] = active ? 1 : 0;
-    return bcheck(b, upload_tiles(b->a, b->a->tile_w, b->a->tile_h));
+    h->atlas_active[i] = active ? 1 : 0;
+    return bcheck_h(b, h, upload_tiles(h, h->tile_w, h->tile_h));
+}
+
+// The packed grid of ladder level l, created (every cavity inactive) on first use.
+int ladder_grid(lbmfvm_batch_t *b, int l) {
+    if (b->lv[l]) return LBMFVM_OK;
+    lbmfvm_opts_t o = b->opts;
+    o.store = b->prec[l];
+    lbmfvm_t *h = nullptr;
+    if (int r = create_impl(&b->atlas_grid, nullptr, 0.1, 0.1, 0.0, nullptr, &o, &h, &b->spec))
+        return bfail(b, r, "creating a grid of the precision ladder failed: %s", g_err);
+    h->atlas_active.assign(b->cav.size(), 0);
+    if (int r = upload_tiles(h, h->tile_w, h->tile_h)) {
+        bfail(b, r, "%s", h->err);
+        lbmfvm_destroy(h);
+        return r;
+    }
+    b->lv[l] = h;
+    return LBMFVM_OK;
+}
+
+// Moves active cavity i one level up the ladder: both population and
+// temperature buffers converted, the residual snapshot carried over, the tile
+// lists of both grids rebuilt.  Called between steps, with both grids'
+// streams idle.
+int promote(lbmfvm_batch_t *b, int i) {
+    auto &c = b->cav[i];
+    if (c.level + 1 >= b->nlv) return LBMFVM_OK;
+    if (int r = ladder_grid(b, c.level + 1)) return r;
+    lbmfvm_t *a = b->lv[c.level], *p = b->lv[c.level + 1];
+    const long long off = (long long)c.y0 * a->L.pitch + c.x0;
+    if (int r = bcheck_h(b, a, join_in(a))) return r;
+    if (cudaStreamSynchronize(a->s) != cudaSuccess) return bfail(b, LBMFVM_ERR_CUDA, "stream synchronisation failed");
+    if (int r = bcheck_h(b, p, join_in(p))) return r;
+    BDISPATCH(a, launch_convert_from, a, p, off, off, c.grid.nx, c.grid.ny, a->parity ^ p->parity);
+    cudaError_t e = cudaGetLastError();
+    const size_t n = (size_t)c.grid.nx * c.grid.ny;
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(reinterpret_cast<double *>(p->base + p->L.snap) + c.snap_off,
+                            reinterpret_cast<const double *>(a->base + a->L.snap) + c.snap_off, 2 * n * sizeof(double),
+                            cudaMemcpyDeviceToDevice, p->s);
+    if (e != cudaSuccess) return bfail(b, LBMFVM_ERR_CUDA, "polish conversion failed: %s", cudaGetErrorString(e));
+    if (int r = bcheck_h(b, p, join_out(p))) return r;
+    if (int r = set_active(b, i, false)) return r;
+    c.level++;
+    c.best_r = INFINITY;
+    c.since_best = 0;
+    return set_active(b, i, true);
+}
+
+// Whether cavity i, with residual r, moves up the ladder: below its level's
+// switch value, or within a factor 100 of it and without halving its best
+// residual for stall_checks checks (a floor above the switch value; the
+// factor keeps slow transients at their level).
+bool wants_promotion(lbmfvm_batch_t *b, int i, double r) {
+    auto &c = b->cav[i];
+    if (c.level + 1 >= b->nlv) return false;
+    if (r < 0.5 * c.best_r) {
+        c.best_r = r;
+        c.since_best = 0;
+    } else {
+        c.since_best++;
+    }
+    const double sw = b->switch_r[c.level];
+    const int stall = b->stall_checks[c.level];
+    return sw > 0.0 && (r < sw || (stall > 0 && c.since_best >= stall && r < 100.0 * sw));
+}
+
+// Mass renormalisation of every active cavity from the totals of the last
+// residual pass (see rescale_kernel).
+int rescale_active(lbmfvm_batch_t *b) {
+    for (lbmfvm_t *h : b->lv) {
+        if (!h) continue;
+        if (int r = bcheck_h(b, h, join_in(h))) return r;
+        for (int i = 0; i < (int)b->cav.size(); i++)
+            if (b->cav[i].active && hnd(b, i) == h) BDISPATCH(h, launch_cav_rescale, b, i);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return bfail(b, LBMFVM_ERR_CUDA, "mass renormalisation failed: %s", cudaGetErrorString(e));
+        if (int r = bcheck_h(b, h, join_out(h))) return r;
+    }
+    return LBMFVM_OK;
+}
+
+// Cavity i back to the storage grid (inactive there until set_state).
+int unpolish(lbmfvm_batch_t *b, int i) {
+    auto &c = b->cav[i];
+    if (c.level == 0) return LBMFVM_OK;
+    if (int r = set_active(b, i, false)) return r;
+    c.level = 0;
+    c.active = false;
+    return LBMFVM_OK;
 }
 
 int cav_set_state(lbmfvm_batch_t *b, int i, const float *u, const float *v, const float *T) {
     lbmfvm_t *h = b->a;
+    if (int r = unpolish(b, i)) return r;
     if (int r = set_active(b, i, true)) return r;
     const auto &c = b->cav[i];
     const size_t n = (size_t)c.grid.nx * c.grid.ny;
@@ -186,13 +320,15 @@ int cav_set_state(lbmfvm_batch_t *b, int i, const float *u, const float *v, cons
         dT = stage + 2 * n;
     }
     if (e != cudaSuccess) return bfail(b, LBMFVM_ERR_CUDA, "staging the state failed: %s", cudaGetErrorString(e));
-    BDISPATCH(b, launch_cav_init, b, i, du, dv, dT);
+    BDISPATCH(h, launch_cav_init, b, i, du, dv, dT);
     b->cav[i].steps = 0;
-    BDISPATCH(b, launch_cav_residual, b, i, 1);  // snapshot := u^0
+    BDISPATCH(h, launch_cav_residual, b, i, 1);  // snapshot := u^0
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->s);
     if (e != cudaSuccess) return bfail(b, LBMFVM_ERR_CUDA, "initial state failed: %s", cudaGetErrorString(e));
     b->cav[i].last_r = NAN;
+    b->cav[i].best_r = INFINITY;
+    b->cav[i].since_best = 0;
     return bcheck(b, join_out(h));
 }
 
@@ -240,6 +376,9 @@ int lbmfvm_batch_create(int32_t n, const lbmfvm_grid_t *grids, const uint8_t *co
             return fail_thread(LBMFVM_ERR_UNSTABLE, "cavity %d: %s", i, why);
         }
         c.active = true;
+        c.level = 0;
+        c.best_r = INFINITY;
+        c.since_best = 0;
         c.steps = 0;
         c.parity = 0;
         c.last_r = NAN;
@@ -291,14 +430,16 @@ int lbmfvm_batch_create(int32_t n, const lbmfvm_grid_t *grids, const uint8_t *co
         cd.y0 = c.y0;
         cd.nx = c.grid.nx;
         cd.ny = c.grid.ny;
-        cd.omega = (float)(1.0 / c.tau);
-        cd.alpha = (float)c.alpha;
-        cd.gbeta = (float)c.gbeta;
-        cd.t_ref = (float)c.t_ref;
+        cd.omega = 1.0 / c.tau;
+        cd.alpha = c.alpha;
+        cd.gbeta = c.gbeta;
+        cd.t_ref = c.t_ref;
         for (int s = 0; s < 4; s++) {
             const bool moving = c.grid.bc[s] == LBMFVM_BC_MOVING;
-            cd.wall_u[s] = (float)(moving && s >= 2 ? c.grid.u_lid : 0.0);
-            cd.wall_v[s] = (float)(moving && s < 2 ? c.grid.u_lid : 0.0);
+            cd.wall_u[s] = moving && s >= 2 ? c.grid.u_lid : 0.0;
+            cd.wall_v[s] = moving && s < 2 ? c.grid.u_lid : 0.0;
+            cd.wall_uf[s] = (float)cd.wall_u[s];
+            cd.wall_vf[s] = (float)cd.wall_v[s];
         }
         spec.cavs.push_back(cd);
     }
@@ -320,6 +461,24 @@ int lbmfvm_batch_create(int32_t n, const lbmfvm_grid_t *grids, const uint8_t *co
         delete b;
         return r;
     }
+    // the ladder above the storage precision (see the top of this file)
+    b->lv[0] = b->a;
+    b->prec[0] = o.store;
+    if (o.store == LBMFVM_F16 || o.store == LBMFVM_BF16) {
+        b->prec[b->nlv] = LBMFVM_F32;
+        b->switch_r[b->nlv - 1] = o.store == LBMFVM_F16 ? 2e-3 : 1e-2;
+        b->stall_checks[b->nlv - 1] = 16;
+        b->nlv++;
+    }
+    if (o.store != LBMFVM_F64) {
+        b->prec[b->nlv] = LBMFVM_F64;
+        b->switch_r[b->nlv - 1] = 1e-6;
+        b->stall_checks[b->nlv - 1] = 32;
+        b->nlv++;
+    }
+    b->atlas_grid = atlas;
+    b->spec = std::move(spec);
+    b->opts = o;
     // wall temperatures per cavity for the initial-state kernel
     std::vector<double> tw(4 * (size_t)n);
     for (int i = 0; i < n; i++)
@@ -347,10 +506,13 @@ int lbmfvm_batch_set_state(lbmfvm_batch_t *b, int32_t i, const float *u, const f
 int lbmfvm_batch_step(lbmfvm_batch_t *b, int64_t n) {
     if (!b) return fail_thread(LBMFVM_ERR_ARG, "batch is NULL");
     if (n < 0) return bfail(b, LBMFVM_ERR_ARG, "n = %lld is negative", (long long)n);
-    bool any = false;
-    for (auto &c : b->cav) any |= c.active;
-    if (!any || n == 0) return LBMFVM_OK;
-    if (int r = bcheck(b, lbmfvm_step(b->a, n))) return r;
+    bool any[3] = {false, false, false};
+    for (auto &c : b->cav)
+        if (c.active) any[c.level] = true;
+    if (n == 0) return LBMFVM_OK;
+    for (int l = 0; l < b->nlv; l++)
+        if (any[l])
+            if (int r = bcheck_h(b, b->lv[l], lbmfvm_step(b->lv[l], n))) return r;
     for (auto &c : b->cav)
         if (c.active) c.steps += n;
     return LBMFVM_OK;
@@ -358,23 +520,31 @@ int lbmfvm_batch_step(lbmfvm_batch_t *b, int64_t n) {
 
 int lbmfvm_batch_residuals(lbmfvm_batch_t *b, double *r) {
     if (!b || !r) return fail_thread(LBMFVM_ERR_ARG, "batch or r is NULL");
-    lbmfvm_t *h = b->a;
-    if (int e = bcheck(b, join_in(h))) return e;
     const int n = (int)b->cav.size();
-    for (int i = 0; i < n; i++)
-        if (b->cav[i].active) BDISPATCH(b, launch_cav_residual, b, i, 0);
-    std::vector<double> res(4 * (size_t)n);
-    cudaError_t e = cudaGetLastError();
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(res.data(), h->base + h->L.cavres, res.size() * sizeof(double), cudaMemcpyDeviceToHost, h->s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(h->s);
-    if (e != cudaSuccess) return bfail(b, LBMFVM_ERR_CUDA, "batch residual failed: %s", cudaGetErrorString(e));
-    if (int e2 = bcheck(b, check_device_status(h))) return e2;
+    // per grid: residual kernels of its active cavities, then the table
+    std::vector<double> res[3];
+    for (int g = 0; g < 3; g++) {
+        lbmfvm_t *h = b->lv[g];
+        if (!h) continue;
+        if (int e = bcheck_h(b, h, join_in(h))) return e;
+        for (int i = 0; i < n; i++)
+            if (b->cav[i].active && hnd(b, i) == h) BDISPATCH(h, launch_cav_residual, b, i, 0);
+        res[g].resize(kCavRes * (size_t)n);
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(res[g].data(), h->base + h->L.cavres, res[g].size() * sizeof(double),
+                                cudaMemcpyDeviceToHost, h->s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->s);
+        if (e != cudaSuccess) return bfail(b, LBMFVM_ERR_CUDA, "batch residual failed: %s", cudaGetErrorString(e));
+        if (int e2 = bcheck_h(b, h, check_device_status(h))) return e2;
+        if (int e2 = bcheck_h(b, h, join_out(h))) return e2;
+    }
     int status = LBMFVM_OK;
     for (int i = 0; i < n; i++) {
         auto &c = b->cav[i];
         if (c.active) {
-            const double num = res[4 * i], den = res[4 * i + 1];
+            const std::vector<double> &rs = res[c.level];
+            const double num = rs[kCavRes * i], den = rs[kCavRes * i + 1];
             if (!std::isfinite(num) || !std::isfinite(den)) {
                 c.last_r = NAN;
                 status = bfail(b, LBMFVM_ERR_DIVERGED, "cavity %d: non-finite velocity", i);
@@ -384,7 +554,6 @@ int lbmfvm_batch_residuals(lbmfvm_batch_t *b, double *r) {
         }
         r[i] = c.last_r;
     }
-    if (int e2 = bcheck(b, join_out(h))) return e2;
     return status;
 }
 
@@ -404,9 +573,13 @@ int lbmfvm_batch_run(lbmfvm_batch_t *b, double tol, int64_t check_every, int64_t
         if ((status = lbmfvm_batch_step(b, k))) break;
         done += k;
         if ((status = lbmfvm_batch_residuals(b, r.data()))) break;
-        for (int i = 0; i < n; i++)
-            if (b->cav[i].active && r[i] < tol)
-                if ((status = set_active(b, i, false))) break;
+        if ((status = rescale_active(b))) break;
+        for (int i = 0; i < n && !status; i++) {
+            auto &c = b->cav[i];
+            if (!c.active) continue;
+            if (r[i] < tol) status = set_active(b, i, false);
+            else if (wants_promotion(b, i, r[i])) status = promote(b, i);
+        }
         if (status) break;
     }
     for (int i = 0; i < n; i++) {
@@ -418,15 +591,16 @@ int lbmfvm_batch_run(lbmfvm_batch_t *b, double tol, int64_t check_every, int64_t
 
 int lbmfvm_batch_fields(lbmfvm_batch_t *b, int32_t i, double *rho, double *u, double *v, double *T) {
     if (int r = check_index(b, i)) return r;
-    lbmfvm_t *h = b->a;
+    lbmfvm_t *h = hnd(b, i);
     const size_t n = (size_t)b->cav[i].grid.nx * b->cav[i].grid.ny;
     double *st = reinterpret_cast<double *>(h->base + h->L.stage);
-    if (int r = bcheck(b, join_in(h))) return r;
+    if (int r = bcheck_h(b, h, join_in(h))) return r;
     double *outs[2][2] = {{rho, u}, {v, T}};
     cudaError_t e = cudaSuccess;
     for (int which = 0; which < 2 && e == cudaSuccess; which++) {
         if (!outs[which][0] && !outs[which][1]) continue;
         switch (h->prec) {
+            case LBMFVM_F64: launch_cav_fields<double, double>(b, i, which, st, st + n); break;
             case LBMFVM_F32: launch_cav_fields<float, double>(b, i, which, st, st + n); break;
             case LBMFVM_F16: launch_cav_fields<__half, double>(b, i, which, st, st + n); break;
             case LBMFVM_BF16: launch_cav_fields<__nv_bfloat16, double>(b, i, which, st, st + n); break;
@@ -437,29 +611,29 @@ int lbmfvm_batch_fields(lbmfvm_batch_t *b, int32_t i, double *rho, double *u, do
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->s);
     if (e != cudaSuccess) return bfail(b, LBMFVM_ERR_CUDA, "batch fields failed: %s", cudaGetErrorString(e));
-    if (int r = bcheck(b, check_device_status(h))) return r;
-    return bcheck(b, join_out(h));
+    if (int r = bcheck_h(b, h, check_device_status(h))) return r;
+    return bcheck_h(b, h, join_out(h));
 }
 
 int lbmfvm_batch_nusselt(lbmfvm_batch_t *b, int32_t i, double *mean_hot, double *local_hot, double *mean_cold) {
     if (int r = check_index(b, i)) return r;
-    lbmfvm_t *h = b->a;
-    if (int r = bcheck(b, join_in(h))) return r;
-    BDISPATCH(b, launch_cav_nusselt, b, i);
+    lbmfvm_t *h = hnd(b, i);
+    if (int r = bcheck_h(b, h, join_in(h))) return r;
+    BDISPATCH(h, launch_cav_nusselt, b, i);
     double means[2];
     double *red = reinterpret_cast<double *>(h->base + h->L.red);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(means, reinterpret_cast<double *>(h->base + h->L.cavres) + 4 * i + 2, sizeof(means),
+        e = cudaMemcpyAsync(means, reinterpret_cast<double *>(h->base + h->L.cavres) + kCavRes * i + kCavNu, sizeof(means),
                             cudaMemcpyDeviceToHost, h->s);
     if (e == cudaSuccess && local_hot)
-        e = cudaMemcpyAsync(local_hot, red + 2 * kResidualBlocks + 8, b->cav[i].grid.ny * sizeof(double),
+        e = cudaMemcpyAsync(local_hot, red + kRedLocal, b->cav[i].grid.ny * sizeof(double),
                             cudaMemcpyDefault, h->s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->s);
     if (e != cudaSuccess) return bfail(b, LBMFVM_ERR_CUDA, "batch Nusselt failed: %s", cudaGetErrorString(e));
     if (mean_hot) *mean_hot = means[0];
     if (mean_cold) *mean_cold = means[1];
-    return bcheck(b, join_out(h));
+    return bcheck_h(b, h, join_out(h));
 }
 
 int lbmfvm_batch_info(const lbmfvm_batch_t *b, int32_t i, int64_t *steps, int32_t *active, double *params) {
@@ -477,8 +651,28 @@ int lbmfvm_batch_info(const lbmfvm_batch_t *b, int32_t i, int64_t *steps, int32_
     return LBMFVM_OK;
 }
 
+int lbmfvm_batch_set_polish(lbmfvm_batch_t *b, int32_t prec, double r_switch, int32_t stall_checks) {
+    if (!b) return fail_thread(LBMFVM_ERR_ARG, "batch is NULL");
+    if (std::isnan(r_switch)) return bfail(b, LBMFVM_ERR_ARG, "r_switch is NaN");
+    for (int l = 0; l + 1 < b->nlv; l++)
+        if (b->prec[l] == prec) {
+            b->switch_r[l] = r_switch > 0.0 ? r_switch : 0.0;
+            b->stall_checks[l] = stall_checks > 0 ? stall_checks : 0;
+            return LBMFVM_OK;
+        }
+    return bfail(b, LBMFVM_ERR_ARG, "precision %d is not a level of this batch's ladder below its top", prec);
+}
+
+int lbmfvm_batch_precision(const lbmfvm_batch_t *b, int32_t i, int32_t *prec) {
+    if (!b || !prec) return fail_thread(LBMFVM_ERR_ARG, "batch or prec is NULL");
+    if (i < 0 || i >= (int)b->cav.size()) return fail_thread(LBMFVM_ERR_ARG, "cavity index %d out of range", i);
+    *prec = hnd(b, i)->prec;
+    return LBMFVM_OK;
+}
+
 void lbmfvm_batch_destroy(lbmfvm_batch_t *b) {
     if (!b) return;
+    for (int l = 1; l < 3; l++) lbmfvm_destroy(b->lv[l]);
     lbmfvm_destroy(b->a);
     delete b;
 }

@@ -31,6 +31,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace lbmfvm_dev {
 
 // Node codes: bits 0-1 kind, bits 2-5 partner direction of wall nodes,
@@ -103,21 +105,27 @@ struct StepArgs {
 
 // One cavity of the TMA path: its rectangle in the (possibly multi-cavity)
 // node arrays, which starts on a tile corner, and its lattice parameters.
+// Wall velocities are kept in both arithmetic precisions (FP64 conversions
+// are slow on this GPU; no kernel converts).
 struct CavityDesc {
     int x0, y0, nx, ny;
-    float omega, alpha, gbeta, t_ref, fx, fy;
-    float wall_u[4], wall_v[4];  // box-wall velocity per side W, E, S, N
+    double omega, alpha, gbeta, t_ref, fx, fy;
+    double wall_u[4], wall_v[4];    // box-wall velocity per side W, E, S, N
+    float wall_uf[4], wall_vf[4];   // the same in FP32
 };
 
 // One tile of the TMA path: what a block needs to know about it.  A tile
 // holds nodes of one cavity only (plus unused padding beyond its rectangle).
 // The host writes the list; the issuing thread copies a tile's header next
 // to its stage with the same bulk-copy barrier as the tile's data.
+// The lattice parameters come in both arithmetic precisions, rounded by the
+// host, so that no kernel converts (FP64 conversions are slow on this GPU).
 struct TileHeader {
     int x0, y0, ox, oy, nx, ny, cav, pad;  // origin; origin relative to the cavity; cavity size
-    float omega, alpha, gbeta, t_ref, fx, fy, pad1, pad2;
+    double omega, alpha, gbeta, t_ref, fx, fy;
+    float omega_f, alpha_f, gbeta_f, t_ref_f, fx_f, fy_f, pad1, pad2;
 };
-static_assert(sizeof(TileHeader) == 64, "tile headers are 64-byte bulk copies");
+static_assert(sizeof(TileHeader) == 112, "tile headers are 112-byte bulk copies");
 
 
 // ---------------------------------------------------------------------------
@@ -448,6 +456,7 @@ __device__ __forceinline__ void load_2d(void *dst, const CUtensorMap *map, uint6
 // same bytes receive the tile's results, which one TMA bulk store writes back.
 template <class S, int TW_, int TH_, int STAGES_, int THREADS_, int MINB_ = 1>
 struct TmaTile {
+    using TC = typename Compute<S>::type;  // temperature and ring element
     static constexpr int TW = TW_, TH = TH_, STAGES = STAGES_, THREADS = THREADS_;
     static constexpr int MINB = MINB_;             // blocks per SM the register budget must allow
     static constexpr int NPT = TW * TH / THREADS;  // own nodes per thread
@@ -458,7 +467,7 @@ struct TmaTile {
     static constexpr int RW = TW + 2, RH = TH + 2;         // tile + ring
     static constexpr int NRING = 2 * RW + 2 * TH;          // ring nodes
     static constexpr uint32_t F_BYTES = 9u * FH * FW * sizeof(S);
-    static constexpr uint32_t T_BYTES = (uint32_t)THT * TWD * 4u;
+    static constexpr uint32_t T_BYTES = (uint32_t)THT * TWD * (uint32_t)sizeof(TC);
     static constexpr uint32_t C_BYTES = (uint32_t)CHT * CWD;
     static constexpr uint32_t align128(uint32_t v) { return (v + 127u) & ~127u; }
     static constexpr uint32_t F_OFF = 0, T_OFF = align128(F_BYTES), C_OFF = T_OFF + align128(T_BYTES);
@@ -467,17 +476,19 @@ struct TmaTile {
     // results, inside the stage's population bytes: [9][TH][TW] then [TH][TW]
     static constexpr uint32_t OF_BYTES = 9u * TH * TW * sizeof(S);
     static constexpr uint32_t OT_OFF = align128(OF_BYTES);
-    static constexpr uint32_t OT_BYTES = (uint32_t)TH * TW * 4u;
+    static constexpr uint32_t OT_BYTES = (uint32_t)TH * TW * (uint32_t)sizeof(TC);
     static constexpr uint32_t RING_OFF = STAGES * STAGE_BYTES;
-    static constexpr uint32_t RING_BYTES = align128(2u * RH * RW * 4u);  // u, v of tile + ring
+    static constexpr uint32_t RING_BYTES = align128(2u * RH * RW * (uint32_t)sizeof(TC));  // u, v of tile + ring
     static constexpr uint32_t BAR_OFF = RING_OFF + 2u * RING_BYTES;      // two ring buffers
     static constexpr uint32_t HDR_OFF = BAR_OFF + align128(8u * STAGES + 16u);
-    static constexpr uint32_t SMEM_BYTES = HDR_OFF + STAGES * 64u;
+    static constexpr uint32_t SMEM_BYTES = HDR_OFF + STAGES * (uint32_t)sizeof(TileHeader);
     static_assert(SMEM_BYTES <= 232448u, "tile configuration exceeds 227 KB of shared memory");
     static_assert(OT_OFF + OT_BYTES <= F_BYTES, "results must fit in the staged population bytes");
-    static_assert((FW * sizeof(S)) % 16 == 0 && (TWD * 4) % 16 == 0 && CWD % 16 == 0 && (TW * sizeof(S)) % 16 == 0,
+    static_assert((FW * sizeof(S)) % 16 == 0 && (TWD * sizeof(TC)) % 16 == 0 && CWD % 16 == 0 &&
+                      (TW * sizeof(S)) % 16 == 0 && (TW * sizeof(TC)) % 16 == 0,
                   "TMA boxes need 16-byte inner extents");
     static_assert(TW % 16 == 0, "tile origins must stay 16-byte aligned for every box");
+    static_assert(TW >= 32 && TH >= 8, "tile lists are sized for tiles of at least 32 x 8 nodes");
     static_assert(NPT >= 1 && NPT * THREADS == TW * TH && NRING <= THREADS, "thread mapping");
     static_assert(STAGES >= 2, "the pipeline needs two stages");
 };
@@ -525,7 +536,7 @@ __global__ void __launch_bounds__(G::THREADS, G::MINB)
                     const int *__restrict__ ntiles_p, const __grid_constant__ CUtensorMap map_f,
                     const __grid_constant__ CUtensorMap map_T, const __grid_constant__ CUtensorMap map_c,
                     const __grid_constant__ CUtensorMap map_f_out, const __grid_constant__ CUtensorMap map_T_out) {
-    using C = float;
+    using C = typename Compute<S>::type;
     constexpr int TW = G::TW, TH = G::TH, FW = G::FW, FH = G::FH, RW = G::RW, NPT = G::NPT;
     constexpr int XOFF = G::XOFF;
     constexpr int OPLANE = TH * TW;
@@ -602,9 +613,15 @@ __global__ void __launch_bounds__(G::THREADS, G::MINB)
         // node (lx, ly) of the tile sits at (ox + lx, oy + ly) of its cavity
         const int ox = hd.ox, oy = hd.oy, cv_nx = hd.nx, cv_ny = hd.ny;
         const CavityDesc *cvp = cavs + hd.cav;
-        const C alpha = hd.alpha, omega = hd.omega, gbeta = hd.gbeta, t_ref = hd.t_ref, fx = hd.fx, fy = hd.fy;
+        C alpha, omega, gbeta, t_ref, fx, fy;
+        if constexpr (std::is_same<C, double>::value) {
+            alpha = hd.alpha, omega = hd.omega, gbeta = hd.gbeta, t_ref = hd.t_ref, fx = hd.fx, fy = hd.fy;
+        } else {
+            alpha = hd.alpha_f, omega = hd.omega_f, gbeta = hd.gbeta_f, t_ref = hd.t_ref_f, fx = hd.fx_f,
+            fy = hd.fy_f;
+        }
         const S *F = reinterpret_cast<const S *>(stg + G::F_OFF);
-        const float *TT = reinterpret_cast<const float *>(stg + G::T_OFF);
+        const C *TT = reinterpret_cast<const C *>(stg + G::T_OFF);
         const uint8_t *CC = reinterpret_cast<const uint8_t *>(stg + G::C_OFF);
         C *RU = reinterpret_cast<C *>(smem + G::RING_OFF + (k & 1) * G::RING_BYTES), *RV = RU + G::RH * RW;
         // staged-box index of node (lx, ly) relative to the tile origin
@@ -630,8 +647,13 @@ __global__ void __launch_bounds__(G::THREADS, G::MINB)
                     // box walls: vertical sides own the corners
                     const int cx = ox + lx, cy = oy + ly;
                     const int side = cx == 0 ? 0 : (cx == cv_nx - 1 ? 1 : (cy == 0 ? 2 : 3));
-                    uw = cvp->wall_u[side];
-                    vw = cvp->wall_v[side];
+                    if constexpr (std::is_same<C, double>::value) {
+                        uw = cvp->wall_u[side];
+                        vw = cvp->wall_v[side];
+                    } else {
+                        uw = cvp->wall_uf[side];
+                        vw = cvp->wall_vf[side];
+                    }
                 }
                 nee<C>(g, drho, ux, uy, uw, vw);
             } else {
@@ -682,7 +704,7 @@ __global__ void __launch_bounds__(G::THREADS, G::MINB)
         // Phase B: energy balance and collision of the own nodes; results go
         // to the stage's (now dead) population bytes.  Inert nodes keep T.
         S *OF = reinterpret_cast<S *>(stg + G::F_OFF);
-        float *OT = reinterpret_cast<float *>(stg + G::F_OFF + G::OT_OFF);
+        C *OT = reinterpret_cast<C *>(stg + G::F_OFF + G::OT_OFF);
 #pragma unroll
         for (int j = 0; j < NPT; j++) {
             const int i = tid + j * G::THREADS;
@@ -782,6 +804,31 @@ __global__ void init_kernel(const StepArgs<S> a, S *f0_out, S *fstar_out, const 
     collide<C>(g, drho, ux, uy, a.omega, a.fx, Gy, [&](int q, C v2) { st(out + q * plane, v2); });
 }
 
+// State copy between storage precisions.  Every precision stores f - w_i, so
+// converting a state is a value conversion of each stored population and
+// temperature; buffer b of the source goes to buffer b ^ flip of the
+// destination, which keeps the two ping-pong buffers' roles when the two
+// handles are at opposite parities.
+template <class S, class D>
+__global__ void convert_kernel(const S *fs0, const S *fs1, const typename Compute<S>::type *Ts0,
+                               const typename Compute<S>::type *Ts1, int pitch_s, long long plane_s, D *fd0, D *fd1,
+                               typename Compute<D>::type *Td0, typename Compute<D>::type *Td1, int pitch_d,
+                               long long plane_d, int nx, int ny, int flip) {
+    using CD = typename Compute<D>::type;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= nx || y >= ny) return;
+    const int b = blockIdx.z;
+    const S *fs = b ? fs1 : fs0;
+    const typename Compute<S>::type *Ts = b ? Ts1 : Ts0;
+    D *fd = (b ^ flip) ? fd1 : fd0;
+    CD *Td = (b ^ flip) ? Td1 : Td0;
+    const long long ks = (long long)y * pitch_s + x, kd = (long long)y * pitch_d + x;
+#pragma unroll
+    for (int q = 0; q < 9; q++) st(fd + kd + q * plane_d, CD(ld(fs + ks + q * plane_s)));
+    Td[kd] = CD(Ts[ks]);
+}
+
 // Pre-collision moments of the current step: re-pulled from the previous
 // post-collision buffer (direct = 0), or read in place from the unrelaxed
 // initial populations (direct = 1, step 0).
@@ -834,12 +881,16 @@ __global__ void fields_kernel(const StepArgs<S> a, int direct, int which, O *out
 // fluid nodes, snapshot update; partials[2*b], partials[2*b+1].
 // A fixed assignment of rows to blocks and a fixed reduction tree make the
 // result independent of scheduling.
+// Sums of the residual pass, per block and in total: |u - u_s|^2, |u|^2,
+// rho - 1 and the node count, all over the fluid nodes.
+constexpr int kResidualSums = 4;
+
 template <class S>
 __global__ void __launch_bounds__(256) residual_kernel(const StepArgs<S> a, int direct, double *su,
                                                        double *sv, double *partials, int update_only) {
     using C = typename Compute<S>::type;
-    __shared__ double red[2][8];
-    double num = 0.0, den = 0.0;
+    __shared__ double red[kResidualSums][8];
+    double num = 0.0, den = 0.0, mass = 0.0, cnt = 0.0;
     for (int y = blockIdx.x; y < a.ny; y += gridDim.x) {
         for (int x = threadIdx.x; x < a.nx; x += blockDim.x) {
             const long long k = (long long)y * a.pitch + x;
@@ -851,49 +902,69 @@ __global__ void __launch_bounds__(256) residual_kernel(const StepArgs<S> a, int 
             const double du = (double)ux - su[i], dv = (double)uy - sv[i];
             num += du * du + dv * dv;
             den += (double)ux * (double)ux + (double)uy * (double)uy;
+            mass += (double)drho;
+            cnt += 1.0;
             su[i] = (double)ux;
             sv[i] = (double)uy;
         }
     }
     if (update_only) return;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        num += __shfl_down_sync(0xffffffffu, num, o);
-        den += __shfl_down_sync(0xffffffffu, den, o);
-    }
+    double v[kResidualSums] = {num, den, mass, cnt};
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (lane == 0) {
-        red[0][wid] = num;
-        red[1][wid] = den;
+#pragma unroll
+    for (int j = 0; j < kResidualSums; j++) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[j] += __shfl_down_sync(0xffffffffu, v[j], o);
+        if (lane == 0) red[j][wid] = v[j];
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double a0 = 0.0, a1 = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); w++) {
-            a0 += red[0][w];
-            a1 += red[1][w];
-        }
-        partials[2 * blockIdx.x] = a0;
-        partials[2 * blockIdx.x + 1] = a1;
+    if (threadIdx.x < kResidualSums) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += red[threadIdx.x][w];
+        partials[kResidualSums * blockIdx.x + threadIdx.x] = t;
     }
 }
 
 // Residual, pass 2: one warp sums the block partials in a fixed order.
 __global__ void residual_finish_kernel(const double *partials, int nblocks, double *out) {
-    double a0 = 0.0, a1 = 0.0;
-    for (int b = threadIdx.x; b < nblocks; b += 32) {
-        a0 += partials[2 * b];
-        a1 += partials[2 * b + 1];
-    }
+    double v[kResidualSums] = {};
+    for (int b = threadIdx.x; b < nblocks; b += 32)
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        a0 += __shfl_down_sync(0xffffffffu, a0, o);
-        a1 += __shfl_down_sync(0xffffffffu, a1, o);
+        for (int j = 0; j < kResidualSums; j++) v[j] += partials[kResidualSums * b + j];
+#pragma unroll
+    for (int j = 0; j < kResidualSums; j++) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[j] += __shfl_down_sync(0xffffffffu, v[j], o);
     }
-    if (threadIdx.x == 0) {
-        out[0] = a0;
-        out[1] = a1;
-    }
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int j = 0; j < kResidualSums; j++) out[j] = v[j];
+}
+
+// Mass renormalisation.  With the Eq. 18 force and the pressure read as
+// rho0 cs^2, one step is homogeneous of degree one in f: f -> c f scales the
+// whole trajectory by c and leaves u and T unchanged.  The non-equilibrium
+// extrapolation walls (Eqs. 94, 96) do not conserve mass, and once the flow
+// settles the mass shrinks by a fixed factor per step; rescaling both
+// population buffers so that the fluid nodes average rho = 1 keeps the stored
+// f - w_i at the size of the flow's own deviations without changing u or T.
+// tot: the totals of residual_kernel (tot[2] = sum of rho - 1, tot[3] = node
+// count) for this state.
+template <class S>
+__global__ void rescale_kernel(const StepArgs<S> a, S *f0, S *f1, const double *tot) {
+    using C = typename Compute<S>::type;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= a.nx || y >= a.ny) return;
+    const double n = tot[3], m = n + tot[2];
+    if (!(n > 0.0) || !(m > 0.0) || !isfinite(m)) return;
+    const long long k = (long long)y * a.pitch + x;
+    if ((decode(a.code[k]) & 3) == KIND_SOLID) return;
+    // f' = c f with c = n / m, stored as f' - w = c (f - w) + (c - 1) w
+    const C c = C(n / m), cm1 = C(-tot[2] / m);
+    S *f = (blockIdx.z ? f1 : f0) + k;
+#pragma unroll
+    for (int q = 0; q < 9; q++) st(f + q * a.plane, c * ld(f + q * a.plane) + cm1 * wq<C>(q));
 }
 
 // Nusselt number (Eq. 90) along the west (hot) and east (cold) walls in FP64:

@@ -25,6 +25,16 @@ namespace {
 
 constexpr int kGraphSteps = 64;      // launches per captured graph (even)
 constexpr int kResidualBlocks = 608; // 4 x 152 SMs
+// Reduction scratch (doubles): kResidualSums partials per residual block,
+// then the totals, the wall temperatures of the initial state, the two mean
+// Nusselt numbers and the local Nusselt numbers of the hot wall.
+constexpr int kRedTot = kResidualSums * kResidualBlocks;
+constexpr int kRedTwall = kRedTot + 4;
+constexpr int kRedNu = kRedTot + 8;
+constexpr int kRedLocal = kRedTot + 12;
+// Per cavity of a batch: the residual totals, the two mean Nusselt numbers.
+constexpr int kCavRes = 8;
+constexpr int kCavNu = 4;
 constexpr size_t kAlign = 256;
 
 thread_local char g_err[512] = "";
@@ -53,6 +63,7 @@ struct Layout {
     int pitch;
     long long plane;
     size_t f[2], T[2], code, snap, stage, red, err, cav, tiles, cavres, twall, total;
+    size_t tile_cap;  // headers the tile list holds
 };
 
 Layout make_layout(const lbmfvm_grid_t &g, int prec, int ncav = 1) {
@@ -73,14 +84,16 @@ Layout make_layout(const lbmfvm_grid_t &g, int prec, int ncav = 1) {
     L.code = take((size_t)L.plane);
     L.snap = take(2 * (size_t)g.nx * g.ny * sizeof(double));
     L.stage = take(2 * (size_t)g.nx * g.ny * sizeof(double));
-    L.red = take((2 * kResidualBlocks + 8 + (size_t)g.ny) * sizeof(double));
+    L.red = take((kRedLocal + (size_t)g.ny) * sizeof(double));
     L.err = take(16);
     // cavity table (one entry) and tile list of the TMA kernel (tiles of at
     // least 64 x 8 nodes), plus the tile count
     L.cav = take(ncav * sizeof(CavityDesc));
-    L.cavres = take(ncav * 4 * sizeof(double));  // per cavity: residual sums, Nusselt means
+    L.cavres = take(ncav * kCavRes * sizeof(double));
     L.twall = take(ncav * 4 * sizeof(double));   // per cavity: wall temperatures W, E, S, N
-    const size_t max_tiles = ((size_t)g.nx + 63) / 64 * (((size_t)g.ny + 7) / 8);
+    // enough for the smallest tile shape (32 x 8) of every configuration
+    const size_t max_tiles = ((size_t)g.nx + 31) / 32 * (((size_t)g.ny + 7) / 8);
+    L.tile_cap = max_tiles;
     L.tiles = take((max_tiles + 1) * sizeof(TileHeader));  // count slot, then the headers
     L.total = off;
     return L;
@@ -206,6 +219,7 @@ struct lbmfvm {
     int parity;       // buffer holding the current post-collision state
     int64_t steps;    // steps since set_state
     cudaGraphExec_t graph;
+    int graph_blocks; // grid of the TMA launches the graph holds
     bool use_tma;     // persistent TMA kernel (walled domains, 32/16-bit storage)
     bool stall_next;  // test hook armed by lbmfvm_inject_stall
     int tma_config;   // tile shape of the TMA kernel
@@ -286,15 +300,27 @@ template <class S> struct TmaConfig<S, 0> { using G = TmaTile<S, 64, 16, 3, 1024
 template <class S> struct TmaConfig<S, 1> { using G = TmaTile<S, 64, 16, 3, 512>; };
 template <class S> struct TmaConfig<S, 2> { using G = TmaTile<S, 64, 8, sizeof(S) == 4 ? 2 : 3, 512, 2>; };
 template <class S> struct TmaConfig<S, 3> { using G = TmaTile<S, 128, 8, sizeof(S) == 4 ? 2 : 3, 1024>; };
+// 64-bit storage: a 32 x 8 tile stages 43 KB, a 64 x 8 tile 78 KB.
+template <> struct TmaConfig<double, 0> { using G = TmaTile<double, 64, 8, 2, 256>; };
+template <> struct TmaConfig<double, 1> { using G = TmaTile<double, 32, 8, 3, 256>; };
+template <> struct TmaConfig<double, 2> { using G = TmaTile<double, 32, 16, 2, 512>; };
+template <> struct TmaConfig<double, 3> { using G = TmaTile<double, 32, 8, 2, 256, 2>; };
 constexpr int kTmaConfigs = 4;
+
+// Persistent grid of the TMA kernel: one block per resident slot, or one per
+// tile when there are fewer tiles.
+int tma_grid(const lbmfvm_t *h) {
+    const int resident = h->num_sms * h->tma_blocks_per_sm;
+    return h->ntiles < resident ? h->ntiles : resident;
+}
 
 template <class S, int CFG>
 void launch_tma_cfg(const lbmfvm_t *h, int cur, cudaStream_t s, bool stall) {
     using G = typename TmaConfig<S, CFG>::G;
     StepArgs<S> a = args_for<S>(h, cur);
     a.stall = stall ? 1 : 0;
-    const int resident = h->num_sms * h->tma_blocks_per_sm;
-    const int blocks = h->ntiles < resident ? h->ntiles : resident;
+    const int blocks = tma_grid(h);
+    if (blocks < 1) return;  // no active tile
     const CavityDesc *cavs = reinterpret_cast<const CavityDesc *>(h->base + h->L.cav);
     // the count sits at a fixed address in front of the list, so that a
     // captured graph reads the current count after the list has changed
@@ -316,11 +342,9 @@ void launch_step_tma(const lbmfvm_t *h, int cur, cudaStream_t s, bool stall) {
 
 template <class S>
 void launch_step(const lbmfvm_t *h, int cur, cudaStream_t s, bool stall) {
-    if constexpr (!std::is_same<S, double>::value) {
-        if (h->use_tma) {
-            launch_step_tma<S>(h, cur, s, stall);
-            return;
-        }
+    if (h->use_tma) {
+        launch_step_tma<S>(h, cur, s, stall);
+        return;
     }
     switch (h->tile_y) {
         case 4: launch_step_ty<S, 4>(h, cur, s); break;
@@ -362,6 +386,7 @@ int build_graph(lbmfvm_t *h) {
         h->graph = nullptr;
         return fail(h, LBMFVM_ERR_CUDA, "graph instantiation failed: %s", cudaGetErrorString(e));
     }
+    h->graph_blocks = h->use_tma ? tma_grid(h) : 0;
     return LBMFVM_OK;
 }
 
@@ -373,7 +398,7 @@ void launch_init(lbmfvm_t *h, const float *u0, const float *v0, const float *T0)
     S *f0 = reinterpret_cast<S *>(h->base + h->L.f[1]);
     C *Ta = reinterpret_cast<C *>(h->base + h->L.T[0]);
     C *Tb = reinterpret_cast<C *>(h->base + h->L.T[1]);
-    double *tw = reinterpret_cast<double *>(h->base + h->L.red) + 2 * kResidualBlocks + 2;
+    double *tw = reinterpret_cast<double *>(h->base + h->L.red) + kRedTwall;
     dim3 block(32, 8), grid((h->grid.nx + 31) / 32, (h->grid.ny + 7) / 8);
     init_kernel<S><<<grid, block, 0, h->s>>>(a, f0, fstar, u0, v0, T0, h->grid.t_init, tw, h->grid.bc[0],
                                              h->grid.bc[1], h->grid.bc[2], h->grid.bc[3], Ta, Tb);
@@ -399,7 +424,7 @@ void launch_residual(lbmfvm_t *h, int update_only) {
     double *sv = su + (size_t)h->grid.nx * h->grid.ny;
     double *red = reinterpret_cast<double *>(h->base + h->L.red);
     residual_kernel<S><<<kResidualBlocks, 256, 0, h->s>>>(a, direct, su, sv, red, update_only);
-    if (!update_only) residual_finish_kernel<<<1, 32, 0, h->s>>>(red, kResidualBlocks, red + 2 * kResidualBlocks);
+    if (!update_only) residual_finish_kernel<<<1, 32, 0, h->s>>>(red, kResidualBlocks, red + kRedTot);
 }
 
 template <class S, class O>
@@ -415,8 +440,19 @@ void launch_nusselt(lbmfvm_t *h) {
     StepArgs<S> a = args_for<S>(h, h->parity);
     double *red = reinterpret_cast<double *>(h->base + h->L.red);
     const double dT = h->grid.t_wall[LBMFVM_SIDE_W] - h->grid.t_wall[LBMFVM_SIDE_E];
-    nusselt_kernel<S><<<1, 256, 0, h->s>>>(a, (double)(h->grid.ny - 1), dT, red + 2 * kResidualBlocks + 8,
-                                           red + 2 * kResidualBlocks + 6);
+    nusselt_kernel<S><<<1, 256, 0, h->s>>>(a, (double)(h->grid.ny - 1), dT, red + kRedLocal, red + kRedNu);
+}
+
+// Mass renormalisation of the current state (both population buffers) from
+// the totals of the last residual pass.
+template <class S>
+void launch_rescale(lbmfvm_t *h) {
+    StepArgs<S> a = args_for<S>(h, h->parity);
+    S *f0 = reinterpret_cast<S *>(h->base + h->L.f[0]);
+    S *f1 = reinterpret_cast<S *>(h->base + h->L.f[1]);
+    const double *tot = reinterpret_cast<const double *>(h->base + h->L.red) + kRedTot;
+    dim3 block(32, 8), grid((h->grid.nx + 31) / 32, (h->grid.ny + 7) / 8, 2);
+    rescale_kernel<S><<<grid, block, 0, h->s>>>(a, f0, f1, tot);
 }
 
 #define DISPATCH(h, FN, ...)                                          \
@@ -439,7 +475,7 @@ int set_state_impl(lbmfvm_t *h, const float *u, const float *v, const float *T) 
     if (T) { CU(h, cudaMemcpyAsync(stage + 2 * n, T, n * sizeof(float), cudaMemcpyDefault, h->s)); dT = stage + 2 * n; }
     double tw[4];
     for (int s = 0; s < 4; s++) tw[s] = h->grid.t_wall[s];
-    double *dtw = reinterpret_cast<double *>(h->base + h->L.red) + 2 * kResidualBlocks + 2;
+    double *dtw = reinterpret_cast<double *>(h->base + h->L.red) + kRedTwall;
     CU(h, cudaMemcpyAsync(dtw, tw, sizeof(tw), cudaMemcpyHostToDevice, h->s));
     DISPATCH(h, launch_init, h, du, dv, dT);
     CU(h, cudaGetLastError());
@@ -451,6 +487,37 @@ int set_state_impl(lbmfvm_t *h, const float *u, const float *v, const float *T) 
     // valid until the kernels above have read them.
     CU(h, cudaStreamSynchronize(h->s));
     return join_out(h);
+}
+
+// Converts both population buffers and both temperature buffers of a
+// rectangle of `src` (origin off_s) into `dst` (origin off_d); flip swaps the
+// buffers' indices when the handles stand at opposite parities.
+template <class S, class D>
+void launch_convert(const lbmfvm_t *src, lbmfvm_t *dst, long long off_s, long long off_d, int nx, int ny, int flip) {
+    using CS = typename Compute<S>::type;
+    using CD = typename Compute<D>::type;
+    const S *fs0 = reinterpret_cast<const S *>(src->base + src->L.f[0]) + off_s;
+    const S *fs1 = reinterpret_cast<const S *>(src->base + src->L.f[1]) + off_s;
+    const CS *Ts0 = reinterpret_cast<const CS *>(src->base + src->L.T[0]) + off_s;
+    const CS *Ts1 = reinterpret_cast<const CS *>(src->base + src->L.T[1]) + off_s;
+    D *fd0 = reinterpret_cast<D *>(dst->base + dst->L.f[0]) + off_d;
+    D *fd1 = reinterpret_cast<D *>(dst->base + dst->L.f[1]) + off_d;
+    CD *Td0 = reinterpret_cast<CD *>(dst->base + dst->L.T[0]) + off_d;
+    CD *Td1 = reinterpret_cast<CD *>(dst->base + dst->L.T[1]) + off_d;
+    dim3 block(32, 8), grid((nx + 31) / 32, (ny + 7) / 8, 2);
+    convert_kernel<S, D><<<grid, block, 0, dst->s>>>(fs0, fs1, Ts0, Ts1, src->L.pitch, src->L.plane, fd0, fd1, Td0,
+                                                      Td1, dst->L.pitch, dst->L.plane, nx, ny, flip);
+}
+
+template <class S>
+void launch_convert_from(const lbmfvm_t *src, lbmfvm_t *dst, long long off_s, long long off_d, int nx, int ny,
+                         int flip) {
+    switch (dst->prec) {
+        case LBMFVM_F64: launch_convert<S, double>(src, dst, off_s, off_d, nx, ny, flip); break;
+        case LBMFVM_F32: launch_convert<S, float>(src, dst, off_s, off_d, nx, ny, flip); break;
+        case LBMFVM_F16: launch_convert<S, __half>(src, dst, off_s, off_d, nx, ny, flip); break;
+        case LBMFVM_BF16: launch_convert<S, __nv_bfloat16>(src, dst, off_s, off_d, nx, ny, flip); break;
+    }
 }
 
 // cuTensorMapEncodeTiled through the runtime's driver entry point (no
@@ -472,6 +539,7 @@ EncodeTiledFn encode_tiled() {
 }
 
 template <class S> constexpr CUtensorMapDataType tmap_type() { return CU_TENSOR_MAP_DATA_TYPE_FLOAT32; }
+template <> constexpr CUtensorMapDataType tmap_type<double>() { return CU_TENSOR_MAP_DATA_TYPE_FLOAT64; }
 template <> constexpr CUtensorMapDataType tmap_type<__half>() { return CU_TENSOR_MAP_DATA_TYPE_FLOAT16; }
 template <> constexpr CUtensorMapDataType tmap_type<__nv_bfloat16>() { return CU_TENSOR_MAP_DATA_TYPE_BFLOAT16; }
 
@@ -530,9 +598,17 @@ int upload_tiles(lbmfvm_t *h, int tw, int th) {
                 t.t_ref = cd.t_ref;
                 t.fx = cd.fx;
                 t.fy = cd.fy;
+                t.omega_f = (float)cd.omega;
+                t.alpha_f = (float)cd.alpha;
+                t.gbeta_f = (float)cd.gbeta;
+                t.t_ref_f = (float)cd.t_ref;
+                t.fx_f = (float)cd.fx;
+                t.fy_f = (float)cd.fy;
                 tl.push_back(t);
             }
     }
+    if (tl.size() - 1 > h->L.tile_cap)
+        return fail(h, LBMFVM_ERR_ARG, "%zu tiles exceed the list's %zu entries", tl.size() - 1, h->L.tile_cap);
     h->ntiles = (int)tl.size() - 1;
     tl[0].x0 = h->ntiles;
     // on the handle's stream, after the workspace has been cleared
@@ -550,16 +626,18 @@ CavityDesc single_cavity_desc(const lbmfvm_t *h) {
     cd.y0 = 0;
     cd.nx = h->grid.nx;
     cd.ny = h->grid.ny;
-    cd.omega = (float)(1.0 / h->tau);
-    cd.alpha = (float)h->alpha;
-    cd.gbeta = (float)h->gbeta;
-    cd.t_ref = (float)h->t_ref;
-    cd.fx = (float)h->force[0];
-    cd.fy = (float)h->force[1];
+    cd.omega = 1.0 / h->tau;
+    cd.alpha = h->alpha;
+    cd.gbeta = h->gbeta;
+    cd.t_ref = h->t_ref;
+    cd.fx = h->force[0];
+    cd.fy = h->force[1];
     for (int sd = 0; sd < 4; sd++) {
         const bool moving = h->grid.bc[sd] == LBMFVM_BC_MOVING;
-        cd.wall_u[sd] = (float)(moving && sd >= 2 ? h->grid.u_lid : 0.0);
-        cd.wall_v[sd] = (float)(moving && sd < 2 ? h->grid.u_lid : 0.0);
+        cd.wall_u[sd] = moving && sd >= 2 ? h->grid.u_lid : 0.0;
+        cd.wall_v[sd] = moving && sd < 2 ? h->grid.u_lid : 0.0;
+        cd.wall_uf[sd] = (float)cd.wall_u[sd];
+        cd.wall_vf[sd] = (float)cd.wall_v[sd];
     }
     return cd;
 }
@@ -582,9 +660,10 @@ int encode_maps(lbmfvm_t *h, int fw, int fh, int tw, int th, int cw, int ch) {
                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) return fail(h, LBMFVM_ERR_CUDA, "tensor map of the populations failed (%d)", (int)r);
         const cuuint64_t dims2[2] = {nx, ny};
-        const cuuint64_t strides2[1] = {pitch * sizeof(float)};
+        using C = typename Compute<S>::type;
+        const cuuint64_t strides2[1] = {pitch * sizeof(C)};
         const cuuint32_t box2[2] = {(cuuint32_t)tw, (cuuint32_t)th};
-        r = enc(&h->map_T[b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, h->base + h->L.T[b], dims2, strides2, box2, one,
+        r = enc(&h->map_T[b], tmap_type<C>(), 2, h->base + h->L.T[b], dims2, strides2, box2, one,
                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) return fail(h, LBMFVM_ERR_CUDA, "tensor map of the temperature failed (%d)", (int)r);
@@ -612,6 +691,7 @@ int setup_tma(lbmfvm_t *h) {
 int setup_kernels(lbmfvm_t *h) {
     if (!h->use_tma) return LBMFVM_OK;
     switch (h->prec) {
+        case LBMFVM_F64: return setup_tma<double>(h);
         case LBMFVM_F32: return setup_tma<float>(h);
         case LBMFVM_F16: return setup_tma<__half>(h);
         case LBMFVM_BF16: return setup_tma<__nv_bfloat16>(h);
@@ -652,20 +732,20 @@ int create_impl(const lbmfvm_grid_t *grid, const uint8_t *mask, double nu, doubl
     if (opts.tile_y != 0 && opts.tile_y != 4 && opts.tile_y != 8 && opts.tile_y != 16)
         return fail_thread(LBMFVM_ERR_ARG, "tile_y must be 0, 4, 8 or 16 (got %d)", opts.tile_y);
     const bool periodic = grid->bc[LBMFVM_SIDE_W] == LBMFVM_BC_PERIODIC || grid->bc[LBMFVM_SIDE_S] == LBMFVM_BC_PERIODIC;
-    const bool tma_ok = !periodic && opts.store != LBMFVM_F64;
+    const bool tma_ok = !periodic;
     if (opts.kernel < LBMFVM_KERNEL_AUTO || opts.kernel > LBMFVM_KERNEL_TMA)
         return fail_thread(LBMFVM_ERR_ARG, "kernel = %d is not a LBMFVM_KERNEL_* value", opts.kernel);
     if (opts.tma_config < 0 || opts.tma_config >= kTmaConfigs)
         return fail_thread(LBMFVM_ERR_ARG, "tma_config must be in [0, %d) (got %d)", kTmaConfigs, opts.tma_config);
     if (opts.kernel == LBMFVM_KERNEL_TMA && !tma_ok)
-        return fail_thread(LBMFVM_ERR_ARG, "the TMA kernel needs walls on every side and 32- or 16-bit storage");
+        return fail_thread(LBMFVM_ERR_ARG, "the TMA kernel needs walls on every side");
     if (!(nu > 0.0) || !std::isfinite(nu) || !(alpha > 0.0) || !std::isfinite(alpha) || !std::isfinite(gbeta))
         return fail_thread(LBMFVM_ERR_ARG, "nu and alpha must be positive and finite, gbeta finite");
     const double tau = 3.0 * nu + 0.5;
     if (tau < 0.51) return fail_thread(LBMFVM_ERR_UNSTABLE, "tau = %.6g < 0.51", tau);
     if (alpha > 0.25)
         return fail_thread(LBMFVM_ERR_UNSTABLE, "alpha = %.6g exceeds the explicit diffusion limit 0.25", alpha);
-    if (atlas && !tma_ok) return fail_thread(LBMFVM_ERR_ARG, "a batch needs 32- or 16-bit storage");
+    if (atlas && !tma_ok) return fail_thread(LBMFVM_ERR_ARG, "a batch needs walls on every side");
     const Layout L = make_layout(*grid, opts.store, atlas ? (int)atlas->cavs.size() : 1);
     if (opts.workspace && opts.workspace_bytes < L.total)
         return fail_thread(LBMFVM_ERR_NOMEM, "workspace of %zu bytes is smaller than the %zu needed",
@@ -813,6 +893,11 @@ int lbmfvm_step(lbmfvm_t *h, int64_t n) {
     if (n < 0) return fail(h, LBMFVM_ERR_ARG, "n = %lld is negative", (long long)n);
     if (n == 0) return LBMFVM_OK;
     if (int r = join_in(h)) return r;
+    // a tile list that changed size since the capture needs another grid
+    if (h->graph && h->use_tma && h->graph_blocks != tma_grid(h)) {
+        CU(h, cudaGraphExecDestroy(h->graph));
+        h->graph = nullptr;
+    }
     if (n >= kGraphSteps && !h->graph)
         if (int r = build_graph(h)) return r;
     while (n > 0) {
@@ -862,9 +947,9 @@ int lbmfvm_nusselt(lbmfvm_t *h, double *mean_hot, double *local_hot, double *mea
     CU(h, cudaGetLastError());
     double *red = reinterpret_cast<double *>(h->base + h->L.red);
     double means[2];
-    CU(h, cudaMemcpyAsync(means, red + 2 * kResidualBlocks + 6, sizeof(means), cudaMemcpyDeviceToHost, h->s));
+    CU(h, cudaMemcpyAsync(means, red + kRedNu, sizeof(means), cudaMemcpyDeviceToHost, h->s));
     if (local_hot)
-        CU(h, cudaMemcpyAsync(local_hot, red + 2 * kResidualBlocks + 8, h->grid.ny * sizeof(double),
+        CU(h, cudaMemcpyAsync(local_hot, red + kRedLocal, h->grid.ny * sizeof(double),
                               cudaMemcpyDefault, h->s));
     CU(h, cudaStreamSynchronize(h->s));
     if (mean_hot) *mean_hot = means[0];
@@ -882,7 +967,7 @@ int lbmfvm_residual(lbmfvm_t *h, double *r) {
     CU(h, cudaGetLastError());
     double sums[2];
     double *red = reinterpret_cast<double *>(h->base + h->L.red);
-    CU(h, cudaMemcpyAsync(sums, red + 2 * kResidualBlocks, sizeof(sums), cudaMemcpyDeviceToHost, h->s));
+    CU(h, cudaMemcpyAsync(sums, red + kRedTot, sizeof(sums), cudaMemcpyDeviceToHost, h->s));
     CU(h, cudaStreamSynchronize(h->s));
     if (int e = check_device_status(h)) {
         *r = NAN;
@@ -912,10 +997,32 @@ int lbmfvm_run_to_steady(lbmfvm_t *h, double tol, int64_t check_every, int64_t m
             return e;
         }
         if (r < tol) break;
+        // the residual pass left the mass total of this state in the scratch
+        if (int e = join_in(h)) return e;
+        DISPATCH(h, launch_rescale, h);
+        CU(h, cudaGetLastError());
+        if (int e = join_out(h)) return e;
     }
     if (steps_done) *steps_done = done;
     if (r_final) *r_final = r;
     return LBMFVM_OK;
+}
+
+int lbmfvm_copy_state(lbmfvm_t *dst, lbmfvm_t *src) {
+    if (!dst || !src || dst == src) return fail_thread(LBMFVM_ERR_ARG, "need two distinct handles");
+    if (dst->grid.nx != src->grid.nx || dst->grid.ny != src->grid.ny)
+        return fail(dst, LBMFVM_ERR_ARG, "grids differ: %dx%d and %dx%d", dst->grid.nx, dst->grid.ny, src->grid.nx,
+                    src->grid.ny);
+    // the source's queued steps finish before the copy reads its buffers
+    if (int r = join_in(src)) return r;
+    CU(src, cudaStreamSynchronize(src->s));
+    if (int r = join_in(dst)) return r;
+    DISPATCH(src, launch_convert_from, src, dst, 0, 0, dst->grid.nx, dst->grid.ny, src->parity ^ dst->parity);
+    CU(dst, cudaGetLastError());
+    CU(dst, cudaMemcpyAsync(dst->base + dst->L.snap, src->base + src->L.snap,
+                            2 * (size_t)dst->grid.nx * dst->grid.ny * sizeof(double), cudaMemcpyDeviceToDevice, dst->s));
+    dst->steps = src->steps;
+    return join_out(dst);
 }
 
 int lbmfvm_params(const lbmfvm_t *h, double *nu, double *alpha, double *gbeta, double *tau) {

@@ -110,10 +110,24 @@ def test_set_state_resets_one_cavity_only():
     assert np.array_equal(np.stack(b.fields(0)), np.stack(single.fields()))
 
 
+def test_fp64_batch_matches_the_oracle_to_rounding():
+    cases = small_cases()
+    b = L.Batch(cases, store="f64")
+    b.step(600)
+    for i in (0, 2, 4):
+        c = cases[i]
+        o = oracle.Oracle.from_groups(c.nx, c.ny, c.Ra, c.Pr, c.Ma, mask=c.mask)
+        o.step(600)
+        _, ug, vg, Tg = b.fields(i)
+        _, uo, vo, To = o.fields()
+        assert max(np.abs(ug - uo).max(), np.abs(vg - vo).max()) / (c.Ma / math.sqrt(3.0)) <= 1e-10
+        assert np.abs(Tg - To).max() <= 1e-10
+
+
 def test_batch_rejects_what_it_cannot_run():
     c = WL.CavityCase(64, 64, 1e4, 0.71, MA)
     with pytest.raises(L.LbmfvmError) as e:
-        L.Batch([c], store="f64")
+        L.Batch([c], store=7)
     assert e.value.code == L.LBMFVM_ERR_ARG
     bad = WL.CavityCase(512, 512, 1e3, 0.71, MA)  # alpha above the explicit limit
     with pytest.raises(L.LbmfvmError) as e:

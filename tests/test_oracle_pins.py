@@ -24,6 +24,7 @@ PINS = [
     P.energy_adiabatic,
     P.quadratic_nusselt,
     P.eq112_conduction,
+    P.homogeneous_in_f,
 ]
 
 
