@@ -77,6 +77,7 @@ extern "C" {
 #define LBMFVM_KERNEL_AUTO 0
 #define LBMFVM_KERNEL_GENERIC 1
 #define LBMFVM_KERNEL_TMA 2
+#define LBMFVM_TMA_AUTOTUNE (-1)
 
 /* Storage precision of the distributions.  F32/F16/BF16 store f - w_i and
  * compute in FP32 with FP32 temperature; F64 stores and computes in FP64. */
@@ -102,11 +103,18 @@ typedef struct {
     int32_t tile_y;         /* rows per thread block of the generic step kernel:
                                0 = default, else one of 4, 8, 16 */
     int32_t kernel;         /* LBMFVM_KERNEL_*; default AUTO */
-    int32_t tma_config;     /* tile shape of the TMA kernel, 0..3 (width x height,
-                               threads): 64x16 with 1024; 64x16 with 512 (the
-                               default, 1); 64x8 with 512 (two blocks per SM);
-                               128x8 with 1024.  Input stages: 2 (3 at 16 bit,
-                               2 for 128x8) */
+    int32_t tma_config;     /* tile shape of the TMA kernel, 0..3, or
+                               LBMFVM_TMA_AUTOTUNE.  32- and 16-bit storage
+                               (width x height, threads, input stages at 32 / 16
+                               bit): 64x16, 1024, 3/3; 64x16, 512, 3/3 (the
+                               default, 1); 64x8, 512, 2/3 (two blocks per SM);
+                               128x8, 1024, 2/3.  64-bit storage: 64x8, 256, 2;
+                               32x8, 256, 3; 32x16, 512, 2; 32x8, 256, 2 (two
+                               blocks per SM).  LBMFVM_TMA_AUTOTUNE times every
+                               shape on the handle's own grid at create and keeps
+                               the fastest (remembered per storage precision and
+                               power-of-two size class for the process); shapes
+                               never change results. */
     double t_ref;           /* reference temperature of the buoyancy term; NaN (the
                                default) selects T_l = t_wall[E] as in Eq. 81 */
     void *cuda_stream;      /* cudaStream_t the handle orders its work on; NULL =
@@ -210,6 +218,10 @@ int lbmfvm_run_to_steady(lbmfvm_t *h, double tol, int64_t check_every, int64_t m
  * after src's queued work. */
 int lbmfvm_copy_state(lbmfvm_t *dst, lbmfvm_t *src);
 
+/* Step kernel in use (LBMFVM_KERNEL_TMA or LBMFVM_KERNEL_GENERIC) and the TMA
+ * tile shape (-1 for the generic kernel); either pointer may be NULL. */
+int lbmfvm_kernel_info(const lbmfvm_t *h, int32_t *kernel, int32_t *tma_config);
+
 /* Derived lattice parameters: nu, alpha, gbeta, tau (any may be NULL). */
 int lbmfvm_params(const lbmfvm_t *h, double *nu, double *alpha, double *gbeta, double *tau);
 
@@ -294,6 +306,9 @@ int lbmfvm_batch_info(const lbmfvm_batch_t *b, int32_t i, int64_t *steps, int32_
  * r_switch).  r_switch <= 0 keeps them at prec; stall_checks <= 0 turns the
  * second rule off. */
 int lbmfvm_batch_set_polish(lbmfvm_batch_t *b, int32_t prec, double r_switch, int32_t stall_checks);
+/* TMA tile shape of the batch's packed grid in precision prec (-1 while that
+ * level of the ladder has not been created). */
+int lbmfvm_batch_kernel_info(const lbmfvm_batch_t *b, int32_t prec, int32_t *tma_config);
 /* Storage precision cavity i is currently stepped in (lbmfvm_prec). */
 int lbmfvm_batch_precision(const lbmfvm_batch_t *b, int32_t i, int32_t *prec);
 void lbmfvm_batch_destroy(lbmfvm_batch_t *b);

@@ -33,6 +33,7 @@ LBMFVM_BC_DIRICHLET, LBMFVM_BC_ADIABATIC, LBMFVM_BC_PERIODIC, LBMFVM_BC_MOVING =
 # Step kernels
 LBMFVM_KERNEL_AUTO, LBMFVM_KERNEL_GENERIC, LBMFVM_KERNEL_TMA = 0, 1, 2
 KERNELS = {"auto": LBMFVM_KERNEL_AUTO, "generic": LBMFVM_KERNEL_GENERIC, "tma": LBMFVM_KERNEL_TMA}
+LBMFVM_TMA_AUTOTUNE = -1
 # Storage precisions
 LBMFVM_F64, LBMFVM_F32, LBMFVM_F16, LBMFVM_BF16 = 0, 1, 2, 3
 PRECISIONS = {"f64": LBMFVM_F64, "f32": LBMFVM_F32, "f16": LBMFVM_F16, "bf16": LBMFVM_BF16}
@@ -41,10 +42,10 @@ PRECISIONS = {"f64": LBMFVM_F64, "f32": LBMFVM_F32, "f16": LBMFVM_F16, "bf16": L
 EXPORTS = (
     "lbmfvm_opts_default", "lbmfvm_workspace_bytes", "lbmfvm_create", "lbmfvm_create_lattice",
     "lbmfvm_set_state", "lbmfvm_step", "lbmfvm_inject_stall", "lbmfvm_step_count", "lbmfvm_fields", "lbmfvm_fields_f32",
-    "lbmfvm_nusselt", "lbmfvm_residual", "lbmfvm_run_to_steady", "lbmfvm_copy_state", "lbmfvm_params", "lbmfvm_residual_noalloc",
+    "lbmfvm_nusselt", "lbmfvm_residual", "lbmfvm_run_to_steady", "lbmfvm_copy_state", "lbmfvm_kernel_info", "lbmfvm_params", "lbmfvm_residual_noalloc",
     "lbmfvm_destroy", "lbmfvm_last_error", "lbmfvm_batch_create", "lbmfvm_batch_set_state", "lbmfvm_batch_step",
     "lbmfvm_batch_residuals", "lbmfvm_batch_run", "lbmfvm_batch_fields", "lbmfvm_batch_nusselt", "lbmfvm_batch_info",
-    "lbmfvm_batch_set_polish", "lbmfvm_batch_precision", "lbmfvm_batch_destroy", "lbmfvm_batch_last_error",
+    "lbmfvm_batch_set_polish", "lbmfvm_batch_kernel_info", "lbmfvm_batch_precision", "lbmfvm_batch_destroy", "lbmfvm_batch_last_error",
 )
 
 
@@ -98,6 +99,7 @@ def lib() -> ctypes.CDLL:
                 "lbmfvm_residual": (ctypes.c_int, [vp, dp]),
                 "lbmfvm_run_to_steady": (ctypes.c_int, [vp, d, i64, i64, i64p, dp]),
                 "lbmfvm_copy_state": (ctypes.c_int, [vp, vp]),
+                "lbmfvm_kernel_info": (ctypes.c_int, [vp, ctypes.POINTER(i32), ctypes.POINTER(i32)]),
                 "lbmfvm_params": (ctypes.c_int, [vp, dp, dp, dp, dp]),
                 "lbmfvm_residual_noalloc": (ctypes.c_int, [vp, vp, vp, vp, vp, i64, vp, dp]),
                 "lbmfvm_destroy": (None, [vp]),
@@ -112,6 +114,7 @@ def lib() -> ctypes.CDLL:
                 "lbmfvm_batch_info": (ctypes.c_int, [vp, i32, i64p, ctypes.POINTER(i32), vp]),
                 "lbmfvm_batch_set_polish": (ctypes.c_int, [vp, i32, d, i32]),
                 "lbmfvm_batch_precision": (ctypes.c_int, [vp, i32, ctypes.POINTER(i32)]),
+                "lbmfvm_batch_kernel_info": (ctypes.c_int, [vp, i32, ctypes.POINTER(i32)]),
                 "lbmfvm_batch_destroy": (None, [vp]),
                 "lbmfvm_batch_last_error": (ctypes.c_char_p, [vp]),
             }
@@ -223,6 +226,16 @@ def lbmfvm_run_to_steady(h, tol=1e-8, check_every=1000, max_steps=10**8):
     return done.value, r.value
 
 
+def lbmfvm_kernel_info(h):
+    k, c = ctypes.c_int32(), ctypes.c_int32()
+    _check(lib().lbmfvm_kernel_info(h, ctypes.byref(k), ctypes.byref(c)), h)
+    return k.value, c.value
+
+
+def _tma_config(cfg):
+    return LBMFVM_TMA_AUTOTUNE if cfg == "auto" else int(cfg)
+
+
 def lbmfvm_copy_state(dst, src):
     _check(lib().lbmfvm_copy_state(dst, src), dst)
 
@@ -273,7 +286,7 @@ class Cavity:
         self.opts.store = PRECISIONS[store] if isinstance(store, str) else int(store)
         self.opts.tile_y = int(tile_y)
         self.opts.kernel = KERNELS[kernel] if isinstance(kernel, str) else int(kernel)
-        self.opts.tma_config = int(tma_config)
+        self.opts.tma_config = _tma_config(tma_config)
         self.opts.t_ref = math.nan if t_ref is None else float(t_ref)
         dev = torch.device("cuda" if device is None else device)
         self.device = dev
@@ -333,6 +346,11 @@ class Cavity:
     def run_to_steady(self, tol=1e-8, check_every=1000, max_steps=10**8):
         return lbmfvm_run_to_steady(self.h, tol, check_every, max_steps)
 
+    @property
+    def tma_config(self):
+        """TMA tile shape in use (-1 on the generic kernel)."""
+        return lbmfvm_kernel_info(self.h)[1]
+
     def copy_state_from(self, other: "Cavity"):
         """Take ``other``'s state (populations, temperature, step count,
         residual snapshot), converted to this cavity's storage precision."""
@@ -354,7 +372,7 @@ class Batch:
     PyTorch's current stream.
     """
 
-    def __init__(self, cases, store="f32", tma_config=1, device=None):
+    def __init__(self, cases, store="f32", tma_config="auto", device=None):
         import torch
 
         self.n = len(cases)
@@ -369,7 +387,7 @@ class Batch:
         ra, pr, ma = arr([c.Ra for c in cases]), arr([c.Pr for c in cases]), arr([c.Ma for c in cases])
         self.opts = lbmfvm_opts_default()
         self.opts.store = PRECISIONS[store] if isinstance(store, str) else int(store)
-        self.opts.tma_config = int(tma_config)
+        self.opts.tma_config = _tma_config(tma_config)
         dev = torch.device("cuda" if device is None else device)
         self.opts.cuda_stream = torch.cuda.current_stream(dev).cuda_stream
         self.b = ctypes.c_void_p()
@@ -434,6 +452,13 @@ class Batch:
         checks without halving that also do (<= 0: off)."""
         p = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
         _bcheck(lib().lbmfvm_batch_set_polish(self.b, p, float(r_switch), int(stall_checks)), self.b)
+
+    def tma_config(self, prec):
+        """TMA tile shape of the packed grid in ``prec`` (-1 before it exists)."""
+        p = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
+        c = ctypes.c_int32()
+        _bcheck(lib().lbmfvm_batch_kernel_info(self.b, p, ctypes.byref(c)), self.b)
+        return c.value
 
     def precision(self, i):
         """Storage precision cavity i is stepped in ("f32", "f16" or "bf16")."""

@@ -663,6 +663,14 @@ int lbmfvm_batch_set_polish(lbmfvm_batch_t *b, int32_t prec, double r_switch, in
     return bfail(b, LBMFVM_ERR_ARG, "precision %d is not a level of this batch's ladder below its top", prec);
 }
 
+int lbmfvm_batch_kernel_info(const lbmfvm_batch_t *b, int32_t prec, int32_t *tma_config) {
+    if (!b || !tma_config) return fail_thread(LBMFVM_ERR_ARG, "batch or tma_config is NULL");
+    *tma_config = -1;
+    for (int l = 0; l < b->nlv; l++)
+        if (b->prec[l] == prec && b->lv[l]) *tma_config = b->lv[l]->tma_config;
+    return LBMFVM_OK;
+}
+
 int lbmfvm_batch_precision(const lbmfvm_batch_t *b, int32_t i, int32_t *prec) {
     if (!b || !prec) return fail_thread(LBMFVM_ERR_ARG, "batch or prec is NULL");
     if (i < 0 || i >= (int)b->cav.size()) return fail_thread(LBMFVM_ERR_ARG, "cavity index %d out of range", i);

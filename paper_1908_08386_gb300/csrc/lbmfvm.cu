@@ -12,6 +12,8 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <type_traits>
 #include <vector>
@@ -712,6 +714,86 @@ int check_device_status(lbmfvm_t *h) {
     return LBMFVM_OK;
 }
 
+// Autotuner of the TMA tile shape.  Each shape steps the handle's own grid
+// (from the cleared workspace, which is the rest state f = w_i, T = 0) a few
+// times; the fastest is kept and remembered for the storage precision and the
+// size class (the power of two of the nodes the tiles cover), so a class is
+// measured once per process.  Every shape computes the same arithmetic per
+// node, so the choice never changes results.  The population and temperature
+// buffers are cleared again afterwards.
+constexpr int kTuneSteps = 10;
+std::mutex g_tune_mu;
+std::map<std::pair<int, int>, int> g_tuned;
+
+int size_class(const lbmfvm_t *h) {
+    long long n = 0;
+    if (h->atlas_cavs.empty()) {
+        n = (long long)h->grid.nx * h->grid.ny;
+    } else {
+        for (size_t c = 0; c < h->atlas_cavs.size(); c++) n += (long long)h->atlas_cavs[c].nx * h->atlas_cavs[c].ny;
+    }
+    int cls = 0;
+    while ((n >>= 1) > 0) cls++;
+    return cls;
+}
+
+int autotune(lbmfvm_t *h) {
+    const std::pair<int, int> key(h->prec, size_class(h));
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        auto it = g_tuned.find(key);
+        if (it != g_tuned.end()) {
+            h->tma_config = it->second;
+            return setup_kernels(h);
+        }
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CU(h, cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return fail(h, LBMFVM_ERR_CUDA, "event creation failed");
+    }
+    int best = -1;
+    float best_ms = 0.0f;
+    int status = LBMFVM_OK;
+    for (int cfg = 0; cfg < kTmaConfigs && status == LBMFVM_OK; cfg++) {
+        h->tma_config = cfg;
+        if (setup_kernels(h) != LBMFVM_OK) continue;  // a shape that does not fit this device
+        for (int i = 0; i < 2; i++) launch_one(h, i & 1, h->s);
+        cudaEventRecord(e0, h->s);
+        for (int i = 0; i < kTuneSteps; i++) launch_one(h, i & 1, h->s);
+        cudaEventRecord(e1, h->s);
+        float ms = 0.0f;
+        cudaError_t e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) {
+            status = fail(h, LBMFVM_ERR_CUDA, "autotuning failed: %s", cudaGetErrorString(e));
+            break;
+        }
+        if (best < 0 || ms < best_ms) {
+            best = cfg;
+            best_ms = ms;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (status != LBMFVM_OK) return status;
+    if (best < 0) return fail(h, LBMFVM_ERR_CUDA, "no TMA tile shape fits this device");
+    h->tma_config = best;
+    if (int r = setup_kernels(h)) return r;
+    if (int r = check_device_status(h)) return r;
+    const size_t fbytes = 9 * (size_t)h->L.plane * store_size(h->prec);
+    const size_t tbytes = (size_t)h->L.plane * (h->prec == LBMFVM_F64 ? 8 : 4);
+    for (int b = 0; b < 2; b++) {
+        CU(h, cudaMemsetAsync(h->base + h->L.f[b], 0, fbytes, h->s));
+        CU(h, cudaMemsetAsync(h->base + h->L.T[b], 0, tbytes, h->s));
+    }
+    CU(h, cudaStreamSynchronize(h->s));
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tuned[key] = best;
+    return LBMFVM_OK;
+}
+
 // Several cavities packed in one grid: their descriptors (rectangles starting
 // on 128 x 16 slot corners, lattice parameters) and the packed node codes.
 struct AtlasSpec {
@@ -735,8 +817,9 @@ int create_impl(const lbmfvm_grid_t *grid, const uint8_t *mask, double nu, doubl
     const bool tma_ok = !periodic;
     if (opts.kernel < LBMFVM_KERNEL_AUTO || opts.kernel > LBMFVM_KERNEL_TMA)
         return fail_thread(LBMFVM_ERR_ARG, "kernel = %d is not a LBMFVM_KERNEL_* value", opts.kernel);
-    if (opts.tma_config < 0 || opts.tma_config >= kTmaConfigs)
-        return fail_thread(LBMFVM_ERR_ARG, "tma_config must be in [0, %d) (got %d)", kTmaConfigs, opts.tma_config);
+    if (opts.tma_config != LBMFVM_TMA_AUTOTUNE && (opts.tma_config < 0 || opts.tma_config >= kTmaConfigs))
+        return fail_thread(LBMFVM_ERR_ARG, "tma_config must be LBMFVM_TMA_AUTOTUNE or in [0, %d) (got %d)",
+                           kTmaConfigs, opts.tma_config);
     if (opts.kernel == LBMFVM_KERNEL_TMA && !tma_ok)
         return fail_thread(LBMFVM_ERR_ARG, "the TMA kernel needs walls on every side");
     if (!(nu > 0.0) || !std::isfinite(nu) || !(alpha > 0.0) || !std::isfinite(alpha) || !std::isfinite(gbeta))
@@ -759,7 +842,7 @@ int create_impl(const lbmfvm_grid_t *grid, const uint8_t *mask, double nu, doubl
     h->prec = opts.store;
     h->tile_y = opts.tile_y ? opts.tile_y : 8;
     h->use_tma = tma_ok && opts.kernel != LBMFVM_KERNEL_GENERIC;
-    h->tma_config = opts.tma_config;
+    h->tma_config = opts.tma_config == LBMFVM_TMA_AUTOTUNE ? 1 : opts.tma_config;
     h->L = L;
     h->nu = nu;
     h->alpha = alpha;
@@ -809,6 +892,8 @@ int create_impl(const lbmfvm_grid_t *grid, const uint8_t *mask, double nu, doubl
         return bail(LBMFVM_ERR_CUDA);
     }
     if (int r = setup_kernels(h)) return bail(r);
+    if (h->use_tma && opts.tma_config == LBMFVM_TMA_AUTOTUNE)
+        if (int r = autotune(h)) return bail(r);
     if (!atlas)
         if (int r = set_state_impl(h, nullptr, nullptr, nullptr)) return bail(r);
     *out = h;
@@ -1023,6 +1108,13 @@ int lbmfvm_copy_state(lbmfvm_t *dst, lbmfvm_t *src) {
                             2 * (size_t)dst->grid.nx * dst->grid.ny * sizeof(double), cudaMemcpyDeviceToDevice, dst->s));
     dst->steps = src->steps;
     return join_out(dst);
+}
+
+int lbmfvm_kernel_info(const lbmfvm_t *h, int32_t *kernel, int32_t *tma_config) {
+    if (!h) return fail_thread(LBMFVM_ERR_ARG, "handle is NULL");
+    if (kernel) *kernel = h->use_tma ? LBMFVM_KERNEL_TMA : LBMFVM_KERNEL_GENERIC;
+    if (tma_config) *tma_config = h->use_tma ? h->tma_config : -1;
+    return LBMFVM_OK;
 }
 
 int lbmfvm_params(const lbmfvm_t *h, double *nu, double *alpha, double *gbeta, double *tau) {

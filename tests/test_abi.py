@@ -94,3 +94,20 @@ def test_null_handle_calls_fail_cleanly():
     assert lib.lbmfvm_step(None, 1) == L.LBMFVM_ERR_ARG
     assert lib.lbmfvm_set_state(None, None, None, None) == L.LBMFVM_ERR_ARG
     lib.lbmfvm_destroy(None)
+
+
+@pytest.mark.parametrize("cfg", [-2, 4, 99])
+def test_rejects_unknown_tile_shapes(cfg):
+    o = L.lbmfvm_opts_default()
+    o.tma_config = cfg
+    with pytest.raises(L.LbmfvmError) as e:
+        L.lbmfvm_create_lattice(L.make_grid(64, 64), None, 0.1, 0.1, 0.0, None, o)
+    assert e.value.code == L.LBMFVM_ERR_ARG
+    assert "tma_config" in L.lbmfvm_last_error()
+
+
+def test_null_handle_queries_fail_cleanly():
+    lib = L.lib()
+    assert lib.lbmfvm_kernel_info(None, None, None) == L.LBMFVM_ERR_ARG
+    assert lib.lbmfvm_copy_state(None, None) == L.LBMFVM_ERR_ARG
+    assert lib.lbmfvm_batch_set_polish(None, L.LBMFVM_F32, 1e-6, 0) == L.LBMFVM_ERR_ARG

@@ -133,3 +133,20 @@ def test_batch_rejects_what_it_cannot_run():
     with pytest.raises(L.LbmfvmError) as e:
         L.Batch([c, bad])
     assert e.value.code == L.LBMFVM_ERR_UNSTABLE
+
+
+def test_autotuned_shapes_change_no_result():
+    # the autotuner picks a shape per precision and size class; every shape
+    # computes the same arithmetic per node
+    case = WL.CavityCase(150, 72, 1e5, 0.71, MA)
+    fixed = L.Cavity(case.nx, case.ny, Ra=case.Ra, Pr=case.Pr, Ma=case.Ma, store="f32", kernel="tma", tma_config=1)
+    tuned = L.Cavity(case.nx, case.ny, Ra=case.Ra, Pr=case.Pr, Ma=case.Ma, store="f32", kernel="tma",
+                     tma_config="auto")
+    again = L.Cavity(case.nx, case.ny, Ra=case.Ra, Pr=case.Pr, Ma=case.Ma, store="f32", kernel="tma",
+                     tma_config="auto")
+    assert 0 <= tuned.tma_config <= 3 and again.tma_config == tuned.tma_config  # remembered per class
+    for c in (fixed, tuned):
+        c.step(300)
+    assert np.array_equal(np.stack(tuned.fields()), np.stack(fixed.fields()))
+    b = L.Batch(small_cases(), store="f16")  # autotuned by default
+    assert 0 <= b.tma_config("f16") <= 3 and b.tma_config("f32") == -1  # upper levels not created yet
