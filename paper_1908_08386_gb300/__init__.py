@@ -407,8 +407,11 @@ class Batch:
             pass
 
     def set_state(self, i, u=None, v=None, T=None):
+        """Initial (u, v, T) of cavity i: host arrays or float32 device tensors
+        of ny x nx values (None: rest, t_init)."""
         ny, nx = self.shapes[i]
-        conv = lambda a: None if a is None else np.ascontiguousarray(a, dtype=np.float32).reshape(ny, nx)
+        conv = lambda a: None if a is None else (a if hasattr(a, "data_ptr") else
+                                                np.ascontiguousarray(a, dtype=np.float32).reshape(ny, nx))
         u, v, T = conv(u), conv(v), conv(T)
         _bcheck(lib().lbmfvm_batch_set_state(self.b, int(i), _addr(u), _addr(v), _addr(T)), self.b)
 

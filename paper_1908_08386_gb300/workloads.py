@@ -98,9 +98,11 @@ def cavity_batch(count: int, seed: int, sizes=(64, 96, 128, 192, 256, 384, 512),
                  aspect=(1, 2)) -> list[CavityCase]:
     """Uneven cavities: side N from `sizes`, aspect ratio 1 or 2 (ny = N,
     nx = a (N - 1) + 1), log10 Ra uniform in [3, 6], Pr in {0.71, 7.0}, up to
-    three obstacles.  U0 = min(0.1, 0.2 sqrt(Ra Pr)/H) keeps the thermal
-    diffusivity at or below 0.2; a size whose relaxation time would fall below
-    0.51 is redrawn from the larger sizes."""
+    three obstacles.  U0 = min(0.1, 0.2 sqrt(Ra Pr)/H, 1.8 H/sqrt(Ra Pr))
+    keeps the thermal diffusivity alpha = U0 H/sqrt(Ra Pr) at or below 0.2 and
+    U0^2 below 2 alpha (the stability conditions of the explicit central FV
+    update); a size whose relaxation time would fall below 0.51 is redrawn
+    from the larger sizes."""
     rng = np.random.default_rng(seed)
     out = []
     sizes = sorted(sizes)
@@ -112,7 +114,7 @@ def cavity_batch(count: int, seed: int, sizes=(64, 96, 128, 192, 256, 384, 512),
         Pr = float(rng.choice([0.71, 7.0]))
         while True:
             H = N - 1
-            U0 = min(0.1, 0.2 * math.sqrt(Ra * Pr) / H)
+            U0 = min(0.1, 0.2 * math.sqrt(Ra * Pr) / H, 1.8 * H / math.sqrt(Ra * Pr))
             tau = 3.0 * U0 * H * math.sqrt(Pr / Ra) + 0.5
             bigger = [s for s in sizes if s > N]
             if tau >= 0.51 or not bigger:
@@ -125,4 +127,38 @@ def cavity_batch(count: int, seed: int, sizes=(64, 96, 128, 192, 256, 384, 512),
             if shapes:
                 mask = rasterize(shapes, nx, ny)
         out.append(CavityCase(nx, ny, Ra, Pr, U0 * math.sqrt(3.0), 0, mask, 0.5, name=f"c{i}_N{N}_a{a}"))
+    return out
+
+
+def warm_start_cases(count: int = 2000, seed: int = 20190823) -> list[CavityCase]:
+    """Training cavities of the learned warm start: the uneven-batch recipe at
+    N = 128 with aspect ratio 1 (Ra log-uniform in [1e3, 1e6], Pr in
+    {0.71, 7.0}, up to three obstacles)."""
+    return cavity_batch(count, seed, sizes=(128,), aspect=(1,))
+
+
+def surrogate_init(widths=(32, 64, 96, 160), seed: int = 0, cin: int = 3, cout: int = 3) -> list[np.ndarray]:
+    """Seeded initial parameters of the warm-start network, in the order and
+    shapes of its layers: per encoder level two 3x3 convolutions (weights
+    [Co, 3, 3, Ci], biases [Co]), per decoder level (coarse to fine) two more,
+    then the 1x1 output layer ([Co, Ci], [Co]).  He-normal weights
+    (std sqrt(2 / fan_in)), zero biases, a small output layer."""
+    rng = np.random.default_rng(seed)
+    shapes = []
+    c = cin
+    for w in widths:
+        shapes += [(w, 3, 3, c), (w,), (w, 3, 3, w), (w,)]
+        c = w
+    for lvl in range(len(widths) - 2, -1, -1):
+        w = widths[lvl]
+        shapes += [(w, 3, 3, widths[lvl + 1] + w), (w,), (w, 3, 3, w), (w,)]
+    shapes += [(cout, widths[0]), (cout,)]
+    out = []
+    for s in shapes:
+        if len(s) == 1:
+            out.append(np.zeros(s))
+        elif len(s) == 2:
+            out.append(rng.standard_normal(s) * 0.01)
+        else:
+            out.append(rng.standard_normal(s) * math.sqrt(2.0 / (9 * s[3])))
     return out

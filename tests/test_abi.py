@@ -111,3 +111,26 @@ def test_null_handle_queries_fail_cleanly():
     assert lib.lbmfvm_kernel_info(None, None, None) == L.LBMFVM_ERR_ARG
     assert lib.lbmfvm_copy_state(None, None) == L.LBMFVM_ERR_ARG
     assert lib.lbmfvm_batch_set_polish(None, L.LBMFVM_F32, 1e-6, 0) == L.LBMFVM_ERR_ARG
+
+
+SG_HEADER = os.path.join(os.path.dirname(os.path.dirname(__file__)), "include", "surrogate.h")
+
+
+def test_surrogate_header_matches_its_binding_and_the_library():
+    from paper_1908_08386_gb300 import surrogate as S
+
+    text = re.sub(r"/\*.*?\*/", "", open(SG_HEADER).read(), flags=re.S)
+    declared = sorted(set(re.findall(r"\b(lbmfvm_sg_[a-z0-9_]+)\s*\(", text)))
+    assert declared == sorted(S.SG_EXPORTS)
+    lib = L.lib()
+    assert not [n for n in declared if not hasattr(lib, n)]
+
+
+def test_surrogate_entry_points_check_shapes_without_a_gpu():
+    from paper_1908_08386_gb300 import surrogate as S
+
+    lib = S._lib()
+    # H not a multiple of 8: refused before any launch
+    assert lib.lbmfvm_sg_conv3x3(16, 16, 16, None, 16, 32, None, 0, 1, 12, 16, 16, 32, 1, None) == -1
+    assert "tile rules" in lib.lbmfvm_sg_last_error().decode()
+    assert lib.lbmfvm_sg_adam(None, None, None, None, None, 10, 1e-3, 0.9, 0.999, 1e-8, 1, None) == -1

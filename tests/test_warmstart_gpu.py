@@ -1,0 +1,80 @@
+"""The trained warm start against the method without it (GPU).
+
+The iteration started from the network's prediction must reach the same
+residual and the same steady Nusselt number as from rest, in fewer steps; an
+untrained network of the same shape does not help.  The held-out cavities are
+the last 200 of the 2000 training recipes, which the network never saw.
+"""
+
+import math
+import os
+
+import numpy as np
+import pytest
+
+import paper_1908_08386_gb300 as L
+from paper_1908_08386_gb300 import surrogate as S
+from paper_1908_08386_gb300 import warmstart as W
+from paper_1908_08386_gb300 import workloads as WL
+
+pytestmark = pytest.mark.gpu
+
+WEIGHTS = os.path.join(os.path.dirname(L.__file__), "data", "warmstart_128.npz")
+
+
+def held_out(k):
+    return WL.warm_start_cases(2000)[1800:1800 + k]
+
+
+def run(cases, net, tol=1e-6):
+    b = L.Batch(cases, store="f32")
+    b.set_polish("f32", 0)
+    if net is not None:
+        W.warm_start(b, net, cases)
+    steps, r = b.run(tol=tol, check_every=500, max_steps=600000)
+    nus = np.array([b.nusselt(i)[0] for i in range(len(cases))])
+    return steps, r, nus
+
+
+def test_trained_network_saves_steps_and_keeps_the_steady_state():
+    cases = held_out(12)
+    net = S.Surrogate.load(WEIGHTS)
+    cold, rc, nu_cold = run(cases, None)
+    warm, rw, nu_warm = run(cases, net)
+    assert (rc < 1e-6).all() and (rw < 1e-6).all()
+    # same steady state, to the accuracy a 1e-6 residual leaves
+    assert np.abs(nu_warm - nu_cold).max() <= 1e-2 * np.abs(nu_cold).max()
+    assert warm.sum() <= 0.92 * cold.sum(), (warm.sum(), cold.sum())
+    untrained = S.Surrogate(net.widths, seed=3)
+    blind, rb, _ = run(cases, untrained)
+    assert (rb < 1e-6).all()
+    assert warm.sum() < blind.sum(), (warm.sum(), blind.sum())
+
+
+def test_prediction_beats_the_rest_state_on_held_out_cavities():
+    cases = held_out(8)
+    targets, _, _ = W.generate(cases, tol=1e-6, log=lambda *a: None)
+    data = W.Dataset(cases, targets)
+    net = S.Surrogate.load(WEIGHTS)
+    pred = W.predict(net, data, list(range(len(cases))))
+    _, _, fluid = W.case_arrays(cases)
+    eT, eu = W.errors(pred, targets, fluid)
+    rest = np.zeros_like(pred)
+    rest[..., 2] = 0.5
+    rT, ru = W.errors(rest, targets, fluid)
+    assert eT <= 0.5 * rT and eu <= 0.5 * ru, (eT, rT, eu, ru)
+
+
+def test_cavities_off_the_network_grid_start_from_resampled_predictions():
+    # aspect 2 and a finer grid: the prediction is resampled both ways
+    cases = [WL.CavityCase(191, 96, 3e4, 0.71, 0.1 * math.sqrt(3.0), name="wide"),
+             WL.CavityCase(160, 160, 1e5, 7.0, 0.1 * math.sqrt(3.0), name="fine")]
+    cases[1].mask = WL.rasterize([("circle", 100.0, 60.0, 15.0)], 160, 160)
+    net = S.Surrogate.load(WEIGHTS)
+    (u, v, T), _ = W.initial_states(net, cases)
+    un, Tn = u.cpu().numpy(), T.cpu().numpy()
+    assert un.shape == (96, 191) and Tn.min() >= 0 and Tn.max() <= 1
+    assert np.all(un[0, :] == 0) and np.all(un[:, 0] == 0)
+    cold, _, nu_cold = run(cases, None)
+    warm, _, nu_warm = run(cases, net)
+    assert np.abs(nu_warm - nu_cold).max() <= 1e-2 * np.abs(nu_cold).max()
