@@ -42,7 +42,7 @@ FALLBACK_HBM_GBS = 6800.0
 
 # DRAM bytes per launch of step_kernel from one ncu capture
 # (profiles/step_kernel_*.md), valid only for the kernel source hashed here.
-NCU_TRAFFIC = {("f32", 4096, "979f9e42e052ec75"): 1344.1e6}
+NCU_TRAFFIC = {("f32", 4096, "8748432a09d92838"): 1335.3e6}
 
 
 def kernel_hash() -> str:

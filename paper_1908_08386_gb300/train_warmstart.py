@@ -85,7 +85,7 @@ def main(argv=None):
     report["rest_T_rms"], report["rest_u_rel_rms"] = W.errors(rest, tg, fluid)
     net.save(a.out)
     ev = cases[a.train:a.train + a.eval_cavities]
-    for tol in (1e-6,):
+    for tol in ((1e-6,) if ev else ()):
         sc, rc, tc, nc = steps_to_residual(ev, net, tol, warm=False)
         sw, rw, tw, nw = steps_to_residual(ev, net, tol, warm=True)
         report[f"steps_cold_{tol:g}"] = [int(x) for x in sc]
