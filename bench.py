@@ -314,8 +314,53 @@ def run_ours(args):
     print(json.dumps(line), flush=True)
 
 
+def run_steady(args):
+    """Time to steady state (residual below --tol) of a seeded draw of uneven
+    cavities: the fast form (one batch, 16-bit storage on the precision
+    ladder, learned warm start) against the plain per-cavity FP32 loop; one
+    JSON line."""
+    import numpy as np
+    import torch
+
+    from paper_1908_08386_gb300 import steady, surrogate, workloads
+
+    sizes = tuple(int(s) for s in args.sizes.split(","))
+    cases = workloads.cavity_batch(args.cavities, args.seed, sizes=sizes)
+    nodes = sum(c.nx * c.ny for c in cases)
+    weights = os.path.join(ROOT, "paper_1908_08386_gb300", "data", "warmstart_128.npz")
+    net = None if args.no_warm else surrogate.Surrogate.load(weights)
+    torch.cuda.synchronize()
+    fast_s, fast_steps, fast_r, fast_nu = steady.fast_form(cases, net, store=args.store_fast, tol=args.tol)
+    line = {"metric": f"time to steady state (residual < {args.tol:g}) of {len(cases)} uneven cavities",
+            "value": fast_s, "unit": "s", "n_gpus": 1, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": args.store_fast, "data": "synthetic",
+            "config": {"workload": f"uneven cavities, seed {args.seed}, sides {sizes}, aspect 1/2, Ra 1e3-1e6, "
+                                   f"Pr 0.71/7, 0-3 obstacles", "cavities": len(cases), "nodes": nodes,
+                       "fast_form": f"one batch, {args.store_fast} storage on the precision ladder"
+                                    + ("" if args.no_warm else ", learned warm start"),
+                       "fast_steps_max": int(fast_steps.max()), "fast_steps_sum": int(fast_steps.sum()),
+                       "fast_residual_max": float(np.max(fast_r))}}
+    if not args.no_plain:
+        plain_s, plain_steps, plain_r, plain_nu = steady.plain_loop(cases, tol=args.tol)
+        line["plain_fp32_loop_s"] = plain_s
+        line["speedup_vs_plain"] = plain_s / fast_s
+        line["config"]["plain_steps_sum"] = int(plain_steps.sum())
+        line["config"]["plain_residual_max"] = float(np.max(plain_r))
+        line["nu_max_rel_diff_vs_plain"] = float(np.max(np.abs(fast_nu - plain_nu) / np.abs(plain_nu)))
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--workload", choices=["step", "steady"], default="step",
+                    help="step: MLUPS of the fused step (default); steady: time to steady state of uneven cavities")
+    ap.add_argument("--cavities", type=int, default=64)
+    ap.add_argument("--sizes", default="64,96,128,192,256,384,512")
+    ap.add_argument("--seed", type=int, default=20190822)
+    ap.add_argument("--tol", type=float, default=1e-8)
+    ap.add_argument("--store-fast", choices=["f16", "bf16", "f32"], default="f16")
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-warm", action="store_true")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
@@ -333,6 +378,8 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "steady":
+        run_steady(args)
     else:
         run_ours(args)
 
