@@ -35,7 +35,8 @@ sys.path.insert(0, ROOT)
 METRIC = "coupled MLUPS (1024^2 cavity, Ra 1e6) & % HBM peak"
 # Algorithmic bytes per lattice update of the fused step: read + write the
 # nine populations, read + write T, read the node code.
-BYTES_PER_LU = {"f64": 72 + 72 + 8 + 8 + 1, "f32": 36 + 36 + 4 + 4 + 1, "f16": 18 + 18 + 4 + 4 + 1,
+BYTES_PER_LU = {"f64": 72 + 72 + 8 + 8 + 1, "f32x2": 72 + 72 + 8 + 8 + 1, "f32": 36 + 36 + 4 + 4 + 1,
+                "f16": 18 + 18 + 4 + 4 + 1,
                 "bf16": 18 + 18 + 4 + 4 + 1}
 L2_FLUSH_BYTES = 512 << 20
 FALLBACK_HBM_GBS = 6800.0
@@ -368,7 +369,7 @@ def main():
     ap.add_argument("--size", type=int, default=1024)
     ap.add_argument("--ra", type=float, default=1e6, help="Rayleigh number (1e7 keeps 4096^2 stable)")
     ap.add_argument("--chunk", type=int, default=1000, help="coupled steps per benchmark step")
-    ap.add_argument("--store", choices=["f32", "f16", "bf16", "f64"], default="f32")
+    ap.add_argument("--store", choices=["f32", "f16", "bf16", "f64", "f32x2"], default="f32")
     ap.add_argument("--kernel", choices=["auto", "tma", "generic"], default="auto")
     ap.add_argument("--tma-config", type=int, default=1)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)

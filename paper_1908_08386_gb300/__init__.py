@@ -35,8 +35,9 @@ LBMFVM_KERNEL_AUTO, LBMFVM_KERNEL_GENERIC, LBMFVM_KERNEL_TMA = 0, 1, 2
 KERNELS = {"auto": LBMFVM_KERNEL_AUTO, "generic": LBMFVM_KERNEL_GENERIC, "tma": LBMFVM_KERNEL_TMA}
 LBMFVM_TMA_AUTOTUNE = -1
 # Storage precisions
-LBMFVM_F64, LBMFVM_F32, LBMFVM_F16, LBMFVM_BF16 = 0, 1, 2, 3
-PRECISIONS = {"f64": LBMFVM_F64, "f32": LBMFVM_F32, "f16": LBMFVM_F16, "bf16": LBMFVM_BF16}
+LBMFVM_F64, LBMFVM_F32, LBMFVM_F16, LBMFVM_BF16, LBMFVM_F32X2 = 0, 1, 2, 3, 4
+PRECISIONS = {"f64": LBMFVM_F64, "f32": LBMFVM_F32, "f16": LBMFVM_F16, "bf16": LBMFVM_BF16,
+              "f32x2": LBMFVM_F32X2}
 
 # Every entry point the header declares (checked by the test-suite).
 EXPORTS = (

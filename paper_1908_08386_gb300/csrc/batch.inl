@@ -15,7 +15,9 @@
 // storage grid the batch keeps packed grids of the wider precisions with the
 // same slots (FP32, then FP64), created when first needed; a cavity whose
 // residual reaches its level's switch value, or stops falling, is converted
-// into the next grid and stepped there from then on.
+// into the next grid and stepped there from then on.  The top of the ladder
+// is double-single storage and arithmetic (FP64-like precision on the FP32
+// units).
 
 struct lbmfvm_batch {
     lbmfvm_t *a = nullptr;          // the storage grid (memory, stream, kernels); lv[0]
@@ -183,6 +185,7 @@ void launch_cav_fields(lbmfvm_batch_t *b, int i, int which, O *o0, O *o1) {
             case LBMFVM_F32: FN<float>(__VA_ARGS__); break;           \
             case LBMFVM_F16: FN<__half>(__VA_ARGS__); break;          \
             case LBMFVM_BF16: FN<__nv_bfloat16>(__VA_ARGS__); break;  \
+            case LBMFVM_F32X2: FN<dsf>(__VA_ARGS__); break;           \
         }                                                             \
     } while (0)
 
@@ -470,8 +473,8 @@ int lbmfvm_batch_create(int32_t n, const lbmfvm_grid_t *grids, const uint8_t *co
         b->stall_checks[b->nlv - 1] = 16;
         b->nlv++;
     }
-    if (o.store != LBMFVM_F64) {
-        b->prec[b->nlv] = LBMFVM_F64;
+    if (o.store != LBMFVM_F64 && o.store != LBMFVM_F32X2) {
+        b->prec[b->nlv] = LBMFVM_F32X2;
         b->switch_r[b->nlv - 1] = 1e-6;
         b->stall_checks[b->nlv - 1] = 32;
         b->nlv++;
@@ -604,6 +607,7 @@ int lbmfvm_batch_fields(lbmfvm_batch_t *b, int32_t i, double *rho, double *u, do
             case LBMFVM_F32: launch_cav_fields<float, double>(b, i, which, st, st + n); break;
             case LBMFVM_F16: launch_cav_fields<__half, double>(b, i, which, st, st + n); break;
             case LBMFVM_BF16: launch_cav_fields<__nv_bfloat16, double>(b, i, which, st, st + n); break;
+            case LBMFVM_F32X2: launch_cav_fields<dsf, double>(b, i, which, st, st + n); break;
         }
         e = cudaGetLastError();
         for (int k = 0; k < 2 && e == cudaSuccess; k++)

@@ -72,7 +72,66 @@ __host__ __device__ constexpr C wq(int q) {
     return q == 0 ? C(4) / C(9) : (q < 5 ? C(1) / C(9) : C(1) / C(36));
 }
 
+// ---------------------------------------------------------------------------
+// Double-single numbers: a value held as the unevaluated sum hi + lo of two
+// FP32 numbers (|lo| <= half an ulp of hi), about 48 significant bits,
+// computed on the FP32 units.  On this GPU the FP32 units outnumber the
+// FP64 ones many times over, so the last stage of a run to a tight residual
+// (where FP32 storage and arithmetic leave a rounding floor near 2e-7) runs
+// in double-single rather than FP64.  The operations are the error-free
+// transformations of floating-point arithmetic: the two-sum of Knuth (exact
+// sum and rounding error of two floats), the fast two-sum of Dekker (the same
+// when |a| >= |b|) and the two-product from a fused multiply-add (exact
+// product and rounding error); additions accumulate the low parts and
+// renormalise once (error a few units of 2^-44 of the operands).  The
+// intrinsics __fadd_rn/__fmul_rn keep the compiler from contracting these
+// sequences into fused operations, which would break their exactness.
+// ---------------------------------------------------------------------------
+struct __align__(8) dsf {
+    float hi, lo;
+    dsf() = default;
+    __host__ __device__ constexpr dsf(float h, float l) : hi(h), lo(l) {}
+    __host__ __device__ constexpr dsf(float f) : hi(f), lo(0.0f) {}
+    __host__ __device__ constexpr dsf(int i) : hi((float)i), lo(0.0f) {}  // exact for |i| < 2^24
+    __host__ __device__ constexpr dsf(double d) : hi((float)d), lo((float)(d - (double)(float)d)) {}
+    __host__ __device__ explicit operator double() const { return (double)hi + (double)lo; }
+    __host__ __device__ explicit operator float() const { return hi + lo; }
+};
+
+__device__ __forceinline__ dsf ds_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    return dsf(s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb)));
+}
+__device__ __forceinline__ dsf ds_fast_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    return dsf(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+__device__ __forceinline__ dsf operator+(dsf x, dsf y) {
+    const dsf s = ds_two_sum(x.hi, y.hi);
+    return ds_fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo)));
+}
+__device__ __forceinline__ dsf operator-(dsf x) { return dsf(-x.hi, -x.lo); }
+__device__ __forceinline__ dsf operator-(dsf x, dsf y) { return x + (-y); }
+__device__ __forceinline__ dsf operator*(dsf x, dsf y) {
+    const float p = __fmul_rn(x.hi, y.hi);
+    float e = __fmaf_rn(x.hi, y.hi, -p);  // exact rounding error of the product
+    e = __fmaf_rn(x.hi, y.lo, e);
+    e = __fmaf_rn(x.lo, y.hi, e);
+    return ds_fast_two_sum(p, e);
+}
+__device__ __forceinline__ dsf &operator+=(dsf &x, dsf y) { return x = x + y; }
+__device__ __forceinline__ bool operator<(dsf a, dsf b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
+__device__ __forceinline__ bool operator>(dsf a, dsf b) { return b < a; }
+
 template <class S> struct Compute { using type = float; };
+template <> struct Compute<dsf> { using type = dsf; };
+
+// The weights in double-single, split from their FP64 values.
+template <>
+__host__ __device__ constexpr dsf wq<dsf>(int q) {
+    return q == 0 ? dsf(4.0 / 9.0) : (q < 5 ? dsf(1.0 / 9.0) : dsf(1.0 / 36.0));
+}
 template <> struct Compute<double> { using type = double; };
 
 __device__ __forceinline__ float ld(const float *p) { return *p; }
@@ -85,6 +144,14 @@ __device__ __forceinline__ void st(__half *p, float v) { *p = __float2half_rn(v)
 __device__ __forceinline__ void st(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
 
 __device__ __forceinline__ float recip(float r) { return __frcp_rn(r); }
+__device__ __forceinline__ dsf ld(const dsf *p) { return *p; }
+__device__ __forceinline__ void st(dsf *p, dsf v) { *p = v; }
+// 1/r: the FP32 reciprocal of the high part, refined by one Newton step
+// q + q (1 - r q) in double-single (the error squares: ~2^-46).
+__device__ __forceinline__ dsf recip(dsf r) {
+    const dsf q(__frcp_rn(r.hi));
+    return q + q * (dsf(1.0f) - r * q);
+}
 __device__ __forceinline__ double recip(double r) { return 1.0 / r; }
 
 template <class S>
@@ -118,14 +185,16 @@ struct CavityDesc {
 // holds nodes of one cavity only (plus unused padding beyond its rectangle).
 // The host writes the list; the issuing thread copies a tile's header next
 // to its stage with the same bulk-copy barrier as the tile's data.
-// The lattice parameters come in both arithmetic precisions, rounded by the
-// host, so that no kernel converts (FP64 conversions are slow on this GPU).
+// The lattice parameters come in every arithmetic precision, rounded by the
+// host, so that no kernel converts (FP64 conversions are slow on this GPU):
+// FP64, FP32, and the low parts that make (FP32, low) the double-single value.
 struct TileHeader {
     int x0, y0, ox, oy, nx, ny, cav, pad;  // origin; origin relative to the cavity; cavity size
     double omega, alpha, gbeta, t_ref, fx, fy;
     float omega_f, alpha_f, gbeta_f, t_ref_f, fx_f, fy_f, pad1, pad2;
+    float omega_lo, alpha_lo, gbeta_lo, t_ref_lo, fx_lo, fy_lo, pad3, pad4;
 };
-static_assert(sizeof(TileHeader) == 112, "tile headers are 112-byte bulk copies");
+static_assert(sizeof(TileHeader) == 144, "tile headers are 144-byte bulk copies");
 
 
 // ---------------------------------------------------------------------------
@@ -616,6 +685,10 @@ __global__ void __launch_bounds__(G::THREADS, G::MINB)
         C alpha, omega, gbeta, t_ref, fx, fy;
         if constexpr (std::is_same<C, double>::value) {
             alpha = hd.alpha, omega = hd.omega, gbeta = hd.gbeta, t_ref = hd.t_ref, fx = hd.fx, fy = hd.fy;
+        } else if constexpr (std::is_same<C, dsf>::value) {
+            alpha = dsf(hd.alpha_f, hd.alpha_lo), omega = dsf(hd.omega_f, hd.omega_lo);
+            gbeta = dsf(hd.gbeta_f, hd.gbeta_lo), t_ref = dsf(hd.t_ref_f, hd.t_ref_lo);
+            fx = dsf(hd.fx_f, hd.fx_lo), fy = dsf(hd.fy_f, hd.fy_lo);
         } else {
             alpha = hd.alpha_f, omega = hd.omega_f, gbeta = hd.gbeta_f, t_ref = hd.t_ref_f, fx = hd.fx_f,
             fy = hd.fy_f;
@@ -647,9 +720,9 @@ __global__ void __launch_bounds__(G::THREADS, G::MINB)
                     // box walls: vertical sides own the corners
                     const int cx = ox + lx, cy = oy + ly;
                     const int side = cx == 0 ? 0 : (cx == cv_nx - 1 ? 1 : (cy == 0 ? 2 : 3));
-                    if constexpr (std::is_same<C, double>::value) {
-                        uw = cvp->wall_u[side];
-                        vw = cvp->wall_v[side];
+                    if constexpr (std::is_same<C, double>::value || std::is_same<C, dsf>::value) {
+                        uw = C(cvp->wall_u[side]);
+                        vw = C(cvp->wall_v[side]);
                     } else {
                         uw = cvp->wall_uf[side];
                         vw = cvp->wall_vf[side];
@@ -977,8 +1050,8 @@ __global__ void __launch_bounds__(256) nusselt_kernel(const StepArgs<S> a, doubl
     const int nx = a.nx;
     for (int j = threadIdx.x; j < a.ny; j += blockDim.x) {
         const auto *r = a.Tin + (long long)j * a.pitch;
-        const double t0 = r[0], t1 = r[1], t2 = r[2];
-        const double e0 = r[nx - 1], e1 = r[nx - 2], e2 = r[nx - 3];
+        const double t0 = (double)r[0], t1 = (double)r[1], t2 = (double)r[2];
+        const double e0 = (double)r[nx - 1], e1 = (double)r[nx - 2], e2 = (double)r[nx - 3];
         const double nh = -H * (-3.0 * t0 + 4.0 * t1 - t2) / (2.0 * dT);
         const double nc = -H * (3.0 * e0 - 4.0 * e1 + e2) / (2.0 * dT);
         loc[j] = nh;

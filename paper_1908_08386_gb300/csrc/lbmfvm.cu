@@ -51,12 +51,16 @@ int fail_thread(int code, const char *fmt, ...) {
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
+// Bytes of one temperature value: FP32 next to 32/16-bit storage.
+size_t temp_size(int prec) { return prec == LBMFVM_F64 || prec == LBMFVM_F32X2 ? 8 : 4; }
+
 size_t store_size(int prec) {
     switch (prec) {
         case LBMFVM_F64: return 8;
         case LBMFVM_F32: return 4;
         case LBMFVM_F16: return 2;
         case LBMFVM_BF16: return 2;
+        case LBMFVM_F32X2: return 8;
     }
     return 0;
 }
@@ -72,7 +76,7 @@ Layout make_layout(const lbmfvm_grid_t &g, int prec, int ncav = 1) {
     Layout L{};
     L.pitch = (int)align_up((size_t)g.nx, 64);
     L.plane = (long long)g.ny * L.pitch;
-    const size_t ss = store_size(prec), cs = prec == LBMFVM_F64 ? 8 : 4;
+    const size_t ss = store_size(prec), cs = temp_size(prec);
     size_t off = 0;
     auto take = [&](size_t bytes) {
         size_t o = off;
@@ -307,6 +311,11 @@ template <> struct TmaConfig<double, 0> { using G = TmaTile<double, 64, 8, 2, 25
 template <> struct TmaConfig<double, 1> { using G = TmaTile<double, 32, 8, 3, 256>; };
 template <> struct TmaConfig<double, 2> { using G = TmaTile<double, 32, 16, 2, 512>; };
 template <> struct TmaConfig<double, 3> { using G = TmaTile<double, 32, 8, 2, 256, 2>; };
+// double-single storage: 8-byte elements like FP64, the same shapes
+template <> struct TmaConfig<dsf, 0> { using G = TmaTile<dsf, 64, 8, 2, 256>; };
+template <> struct TmaConfig<dsf, 1> { using G = TmaTile<dsf, 32, 8, 3, 256>; };
+template <> struct TmaConfig<dsf, 2> { using G = TmaTile<dsf, 32, 16, 2, 512>; };
+template <> struct TmaConfig<dsf, 3> { using G = TmaTile<dsf, 32, 8, 2, 256, 2>; };
 constexpr int kTmaConfigs = 4;
 
 // Persistent grid of the TMA kernel: one block per resident slot, or one per
@@ -361,6 +370,7 @@ void launch_one(const lbmfvm_t *h, int cur, cudaStream_t s, bool stall = false) 
         case LBMFVM_F32: launch_step<float>(h, cur, s, stall); break;
         case LBMFVM_F16: launch_step<__half>(h, cur, s, stall); break;
         case LBMFVM_BF16: launch_step<__nv_bfloat16>(h, cur, s, stall); break;
+        case LBMFVM_F32X2: launch_step<dsf>(h, cur, s, stall); break;
     }
 }
 
@@ -464,6 +474,7 @@ void launch_rescale(lbmfvm_t *h) {
             case LBMFVM_F32: FN<float>(__VA_ARGS__); break;           \
             case LBMFVM_F16: FN<__half>(__VA_ARGS__); break;          \
             case LBMFVM_BF16: FN<__nv_bfloat16>(__VA_ARGS__); break;  \
+            case LBMFVM_F32X2: FN<dsf>(__VA_ARGS__); break;           \
         }                                                             \
     } while (0)
 
@@ -519,6 +530,7 @@ void launch_convert_from(const lbmfvm_t *src, lbmfvm_t *dst, long long off_s, lo
         case LBMFVM_F32: launch_convert<S, float>(src, dst, off_s, off_d, nx, ny, flip); break;
         case LBMFVM_F16: launch_convert<S, __half>(src, dst, off_s, off_d, nx, ny, flip); break;
         case LBMFVM_BF16: launch_convert<S, __nv_bfloat16>(src, dst, off_s, off_d, nx, ny, flip); break;
+        case LBMFVM_F32X2: launch_convert<S, dsf>(src, dst, off_s, off_d, nx, ny, flip); break;
     }
 }
 
@@ -542,6 +554,8 @@ EncodeTiledFn encode_tiled() {
 
 template <class S> constexpr CUtensorMapDataType tmap_type() { return CU_TENSOR_MAP_DATA_TYPE_FLOAT32; }
 template <> constexpr CUtensorMapDataType tmap_type<double>() { return CU_TENSOR_MAP_DATA_TYPE_FLOAT64; }
+// double-single pairs travel as opaque 8-byte words (zero fill = 0 + 0)
+template <> constexpr CUtensorMapDataType tmap_type<dsf>() { return CU_TENSOR_MAP_DATA_TYPE_UINT64; }
 template <> constexpr CUtensorMapDataType tmap_type<__half>() { return CU_TENSOR_MAP_DATA_TYPE_FLOAT16; }
 template <> constexpr CUtensorMapDataType tmap_type<__nv_bfloat16>() { return CU_TENSOR_MAP_DATA_TYPE_BFLOAT16; }
 
@@ -606,6 +620,13 @@ int upload_tiles(lbmfvm_t *h, int tw, int th) {
                 t.t_ref_f = (float)cd.t_ref;
                 t.fx_f = (float)cd.fx;
                 t.fy_f = (float)cd.fy;
+                auto lo = [](double d) { return (float)(d - (double)(float)d); };
+                t.omega_lo = lo(cd.omega);
+                t.alpha_lo = lo(cd.alpha);
+                t.gbeta_lo = lo(cd.gbeta);
+                t.t_ref_lo = lo(cd.t_ref);
+                t.fx_lo = lo(cd.fx);
+                t.fy_lo = lo(cd.fy);
                 tl.push_back(t);
             }
     }
@@ -697,6 +718,7 @@ int setup_kernels(lbmfvm_t *h) {
         case LBMFVM_F32: return setup_tma<float>(h);
         case LBMFVM_F16: return setup_tma<__half>(h);
         case LBMFVM_BF16: return setup_tma<__nv_bfloat16>(h);
+        case LBMFVM_F32X2: return setup_tma<dsf>(h);
     }
     return LBMFVM_OK;
 }
@@ -783,7 +805,7 @@ int autotune(lbmfvm_t *h) {
     if (int r = setup_kernels(h)) return r;
     if (int r = check_device_status(h)) return r;
     const size_t fbytes = 9 * (size_t)h->L.plane * store_size(h->prec);
-    const size_t tbytes = (size_t)h->L.plane * (h->prec == LBMFVM_F64 ? 8 : 4);
+    const size_t tbytes = (size_t)h->L.plane * temp_size(h->prec);
     for (int b = 0; b < 2; b++) {
         CU(h, cudaMemsetAsync(h->base + h->L.f[b], 0, fbytes, h->s));
         CU(h, cudaMemsetAsync(h->base + h->L.T[b], 0, tbytes, h->s));
@@ -809,7 +831,7 @@ int create_impl(const lbmfvm_grid_t *grid, const uint8_t *mask, double nu, doubl
     lbmfvm_opts_t opts;
     lbmfvm_opts_default(&opts);
     if (opts_in) opts = *opts_in;
-    if (opts.store < LBMFVM_F64 || opts.store > LBMFVM_BF16)
+    if (opts.store < LBMFVM_F64 || opts.store > LBMFVM_F32X2)
         return fail_thread(LBMFVM_ERR_ARG, "store = %d is not a LBMFVM_F* value", opts.store);
     if (opts.tile_y != 0 && opts.tile_y != 4 && opts.tile_y != 8 && opts.tile_y != 16)
         return fail_thread(LBMFVM_ERR_ARG, "tile_y must be 0, 4, 8 or 16 (got %d)", opts.tile_y);
@@ -937,7 +959,7 @@ int lbmfvm_workspace_bytes(const lbmfvm_grid_t *grid, const lbmfvm_opts_t *opts,
     if (!bytes) return fail_thread(LBMFVM_ERR_ARG, "bytes is NULL");
     if (int r = check_grid(grid)) return r;
     const int prec = opts ? opts->store : LBMFVM_F32;
-    if (prec < LBMFVM_F64 || prec > LBMFVM_BF16) return fail_thread(LBMFVM_ERR_ARG, "invalid store precision");
+    if (prec < LBMFVM_F64 || prec > LBMFVM_F32X2) return fail_thread(LBMFVM_ERR_ARG, "invalid store precision");
     *bytes = make_layout(*grid, prec).total;
     return LBMFVM_OK;
 }
