@@ -662,6 +662,13 @@ __global__ void __launch_bounds__(G::THREADS, G::MINB)
         tma::fence_mbar_init();
     }
     __syncthreads();
+    // Programmatic dependent launch: the next step's blocks may be scheduled
+    // as soon as every block of this one has started (they take the SMs this
+    // grid frees); a block's global reads and writes of the state wait until
+    // the previous step's grid has finished and its stores are visible.
+    // Without a programmatic predecessor the wait returns at once.
+    if (tid == 0) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     int2 pre = make_int2(0, 0);  // thread 0: origin of the next tile to issue
     if (tid == 0) {
         for (int k = 0; k < G::STAGES && k < my_count; k++)

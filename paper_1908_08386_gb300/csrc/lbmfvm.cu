@@ -337,8 +337,21 @@ void launch_tma_cfg(const lbmfvm_t *h, int cur, cudaStream_t s, bool stall) {
     // captured graph reads the current count after the list has changed
     const int *count = reinterpret_cast<const int *>(h->base + h->L.tiles);
     const TileHeader *tiles = reinterpret_cast<const TileHeader *>(h->base + h->L.tiles) + 1;
-    step_tma_kernel<S, G><<<blocks, G::THREADS, G::SMEM_BYTES, s>>>(a, cavs, tiles, count, h->map_f[cur], h->map_T[cur],
-                                                                    h->map_c, h->map_fo[cur ^ 1], h->map_To[cur ^ 1]);
+    // launched with programmatic stream serialisation: a step overlaps its
+    // launch and prologue with the previous step's last tiles (the kernel
+    // waits for the previous grid before touching the state)
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3(blocks);
+    lc.blockDim = dim3(G::THREADS);
+    lc.dynamicSmemBytes = G::SMEM_BYTES;
+    lc.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    lc.attrs = attr;
+    lc.numAttrs = 1;
+    cudaLaunchKernelEx(&lc, step_tma_kernel<S, G>, a, cavs, tiles, count, h->map_f[cur], h->map_T[cur], h->map_c,
+                       h->map_fo[cur ^ 1], h->map_To[cur ^ 1]);
 }
 
 template <class S>
