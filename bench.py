@@ -43,7 +43,7 @@ FALLBACK_HBM_GBS = 6800.0
 
 # DRAM bytes per launch of step_kernel from one ncu capture
 # (profiles/step_kernel_*.md), valid only for the kernel source hashed here.
-NCU_TRAFFIC = {("f32", 4096, "8748432a09d92838"): 1335.3e6}
+NCU_TRAFFIC = {("f32", 4096, "262bc55f6264da2c"): 1340.5e6}
 
 
 def kernel_hash() -> str:
@@ -229,6 +229,7 @@ def run_ours(args):
     t_wall0 = time.perf_counter()
     total_ms = 0.0
     last = None
+    launches0 = L.lbmfvm_launch_count(cav.h)
     for _ in range(args.steps):
         flush.zero_()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -238,6 +239,7 @@ def run_ours(args):
         e1.record(stream)
         e1.synchronize()
         total_ms += e0.elapsed_time(e1)
+    timed_launches = L.lbmfvm_launch_count(cav.h) - launches0
     torch.cuda.synchronize()
     barrier(world)
     wall_s = time.perf_counter() - t_wall0
@@ -247,19 +249,22 @@ def run_ours(args):
 
     value = replicas.whole_job_rate(n_nodes * args.chunk * args.steps, world, total_ms * 1e-3) / 1e6
 
-    # Dominant kernel: step_kernel.  Average launch duration over a run of
-    # back-to-back launches (graph replays) on the same stream.
+    # Dominant kernel: the step kernel.  Average launch duration over a run
+    # of back-to-back launches (graph replays) on the same stream, launches
+    # counted by the library.
     flush.zero_()
     torch.cuda.synchronize()
-    k_launches = args.chunk
+    k_steps = args.chunk
+    n0 = L.lbmfvm_launch_count(cav.h)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    cav.step(k_launches)
+    cav.step(k_steps)
     e1.record(stream)
     e1.synchronize()
+    k_launches = L.lbmfvm_launch_count(cav.h) - n0
     launch_s = e0.elapsed_time(e1) * 1e-3 / k_launches
-    bytes_per_launch = BYTES_PER_LU[args.store] * n_nodes
+    bytes_per_launch = BYTES_PER_LU[args.store] * n_nodes * k_steps / k_launches
     achieved = bytes_per_launch / launch_s / 1e9
     peak, peak_kind = measured_peak()
     traffic = NCU_TRAFFIC.get((args.store, args.size, kernel_hash()))
@@ -306,10 +311,12 @@ def run_ours(args):
                    "final_nusselt": last[1] if last else None},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "kernel": "step_kernel" if args.kernel == "generic" or args.store == "f64" else "step_tma_kernel", "peak_kind": peak_kind,
-                     "algorithmic_bytes_per_launch": bytes_per_launch, "avg_launch_us": launch_s * 1e6},
+                     "algorithmic_bytes_per_launch": bytes_per_launch, "avg_launch_us": launch_s * 1e6,
+                     "coupled_steps_per_launch": k_steps / k_launches,
+                     "us_per_coupled_step": launch_s * 1e6 * k_launches / k_steps},
         "cpu_baseline": cpu,
         "e2e": e2e,
-        "gpu_launches": args.steps * (args.chunk + 3),
+        "gpu_launches": timed_launches + 3 * args.steps,
         "clocks": clocks,
     }
     print(json.dumps(line), flush=True)

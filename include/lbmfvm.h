@@ -223,6 +223,10 @@ int lbmfvm_run_to_steady(lbmfvm_t *h, double tol, int64_t check_every, int64_t m
  * after src's queued work. */
 int lbmfvm_copy_state(lbmfvm_t *dst, lbmfvm_t *src);
 
+/* Number of step-kernel launches lbmfvm_step has issued on this handle (one
+ * per coupled step; a CUDA-graph replay counts the launches it holds). */
+int lbmfvm_launch_count(const lbmfvm_t *h, int64_t *launches);
+
 /* Step kernel in use (LBMFVM_KERNEL_TMA or LBMFVM_KERNEL_GENERIC) and the TMA
  * tile shape (-1 for the generic kernel); either pointer may be NULL. */
 int lbmfvm_kernel_info(const lbmfvm_t *h, int32_t *kernel, int32_t *tma_config);

@@ -43,7 +43,7 @@ PRECISIONS = {"f64": LBMFVM_F64, "f32": LBMFVM_F32, "f16": LBMFVM_F16, "bf16": L
 EXPORTS = (
     "lbmfvm_opts_default", "lbmfvm_workspace_bytes", "lbmfvm_create", "lbmfvm_create_lattice",
     "lbmfvm_set_state", "lbmfvm_step", "lbmfvm_inject_stall", "lbmfvm_step_count", "lbmfvm_fields", "lbmfvm_fields_f32",
-    "lbmfvm_nusselt", "lbmfvm_residual", "lbmfvm_run_to_steady", "lbmfvm_copy_state", "lbmfvm_kernel_info", "lbmfvm_params", "lbmfvm_residual_noalloc",
+    "lbmfvm_nusselt", "lbmfvm_residual", "lbmfvm_run_to_steady", "lbmfvm_copy_state", "lbmfvm_launch_count", "lbmfvm_kernel_info", "lbmfvm_params", "lbmfvm_residual_noalloc",
     "lbmfvm_destroy", "lbmfvm_last_error", "lbmfvm_batch_create", "lbmfvm_batch_set_state", "lbmfvm_batch_step",
     "lbmfvm_batch_residuals", "lbmfvm_batch_run", "lbmfvm_batch_fields", "lbmfvm_batch_nusselt", "lbmfvm_batch_info",
     "lbmfvm_batch_set_polish", "lbmfvm_batch_kernel_info", "lbmfvm_batch_precision", "lbmfvm_batch_destroy", "lbmfvm_batch_last_error",
@@ -101,6 +101,7 @@ def lib() -> ctypes.CDLL:
                 "lbmfvm_run_to_steady": (ctypes.c_int, [vp, d, i64, i64, i64p, dp]),
                 "lbmfvm_copy_state": (ctypes.c_int, [vp, vp]),
                 "lbmfvm_kernel_info": (ctypes.c_int, [vp, ctypes.POINTER(i32), ctypes.POINTER(i32)]),
+                "lbmfvm_launch_count": (ctypes.c_int, [vp, i64p]),
                 "lbmfvm_params": (ctypes.c_int, [vp, dp, dp, dp, dp]),
                 "lbmfvm_residual_noalloc": (ctypes.c_int, [vp, vp, vp, vp, vp, i64, vp, dp]),
                 "lbmfvm_destroy": (None, [vp]),
@@ -225,6 +226,12 @@ def lbmfvm_run_to_steady(h, tol=1e-8, check_every=1000, max_steps=10**8):
     _check(lib().lbmfvm_run_to_steady(h, float(tol), int(check_every), int(max_steps), ctypes.byref(done),
                                       ctypes.byref(r)), h)
     return done.value, r.value
+
+
+def lbmfvm_launch_count(h) -> int:
+    n = ctypes.c_int64()
+    _check(lib().lbmfvm_launch_count(h, ctypes.byref(n)), h)
+    return n.value
 
 
 def lbmfvm_kernel_info(h):

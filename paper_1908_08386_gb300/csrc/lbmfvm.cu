@@ -226,6 +226,7 @@ struct lbmfvm {
     int64_t steps;    // steps since set_state
     cudaGraphExec_t graph;
     int graph_blocks; // grid of the TMA launches the graph holds
+    int64_t launches; // step-kernel launches issued (a graph replay counts its kernel nodes)
     bool use_tma;     // persistent TMA kernel (walled domains, 32/16-bit storage)
     bool stall_next;  // test hook armed by lbmfvm_inject_stall
     int tma_config;   // tile shape of the TMA kernel
@@ -1025,6 +1026,7 @@ int lbmfvm_step(lbmfvm_t *h, int64_t n) {
             CU(h, cudaGraphLaunch(h->graph, h->s));
             n -= kGraphSteps;
             h->steps += kGraphSteps;
+            h->launches += kGraphSteps;
         } else {
             launch_one(h, h->parity, h->s, h->stall_next);
             h->stall_next = false;
@@ -1032,6 +1034,7 @@ int lbmfvm_step(lbmfvm_t *h, int64_t n) {
             h->parity ^= 1;
             n--;
             h->steps++;
+            h->launches++;
         }
     }
     return join_out(h);
@@ -1143,6 +1146,12 @@ int lbmfvm_copy_state(lbmfvm_t *dst, lbmfvm_t *src) {
                             2 * (size_t)dst->grid.nx * dst->grid.ny * sizeof(double), cudaMemcpyDeviceToDevice, dst->s));
     dst->steps = src->steps;
     return join_out(dst);
+}
+
+int lbmfvm_launch_count(const lbmfvm_t *h, int64_t *launches) {
+    if (!h || !launches) return fail_thread(LBMFVM_ERR_ARG, "handle or launches is NULL");
+    *launches = h->launches;
+    return LBMFVM_OK;
 }
 
 int lbmfvm_kernel_info(const lbmfvm_t *h, int32_t *kernel, int32_t *tma_config) {

@@ -296,3 +296,11 @@ def test_run_to_steady_reaches_tolerance():
     gpu = L.Cavity(33, 33, Ra=1e3, Pr=0.71, Ma=MA, store="f64")
     steps, r = gpu.run_to_steady(tol=1e-9, check_every=500, max_steps=200000)
     assert r < 1e-9 and steps % 500 == 0 and steps < 200000
+
+
+def test_launch_count_follows_the_steps():
+    g = L.Cavity(70, 48, Ra=1e4, Pr=0.71, Ma=MA, store="f32", kernel="tma")
+    n0 = L.lbmfvm_launch_count(g.h)
+    g.step(1)
+    g.step(130)  # single launches and one graph replay of 64
+    assert L.lbmfvm_launch_count(g.h) - n0 == 131
