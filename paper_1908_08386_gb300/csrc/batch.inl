@@ -13,7 +13,7 @@
 // Precision ladder: the rounding of the stored populations puts a floor under
 // the residual (about 1e-3 for 16-bit storage, 1e-7 for FP32).  Above the
 // storage grid the batch keeps packed grids of the wider precisions with the
-// same slots (FP32, then FP64), created when first needed; a cavity whose
+// same slots (FP32, then double-single), created when first needed; a cavity whose
 // residual reaches its level's switch value, or stops falling, is converted
 // into the next grid and stepped there from then on.  The top of the ladder
 // is double-single storage and arithmetic (FP64-like precision on the FP32

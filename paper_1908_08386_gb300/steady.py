@@ -1,8 +1,8 @@
 """Time to steady state of many cavities: the fast form against the plain loop.
 
 Fast form: every cavity in one batch (one persistent launch per step), 16-bit
-storage climbing the precision ladder to FP64, initial states from the
-learned warm start.  Plain form: one cavity after another, each its own handle
+storage climbing the precision ladder (FP32, then double-single), initial
+states from the learned warm start.  Plain form: one cavity after another, each its own handle
 with FP32 storage from rest, switched to FP64 storage at the same point of
 the ladder (FP32 storage cannot reach a 1e-8 residual: its rounding floor is
 about 2e-7), with the same residual checks and mass renormalisation.  Both
