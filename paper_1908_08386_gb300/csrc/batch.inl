@@ -513,9 +513,19 @@ int lbmfvm_batch_step(lbmfvm_batch_t *b, int64_t n) {
     for (auto &c : b->cav)
         if (c.active) any[c.level] = true;
     if (n == 0) return LBMFVM_OK;
+    // The levels' grids are independent (no block of one waits on another),
+    // so their launches go on their own streams at once: a level with few
+    // tiles left then fills SMs the others leave idle instead of paying its
+    // launch fill and drain alone.
     for (int l = 0; l < b->nlv; l++)
         if (any[l])
-            if (int r = bcheck_h(b, b->lv[l], lbmfvm_step(b->lv[l], n))) return r;
+            if (int r = bcheck_h(b, b->lv[l], join_in(b->lv[l]))) return r;
+    for (int l = 0; l < b->nlv; l++)
+        if (any[l])
+            if (int r = bcheck_h(b, b->lv[l], step_impl(b->lv[l], n))) return r;
+    for (int l = 0; l < b->nlv; l++)
+        if (any[l])
+            if (int r = bcheck_h(b, b->lv[l], join_out(b->lv[l]))) return r;
     for (auto &c : b->cav)
         if (c.active) c.steps += n;
     return LBMFVM_OK;

@@ -958,6 +958,37 @@ int fields_impl(lbmfvm_t *h, O *rho, O *u, O *v, O *T) {
 
 }  // namespace
 
+namespace {
+// lbmfvm_step without the joins with the caller's stream: the launches of
+// n steps on the handle's own stream.
+int step_impl(lbmfvm_t *h, int64_t n) {
+    // a tile list that changed size since the capture needs another grid
+    if (h->graph && h->use_tma && h->graph_blocks != tma_grid(h)) {
+        CU(h, cudaGraphExecDestroy(h->graph));
+        h->graph = nullptr;
+    }
+    if (n >= kGraphSteps && !h->graph)
+        if (int r = build_graph(h)) return r;
+    while (n > 0) {
+        if (h->parity == 0 && n >= kGraphSteps && h->graph && !h->stall_next) {
+            CU(h, cudaGraphLaunch(h->graph, h->s));
+            n -= kGraphSteps;
+            h->steps += kGraphSteps;
+            h->launches += kGraphSteps;
+        } else {
+            launch_one(h, h->parity, h->s, h->stall_next);
+            h->stall_next = false;
+            CU(h, cudaGetLastError());
+            h->parity ^= 1;
+            n--;
+            h->steps++;
+            h->launches++;
+        }
+    }
+    return LBMFVM_OK;
+}
+}  // namespace
+
 extern "C" {
 
 void lbmfvm_opts_default(lbmfvm_opts_t *o) {
@@ -1014,29 +1045,7 @@ int lbmfvm_step(lbmfvm_t *h, int64_t n) {
     if (n < 0) return fail(h, LBMFVM_ERR_ARG, "n = %lld is negative", (long long)n);
     if (n == 0) return LBMFVM_OK;
     if (int r = join_in(h)) return r;
-    // a tile list that changed size since the capture needs another grid
-    if (h->graph && h->use_tma && h->graph_blocks != tma_grid(h)) {
-        CU(h, cudaGraphExecDestroy(h->graph));
-        h->graph = nullptr;
-    }
-    if (n >= kGraphSteps && !h->graph)
-        if (int r = build_graph(h)) return r;
-    while (n > 0) {
-        if (h->parity == 0 && n >= kGraphSteps && h->graph && !h->stall_next) {
-            CU(h, cudaGraphLaunch(h->graph, h->s));
-            n -= kGraphSteps;
-            h->steps += kGraphSteps;
-            h->launches += kGraphSteps;
-        } else {
-            launch_one(h, h->parity, h->s, h->stall_next);
-            h->stall_next = false;
-            CU(h, cudaGetLastError());
-            h->parity ^= 1;
-            n--;
-            h->steps++;
-            h->launches++;
-        }
-    }
+    if (int r = step_impl(h, n)) return r;
     return join_out(h);
 }
 
