@@ -208,6 +208,18 @@ __device__ __forceinline__ C eq_poly(int q, C ux, C uy, C usq) {
     return C(3) * eu + C(4.5) * eu * eu - C(1.5) * usq;
 }
 
+// a b + c rounded once and a b rounded on its own, whatever the compiler
+// would contract by itself: a product that feeds several sums may be fused
+// into some of them, and a choice that differed between kernel
+// instantiations would make tile shapes disagree in the last bit.  Double-
+// single has no fused form and keeps its compensated product and sum.
+__device__ __forceinline__ float fma_c(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_c(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ dsf fma_c(dsf a, dsf b, dsf c) { return a * b + c; }
+__device__ __forceinline__ float mul_r(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_r(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ dsf mul_r(dsf a, dsf b) { return a * b; }
+
 // Eqs. 16-17 on shifted populations g = f - w: rho = 1 + sum g, rho u = sum e g.
 template <class C>
 __device__ __forceinline__ void moments(const C g[9], C &drho, C &ux, C &uy) {
@@ -216,8 +228,8 @@ __device__ __forceinline__ void moments(const C g[9], C &drho, C &ux, C &uy) {
     const C jy = ((g[2] + g[5]) + g[6]) - ((g[4] + g[7]) + g[8]);
     const C inv = recip(C(1) + s);
     drho = s;
-    ux = jx * inv;
-    uy = jy * inv;
+    ux = mul_r(jx, inv);
+    uy = mul_r(jy, inv);
 }
 
 // Non-equilibrium extrapolation (Eq. 94): g holds the partner's populations
@@ -225,11 +237,21 @@ __device__ __forceinline__ void moments(const C g[9], C &drho, C &ux, C &uy) {
 // and the wall velocity (uw, vw).
 template <class C>
 __device__ __forceinline__ void nee(C g[9], C &drho, C &ux, C &uy, C uw, C vw) {
+    // g_q += rho w_q (P_q(u_w) - P_q(u_f)); opposite directions share the
+    // even part 4.5 (e.u)^2 - 1.5 u.u and differ in the sign of 3 e.u.
     const C rho = C(1) + drho;
-    const C usw = uw * uw + vw * vw, usf = ux * ux + uy * uy;
-#pragma unroll
-    for (int q = 0; q < 9; q++)
-        g[q] += rho * wq<C>(q) * (eq_poly<C>(q, uw, vw, usw) - eq_poly<C>(q, ux, uy, usf));
+    const C dP0 = mul_r(C(-1.5), fma_c(uw, uw, mul_r(vw, vw)) - fma_c(ux, ux, mul_r(uy, uy)));
+    g[0] = fma_c(mul_r(rho, wq<C>(0)), dP0, g[0]);
+    auto pair = [&](int q, int qb, C euw, C euf) {
+        const C A = fma_c(C(4.5), fma_c(euw, euw, -mul_r(euf, euf)), dP0), B = mul_r(C(3), euw - euf);
+        const C rw = mul_r(rho, wq<C>(q));
+        g[q] = fma_c(rw, A + B, g[q]);
+        g[qb] = fma_c(rw, A - B, g[qb]);
+    };
+    pair(1, 3, uw, ux);
+    pair(2, 4, vw, uy);
+    pair(5, 7, uw + vw, ux + uy);
+    pair(6, 8, vw - uw, uy - ux);
     moments<C>(g, drho, ux, uy);
 }
 
@@ -239,20 +261,38 @@ __device__ __forceinline__ void nee(C g[9], C &drho, C &ux, C &uy, C uw, C vw) {
 // P_q = 3 e.u + 4.5 (e.u)^2 - 1.5 u.u and h_q = G.(e_q - u):
 //   f_eq - w = w (drho + rho P),  F = 3 h f_eq = 3 h w rho (1 + P),
 //   g* = (1 - omega) g + w [omega drho + 3 rho h + P (omega rho + 3 rho h)].
+// Directions are taken in opposite pairs (1, 3), (2, 4), (5, 7), (6, 8): for
+// e = e_q, with s = 3 rho e.G - 3 rho G.u, A = 4.5 (e.u)^2 - 1.5 u.u and
+// B = 3 e.u, the pair's results are
+//   g*_q = (1 - omega) g_q + w [(omega drho + s) + (A + B)(omega rho + s)]
+// and the same with -3 rho e.G and -B for the opposite direction; the rest
+// direction has e = 0.  s joins omega rho inside one fused multiply-add:
+// rounding omega rho first and adding s afterwards would round a value on
+// the FP32 grid plus a nearly constant s the same way at every node (a body
+// force gives every node the same 3 rho G.e), a mass drift of about 1e-10
+// per node and step.
 template <class C, class Store>
 __device__ __forceinline__ void collide(const C g[9], C drho, C ux, C uy, C omega, C Gx, C Gy, Store store) {
     const C rho = C(1) + drho;
-    const C usq = ux * ux + uy * uy;
-    const C Gu = Gx * ux + Gy * uy;
-    const C a = omega * drho, b = omega * rho, c = C(3) * rho, om1 = C(1) - omega;
-    const C P0 = C(-1.5) * usq;
-#pragma unroll
-    for (int q = 0; q < 9; q++) {
-        const C eu = C(cx(q)) * ux + C(cy(q)) * uy;
-        const C P = C(3) * eu + C(4.5) * eu * eu + P0;
-        const C ch = c * (C(cx(q)) * Gx + C(cy(q)) * Gy - Gu);
-        store(q, om1 * g[q] + wq<C>(q) * ((a + ch) + P * (b + ch)));
-    }
+    const C P0 = mul_r(C(-1.5), fma_c(ux, ux, mul_r(uy, uy)));
+    const C c = mul_r(C(3), rho);
+    const C sx = mul_r(c, Gx), sy = mul_r(c, Gy);
+    const C sGu = fma_c(sx, ux, mul_r(sy, uy));
+    const C om1 = C(1) - omega;
+    auto out = [&](int q, C P, C s) {
+        const C w = wq<C>(q);
+        store(q, fma_c(om1, g[q], mul_r(w, fma_c(P, fma_c(omega, rho, s), fma_c(omega, drho, s)))));
+    };
+    out(0, P0, -sGu);
+    auto pair = [&](int q, int qb, C eu, C es) {
+        const C A = fma_c(C(4.5), mul_r(eu, eu), P0), B = mul_r(C(3), eu);
+        out(q, A + B, es - sGu);
+        out(qb, A - B, -es - sGu);
+    };
+    pair(1, 3, ux, sx);
+    pair(2, 4, uy, sy);
+    pair(5, 7, ux + uy, sx + sy);
+    pair(6, 8, uy - ux, sy - sx);
 }
 
 // Explicit finite-volume update (forward Euler, dt = 1) of a node-centred
