@@ -625,8 +625,18 @@ __device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.w
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 }  // namespace tma
 
-// Persistent fused step for walled domains (no periodic sides).  Tile k of a
-// block runs
+// Persistent fused step for walled domains (no periodic sides).  A block's
+// first nfix >= STAGES + 1 tiles are fixed (tile blockIdx.x + k gridDim.x);
+// the rest come one at a time from a counter in global memory, so that
+// blocks on faster SMs take more of them and the grid ends together.  The
+// issuing thread runs two tiles ahead of its loads: a ticket taken at one
+// refill is turned into a tile index (and its origin read) at the next and
+// loaded at the one after, so that neither the atomic nor the list read
+// stalls it.  A tile's
+// existence is settled, and published in shared memory, before the barrier
+// that precedes its iteration.  Each launch uses one of two counters by step
+// parity and clears the other one for the next step (which starts after this
+// grid has finished).  Tile k of a block runs
 //   wait    every thread waits (bounded) for stage k % STAGES to land;
 //   phase A moments of the own nodes (kept in registers) and of the ring
 //           (u, v to ring buffer k % 2);
@@ -644,7 +654,8 @@ __global__ void __launch_bounds__(G::THREADS, G::MINB)
     step_tma_kernel(const StepArgs<S> a, const CavityDesc *__restrict__ cavs, const TileHeader *__restrict__ tiles,
                     const int *__restrict__ ntiles_p, const __grid_constant__ CUtensorMap map_f,
                     const __grid_constant__ CUtensorMap map_T, const __grid_constant__ CUtensorMap map_c,
-                    const __grid_constant__ CUtensorMap map_f_out, const __grid_constant__ CUtensorMap map_T_out) {
+                    const __grid_constant__ CUtensorMap map_f_out, const __grid_constant__ CUtensorMap map_T_out,
+                    int *__restrict__ ctr, int *__restrict__ ctr_next, const int nfix) {
     using C = typename Compute<S>::type;
     constexpr int TW = G::TW, TH = G::TH, FW = G::FW, FH = G::FH, RW = G::RW, NPT = G::NPT;
     constexpr int XOFF = G::XOFF;
@@ -652,27 +663,22 @@ __global__ void __launch_bounds__(G::THREADS, G::MINB)
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + G::BAR_OFF);
     int *abort_flag = reinterpret_cast<int *>(smem + G::BAR_OFF + 8 * G::STAGES);
+    volatile int *known = abort_flag + 1;  // tiles this block is known to have
     TileHeader *hdrs = reinterpret_cast<TileHeader *>(smem + G::HDR_OFF);
 
     const int tid = threadIdx.x;
     const int ntiles = *ntiles_p;
-    const int my_count = (int)blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
-    auto stage = [&](int k) { return smem + (k % G::STAGES) * G::STAGE_BYTES; };
-    // Origin of the k-th tile of this block (the issuing thread loads it one
-    // issue ahead); the rest of the header travels with the tile's data.
-    auto origin = [&](int k) {
-        int2 o = make_int2(0, 0);
-        if (k < my_count) {
-            const TileHeader *t = tiles + (int)blockIdx.x + k * (int)gridDim.x;
-            o = make_int2(t->x0, t->y0);
-        }
-        return o;
+    auto fixed_tile = [&](int k) {
+        const int t = (int)blockIdx.x + k * (int)gridDim.x;
+        return t < ntiles ? t : -1;
     };
+    auto stage = [&](int k) { return smem + (k % G::STAGES) * G::STAGE_BYTES; };
+    auto origin = [&](int t) { return make_int2(tiles[t].x0, tiles[t].y0); };
     // A tile origin off the 16-node grid would give a TMA box an unaligned
     // x coordinate; such a tile is never loaded (its wait then runs out and
     // the block leaves through the abort path with the status word set).
     auto tile_ok = [&](int x0, int y0) { return (x0 & 15) == 0 && x0 >= 0 && y0 >= 0; };
-    auto issue = [&](int k, int2 o) {
+    auto issue = [&](int k, int t, int2 o) {
         const int s = k % G::STAGES;
         const int x0 = o.x, y0 = o.y;
         if (!tile_ok(x0, y0)) {
@@ -681,7 +687,7 @@ __global__ void __launch_bounds__(G::THREADS, G::MINB)
         }
         unsigned char *stg = stage(k);
         tma::mbar_arrive_expect_tx(&bars[s], G::TX_BYTES + (uint32_t)sizeof(TileHeader));
-        tma::load_bytes(&hdrs[s], tiles + (int)blockIdx.x + k * (int)gridDim.x, sizeof(TileHeader), &bars[s]);
+        tma::load_bytes(&hdrs[s], tiles + t, sizeof(TileHeader), &bars[s]);
         tma::load_3d(stg + G::F_OFF, &map_f, &bars[s], x0 - XOFF, y0 - 3, 0);
         tma::load_2d(stg + G::T_OFF, &map_T, &bars[s], x0 - 4, y0 - 1);
         tma::load_2d(stg + G::C_OFF, &map_c, &bars[s], x0 - 16, y0 - 1);
@@ -699,6 +705,7 @@ __global__ void __launch_bounds__(G::THREADS, G::MINB)
     if (tid == 0) {
         for (int s = 0; s < G::STAGES; s++) tma::mbar_init(&bars[s], 1);
         *abort_flag = 0;
+        *known = 0;
         tma::fence_mbar_init();
     }
     __syncthreads();
@@ -709,14 +716,30 @@ __global__ void __launch_bounds__(G::THREADS, G::MINB)
     // Without a programmatic predecessor the wait returns at once.
     if (tid == 0) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     asm volatile("griddepcontrol.wait;" ::: "memory");
-    int2 pre = make_int2(0, 0);  // thread 0: origin of the next tile to issue
+    // thread 0: the next tile to load (index, origin), the ticket in flight,
+    // loads issued
+    int pre_t = -1, ticket = -1, issued = 0;
+    int2 pre_o = make_int2(0, 0);
     if (tid == 0) {
-        for (int k = 0; k < G::STAGES && k < my_count; k++)
-            if (!(a.stall && blockIdx.x == 0 && k == 0)) issue(k, origin(k));
-        pre = origin(G::STAGES);
+        if (blockIdx.x == 0) *ctr_next = 0;
+        int k = 0;
+        for (; k < G::STAGES && fixed_tile(k) >= 0; k++) {
+            if (!(a.stall && blockIdx.x == 0 && k == 0)) issue(k, fixed_tile(k), origin(fixed_tile(k)));
+            issued = k + 1;
+        }
+        if (k == G::STAGES) {
+            pre_t = fixed_tile(G::STAGES);
+            if (pre_t >= 0) {
+                k++;
+                pre_o = origin(pre_t);
+                if (G::STAGES + 1 >= nfix) ticket = atomicAdd(ctr, 1);
+            }
+        }
+        *known = k;
     }
+    __syncthreads();
 
-    for (int k = 0; k < my_count; k++) {
+    for (int k = 0; k < *known; k++) {
         unsigned char *stg = stage(k);
         const bool landed = tma::mbar_wait_bounded(&bars[k % G::STAGES], (uint32_t)(k / G::STAGES) & 1u, kWaitLimitNs);
         if (!landed) {
@@ -813,7 +836,7 @@ __global__ void __launch_bounds__(G::THREADS, G::MINB)
         if (*abort_flag) {
             if (tid == 0) {
                 // let the copies already in flight land before the block exits
-                for (int j = k + 1; j < my_count && j < k + G::STAGES; j++)
+                for (int j = k + 1; j < issued; j++)
                     tma::mbar_wait_bounded(&bars[j % G::STAGES], (uint32_t)(j / G::STAGES) & 1u, kWaitLimitNs / 2);
                 tma::bulk_wait_all();
             }
@@ -863,15 +886,30 @@ __global__ void __launch_bounds__(G::THREADS, G::MINB)
             const C Gy = fy + gbeta * (Tn - t_ref);
             collide<C>(g[j], dr[j], uu[j], vv[j], omega, fx, Gy, [&](int q, C v) { st(of + q * OPLANE, v); });
         }
-        if (tid == 0 && k > 0 && k - 1 + G::STAGES < my_count) {
+        if (tid == 0 && k > 0 && pre_t >= 0) {
             tma::bulk_wait_read();  // the results of tile k-1 have left its stage
-            issue(k - 1 + G::STAGES, pre);
-            pre = origin(k + G::STAGES);
+            issue(k - 1 + G::STAGES, pre_t, pre_o);
+            issued = k + G::STAGES;
+            // tile k + STAGES of this block: fixed, or named by the ticket
+            // taken at the previous refill
+            const int m = k + G::STAGES;
+            if (m < nfix) {
+                pre_t = fixed_tile(m);
+            } else {
+                const int t = nfix * (int)gridDim.x + ticket;
+                pre_t = ticket >= 0 && t < ntiles ? t : -1;
+            }
+            if (pre_t >= 0) {
+                pre_o = origin(pre_t);
+                *known = *known + 1;
+                if (m + 1 >= nfix) ticket = atomicAdd(ctr, 1);
+            }
         }
     }
+    const int count = *known;
     __syncthreads();
-    if (tid == 0 && my_count > 0) {
-        store_tile(my_count - 1);
+    if (tid == 0 && count > 0) {
+        store_tile(count - 1);
         tma::bulk_wait_all();
     }
 }

@@ -326,6 +326,14 @@ int tma_grid(const lbmfvm_t *h) {
     return h->ntiles < resident ? h->ntiles : resident;
 }
 
+// Tiles a block of the TMA kernel takes in a fixed order before it draws the
+// rest from the shared counter: all but the last kTilesDrawn rounds.
+constexpr int kTilesDrawn = 2;
+int fixed_tiles(int ntiles, int blocks, int stages) {
+    const int per = blocks > 0 ? ntiles / blocks : 0;
+    return std::max(stages + 1, per - kTilesDrawn);
+}
+
 template <class S, int CFG>
 void launch_tma_cfg(const lbmfvm_t *h, int cur, cudaStream_t s, bool stall) {
     using G = typename TmaConfig<S, CFG>::G;
@@ -335,8 +343,9 @@ void launch_tma_cfg(const lbmfvm_t *h, int cur, cudaStream_t s, bool stall) {
     if (blocks < 1) return;  // no active tile
     const CavityDesc *cavs = reinterpret_cast<const CavityDesc *>(h->base + h->L.cav);
     // the count sits at a fixed address in front of the list, so that a
-    // captured graph reads the current count after the list has changed
-    const int *count = reinterpret_cast<const int *>(h->base + h->L.tiles);
+    // captured graph reads the current count after the list has changed;
+    // the two tile counters (one per step parity) follow it
+    int *count = reinterpret_cast<int *>(h->base + h->L.tiles);
     const TileHeader *tiles = reinterpret_cast<const TileHeader *>(h->base + h->L.tiles) + 1;
     // launched with programmatic stream serialisation: a step overlaps its
     // launch and prologue with the previous step's last tiles (the kernel
@@ -351,8 +360,9 @@ void launch_tma_cfg(const lbmfvm_t *h, int cur, cudaStream_t s, bool stall) {
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     lc.attrs = attr;
     lc.numAttrs = 1;
-    cudaLaunchKernelEx(&lc, step_tma_kernel<S, G>, a, cavs, tiles, count, h->map_f[cur], h->map_T[cur], h->map_c,
-                       h->map_fo[cur ^ 1], h->map_To[cur ^ 1]);
+    cudaLaunchKernelEx(&lc, step_tma_kernel<S, G>, a, cavs, tiles, (const int *)count, h->map_f[cur], h->map_T[cur],
+                       h->map_c, h->map_fo[cur ^ 1], h->map_To[cur ^ 1], count + 1 + cur, count + 1 + (cur ^ 1),
+                       fixed_tiles(h->ntiles, blocks, G::STAGES));
 }
 
 template <class S>
@@ -508,6 +518,9 @@ int set_state_impl(lbmfvm_t *h, const float *u, const float *v, const float *T) 
     CU(h, cudaGetLastError());
     h->parity = 0;
     h->steps = 0;
+    // a step of parity p clears the tile counter of parity 1 - p for the next
+    // step; restarting at parity 0 clears both here
+    CU(h, cudaMemsetAsync(h->base + h->L.tiles + sizeof(int), 0, 2 * sizeof(int), h->s));
     DISPATCH(h, launch_residual, h, 1);  // snapshot := u^0
     CU(h, cudaGetLastError());
     // The host copy of the wall temperatures and the staged inputs must stay
@@ -608,7 +621,9 @@ int upload_tiles(lbmfvm_t *h, int tw, int th) {
     std::vector<CavityDesc> table;
     if (!h->atlas_cavs.empty()) table = h->atlas_cavs;
     else table.push_back(single_cavity_desc(h));
-    tl.push_back(TileHeader{});  // the count, read by the kernel, in front of the list
+    // the count, read by the kernel, in front of the list; its y0 and ox are
+    // the step kernel's tile counters (parity 0 and 1), cleared here
+    tl.push_back(TileHeader{});
     for (size_t c = 0; c < table.size(); c++) {
         if (!h->atlas_cavs.empty() && !h->atlas_active[c]) continue;
         const CavityDesc &cd = table[c];
