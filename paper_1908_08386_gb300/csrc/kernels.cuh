@@ -311,7 +311,17 @@ __device__ __forceinline__ C fv_update(C TP, C uP, C vP, C ex, C ey, C alpha, bo
     return TP + (ey * (fe + fw) + ex * (fn + fs)) * inv_v;
 }
 
-__device__ __forceinline__ bool fv_open(uint8_t code) { return (code >> 6) <= TH_DIRICHLET; }
+__host__ __device__ __forceinline__ bool fv_open(uint8_t code) { return (code >> 6) <= TH_DIRICHLET; }
+
+// Face flags of the finite-volume update, one byte per node in a plane beside
+// the codes (written by the host): which faces of the node's control volume
+// are open (the neighbour lies in the cavity and is a finite-volume or
+// Dirichlet node) and which neighbours lie in the cavity (the control
+// volume's extents).  Outside every cavity the byte is 0.
+enum : uint8_t {
+    FF_OPEN_E = 1, FF_OPEN_N = 2, FF_OPEN_W = 4, FF_OPEN_S = 8,
+    FF_IN_W = 16, FF_IN_E = 32, FF_IN_S = 64, FF_IN_N = 128
+};
 
 // Velocity of a box wall node from its side (vertical sides own the corners).
 template <class S>
@@ -572,12 +582,13 @@ struct TmaTile {
     static constexpr int XOFF = 16 / (int)sizeof(S) < 4 ? 4 : 16 / (int)sizeof(S);
     static constexpr int FW = TW + 2 * XOFF, FH = TH + 6;  // population box
     static constexpr int TWD = TW + 8, THT = TH + 2;       // temperature box (x0-4, y0-1)
-    static constexpr int CWD = TW + 32, CHT = TH + 2;      // code box (x0-16, y0-1)
+    static constexpr int CWD = TW + 32, CHT = TH + 2;      // code box (x0-16, y0-1), codes then face flags
     static constexpr int RW = TW + 2, RH = TH + 2;         // tile + ring
     static constexpr int NRING = 2 * RW + 2 * TH;          // ring nodes
     static constexpr uint32_t F_BYTES = 9u * FH * FW * sizeof(S);
     static constexpr uint32_t T_BYTES = (uint32_t)THT * TWD * (uint32_t)sizeof(TC);
-    static constexpr uint32_t C_BYTES = (uint32_t)CHT * CWD;
+    static constexpr uint32_t C_PLANE = (uint32_t)CHT * CWD;
+    static constexpr uint32_t C_BYTES = 2u * C_PLANE;
     static constexpr uint32_t align128(uint32_t v) { return (v + 127u) & ~127u; }
     static constexpr uint32_t F_OFF = 0, T_OFF = align128(F_BYTES), C_OFF = T_OFF + align128(T_BYTES);
     static constexpr uint32_t STAGE_BYTES = C_OFF + align128(C_BYTES);
@@ -690,7 +701,7 @@ __global__ void __launch_bounds__(G::THREADS, G::MINB)
         tma::load_bytes(&hdrs[s], tiles + t, sizeof(TileHeader), &bars[s]);
         tma::load_3d(stg + G::F_OFF, &map_f, &bars[s], x0 - XOFF, y0 - 3, 0);
         tma::load_2d(stg + G::T_OFF, &map_T, &bars[s], x0 - 4, y0 - 1);
-        tma::load_2d(stg + G::C_OFF, &map_c, &bars[s], x0 - 16, y0 - 1);
+        tma::load_3d(stg + G::C_OFF, &map_c, &bars[s], x0 - 16, y0 - 1, 0);
     };
     auto store_tile = [&](int k) {
         const int x0 = hdrs[k % G::STAGES].x0, y0 = hdrs[k % G::STAGES].y0;
@@ -750,7 +761,7 @@ __global__ void __launch_bounds__(G::THREADS, G::MINB)
         // block leaves at the next barrier)
         const TileHeader hd = landed ? hdrs[k % G::STAGES] : TileHeader{};
         // node (lx, ly) of the tile sits at (ox + lx, oy + ly) of its cavity
-        const int ox = hd.ox, oy = hd.oy, cv_nx = hd.nx, cv_ny = hd.ny;
+        const int ox = hd.ox, oy = hd.oy, cv_nx = hd.nx;
         const CavityDesc *cvp = cavs + hd.cav;
         C alpha, omega, gbeta, t_ref, fx, fy;
         if constexpr (std::is_same<C, double>::value) {
@@ -766,6 +777,7 @@ __global__ void __launch_bounds__(G::THREADS, G::MINB)
         const S *F = reinterpret_cast<const S *>(stg + G::F_OFF);
         const C *TT = reinterpret_cast<const C *>(stg + G::T_OFF);
         const uint8_t *CC = reinterpret_cast<const uint8_t *>(stg + G::C_OFF);
+        const uint8_t *CF = CC + G::C_PLANE;  // face flags
         C *RU = reinterpret_cast<C *>(smem + G::RING_OFF + (k & 1) * G::RING_BYTES), *RV = RU + G::RH * RW;
         // staged-box index of node (lx, ly) relative to the tile origin
         auto fidx = [&](int lx, int ly) { return (ly + 3) * FW + (lx + XOFF); };
@@ -852,7 +864,6 @@ __global__ void __launch_bounds__(G::THREADS, G::MINB)
         for (int j = 0; j < NPT; j++) {
             const int i = tid + j * G::THREADS;
             const int ly = i / TW, lx = i - ly * TW;
-            const int cx = ox + lx, cy = oy + ly;  // position in the cavity
             const uint8_t c = cc[j];
             const int t = tidx(lx, ly);
             const C TP = TT[t];
@@ -868,16 +879,12 @@ __global__ void __launch_bounds__(G::THREADS, G::MINB)
             C Tn = TP;
             if (th == TH_FV) {
                 // control volume clipped to the cavity; faces beyond it are closed
-                const bool hw = cx > 0, he = cx < cv_nx - 1, hs = cy > 0, hn = cy < cv_ny - 1;
-                const C ex = (hw ? C(0.5) : C(0)) + (he ? C(0.5) : C(0));
-                const C ey = (hs ? C(0.5) : C(0)) + (hn ? C(0.5) : C(0));
-                // (bitwise &: no short circuit, so no branch around the loads)
-                const bool oE = he & fv_open(decode(CC[cidx(lx + 1, ly)]));
-                const bool oN = hn & fv_open(decode(CC[cidx(lx, ly + 1)]));
-                const bool oW = hw & fv_open(decode(CC[cidx(lx - 1, ly)]));
-                const bool oS = hs & fv_open(decode(CC[cidx(lx, ly - 1)]));
-                Tn = fv_update<C>(TP, uu[j], vv[j], ex, ey, alpha, oE, TT[t + 1], RU[r + 1], oN, TT[t + G::TWD],
-                                  RV[r + RW], oW, TT[t - 1], RU[r - 1], oS, TT[t - G::TWD], RV[r - RW]);
+                const uint8_t ff = CF[cidx(lx, ly)];
+                const C ex = ((ff & FF_IN_W) ? C(0.5) : C(0)) + ((ff & FF_IN_E) ? C(0.5) : C(0));
+                const C ey = ((ff & FF_IN_S) ? C(0.5) : C(0)) + ((ff & FF_IN_N) ? C(0.5) : C(0));
+                Tn = fv_update<C>(TP, uu[j], vv[j], ex, ey, alpha, ff & FF_OPEN_E, TT[t + 1], RU[r + 1], ff & FF_OPEN_N,
+                                  TT[t + G::TWD], RV[r + RW], ff & FF_OPEN_W, TT[t - 1], RU[r - 1], ff & FF_OPEN_S,
+                                  TT[t - G::TWD], RV[r - RW]);
             } else if (th == TH_OBSTACLE) {
                 const int d = partner_dir(c);
                 Tn = TT[tidx(lx + cx_rt(d), ly + cy_rt(d))];

@@ -68,7 +68,7 @@ size_t store_size(int prec) {
 struct Layout {
     int pitch;
     long long plane;
-    size_t f[2], T[2], code, snap, stage, red, err, cav, tiles, cavres, twall, total;
+    size_t f[2], T[2], code, fflags, snap, stage, red, err, cav, tiles, cavres, twall, total;
     size_t tile_cap;  // headers the tile list holds
 };
 
@@ -88,6 +88,7 @@ Layout make_layout(const lbmfvm_grid_t &g, int prec, int ncav = 1) {
     L.T[0] = take((size_t)L.plane * cs);
     L.T[1] = take((size_t)L.plane * cs);
     L.code = take((size_t)L.plane);
+    L.fflags = take((size_t)L.plane);  // face flags of the finite-volume update
     L.snap = take(2 * (size_t)g.nx * g.ny * sizeof(double));
     L.stage = take(2 * (size_t)g.nx * g.ny * sizeof(double));
     L.red = take((kRedLocal + (size_t)g.ny) * sizeof(double));
@@ -201,6 +202,27 @@ std::vector<uint8_t> classify(const lbmfvm_grid_t &g, const uint8_t *mask, int p
         }
     for (auto &c : code) c = stored_code(c);
     return code;
+}
+
+// Face flags (FF_* bits) of every node of the given cavity rectangles of a
+// stored-code plane: the finite-volume update's control volume is clipped to
+// its cavity, and a face is open when the neighbour across it lies in the
+// cavity and is a finite-volume or Dirichlet node.
+std::vector<uint8_t> face_flags(const std::vector<uint8_t> &stored, int pitch, const std::vector<CavityDesc> &rects) {
+    std::vector<uint8_t> ff(stored.size(), 0);
+    for (const CavityDesc &r : rects)
+        for (int j = 0; j < r.ny; j++)
+            for (int i = 0; i < r.nx; i++) {
+                const size_t k = (size_t)(r.y0 + j) * pitch + (r.x0 + i);
+                auto open = [&](long long off) { return fv_open(decode(stored[(size_t)((long long)k + off)])); };
+                uint8_t f = 0;
+                if (i > 0) f |= FF_IN_W | (open(-1) ? FF_OPEN_W : 0);
+                if (i < r.nx - 1) f |= FF_IN_E | (open(1) ? FF_OPEN_E : 0);
+                if (j > 0) f |= FF_IN_S | (open(-(long long)pitch) ? FF_OPEN_S : 0);
+                if (j < r.ny - 1) f |= FF_IN_N | (open(pitch) ? FF_OPEN_N : 0);
+                ff[k] = f;
+            }
+    return ff;
 }
 
 }  // namespace
@@ -720,10 +742,11 @@ int encode_maps(lbmfvm_t *h, int fw, int fh, int tw, int th, int cw, int ch) {
                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) return fail(h, LBMFVM_ERR_CUDA, "tensor map of the temperature failed (%d)", (int)r);
     }
-    const cuuint64_t dims2[2] = {nx, ny};
-    const cuuint64_t strides2[1] = {pitch};
-    const cuuint32_t box2[2] = {(cuuint32_t)cw, (cuuint32_t)ch};
-    CUresult r = enc(&h->map_c, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, h->base + h->L.code, dims2, strides2, box2, one,
+    // codes and face flags: two planes of one box
+    const cuuint64_t dims3[3] = {nx, ny, 2};
+    const cuuint64_t strides3[2] = {pitch, (cuuint64_t)(h->L.fflags - h->L.code)};
+    const cuuint32_t box3[3] = {(cuuint32_t)cw, (cuuint32_t)ch, 2};
+    CUresult r = enc(&h->map_c, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, h->base + h->L.code, dims3, strides3, box3, one,
                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(h, LBMFVM_ERR_CUDA, "tensor map of the node codes failed (%d)", (int)r);
@@ -936,9 +959,17 @@ int create_impl(const lbmfvm_grid_t *grid, const uint8_t *mask, double nu, doubl
         h->atlas_active.assign(atlas->cavs.size(), 1);
         h->use_tma = true;
     }
+    std::vector<CavityDesc> rects = atlas ? atlas->cavs : std::vector<CavityDesc>(1);
+    if (!atlas) {
+        rects[0].nx = grid->nx;
+        rects[0].ny = grid->ny;
+    }
+    const std::vector<uint8_t> fflags = face_flags(code, L.pitch, rects);
     if (join_in(h)) return bail(LBMFVM_ERR_CUDA);
     if (cudaMemsetAsync(h->base, 0, L.total, h->s) != cudaSuccess ||
-        cudaMemcpyAsync(h->base + L.code, code.data(), code.size(), cudaMemcpyHostToDevice, h->s) != cudaSuccess) {
+        cudaMemcpyAsync(h->base + L.code, code.data(), code.size(), cudaMemcpyHostToDevice, h->s) != cudaSuccess ||
+        cudaMemcpyAsync(h->base + L.fflags, fflags.data(), fflags.size(), cudaMemcpyHostToDevice, h->s) !=
+            cudaSuccess) {
         fail(h, LBMFVM_ERR_CUDA, "device initialisation failed");
         return bail(LBMFVM_ERR_CUDA);
     }
