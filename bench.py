@@ -43,10 +43,10 @@ FALLBACK_HBM_GBS = 6800.0
 
 # DRAM bytes per launch of step_kernel from one ncu capture
 # (profiles/step_kernel_*.md), valid only for the kernel source hashed here.
-NCU_TRAFFIC = {("f32", 4096, "262bc55f6264da2c"): 1340.5e6,
+NCU_TRAFFIC = {("f32", 4096, "d18624217ad849dc"): 1329.1e6,
                # 1024^2: the 85 MB state stays in the 129 MB L2 between steps,
                # so DRAM sees about half the algorithmic bytes
-               ("f32", 1024, "262bc55f6264da2c"): 45.5e6}
+               ("f32", 1024, "d18624217ad849dc"): 45.5e6}
 
 
 def kernel_hash() -> str:
