@@ -68,11 +68,12 @@ extern "C" {
 
 /* Step kernel selection; both compute the same arithmetic.
  *   TMA      persistent, one block per SM: each tile's populations,
- *            temperature and node codes are staged in shared memory by TMA
- *            through a multi-stage mbarrier pipeline and the results leave by
- *            TMA bulk stores (walls on every side, F32/F16/BF16 storage only);
+ *            temperature, node codes and face flags are staged in shared
+ *            memory by TMA through a multi-stage mbarrier pipeline and the
+ *            results leave by TMA bulk stores (walls on every side; every
+ *            storage type);
  *   GENERIC  one block per tile, gathers straight from global memory (any
- *            boundary, F64).
+ *            boundary, every storage type).
  * AUTO takes TMA where it applies and GENERIC otherwise. */
 #define LBMFVM_KERNEL_AUTO 0
 #define LBMFVM_KERNEL_GENERIC 1
@@ -104,7 +105,7 @@ typedef struct {
 
 /* Options; fill with lbmfvm_opts_default() first. */
 typedef struct {
-    int32_t store;          /* LBMFVM_F64/F32/F16/BF16; default LBMFVM_F32 */
+    int32_t store;          /* LBMFVM_F64/F32/F16/BF16/F32X2; default LBMFVM_F32 */
     int32_t tile_y;         /* rows per thread block of the generic step kernel:
                                0 = default, else one of 4, 8, 16 */
     int32_t kernel;         /* LBMFVM_KERNEL_*; default AUTO */
@@ -134,8 +135,8 @@ typedef struct {
 void lbmfvm_opts_default(lbmfvm_opts_t *opts);
 
 /* Device bytes one handle of this grid and options needs (the distributions,
- * two temperature planes, node codes, a velocity snapshot and reduction
- * scratch).  Returns LBMFVM_ERR_ARG for an invalid grid. */
+ * two temperature planes, node codes and face flags, a velocity snapshot,
+ * the tile list and reduction scratch).  Returns LBMFVM_ERR_ARG for an invalid grid. */
 int lbmfvm_workspace_bytes(const lbmfvm_grid_t *grid, const lbmfvm_opts_t *opts, size_t *bytes);
 
 /* Create a cavity from the nondimensional groups (Eqs. 83-89):
