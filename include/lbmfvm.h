@@ -49,6 +49,7 @@ extern "C" {
 #define LBMFVM_ERR_DIVERGED (-4) /* a reduction met a non-finite value */
 #define LBMFVM_ERR_TIMEOUT (-5)  /* a bounded device-side wait ran out */
 #define LBMFVM_ERR_NOMEM (-6)    /* device allocation failed or workspace too small */
+#define LBMFVM_ERR_IO (-7)       /* a checkpoint file could not be written or read, or is corrupt */
 
 /* Sides of the rectangle, index into lbmfvm_grid_t.bc / t_wall. */
 #define LBMFVM_SIDE_W 0
@@ -323,6 +324,55 @@ int lbmfvm_batch_kernel_info(const lbmfvm_batch_t *b, int32_t prec, int32_t *tma
 int lbmfvm_batch_precision(const lbmfvm_batch_t *b, int32_t i, int32_t *prec);
 void lbmfvm_batch_destroy(lbmfvm_batch_t *b);
 const char *lbmfvm_batch_last_error(const lbmfvm_batch_t *b);
+
+/* Checkpoints.  The paper runs every case from rest to a steady state and
+ * defines no restart; these calls let a long run stop and resume.  A file
+ * holds one handle's state: the 256-byte header below (little-endian, the
+ * struct's layout has no implicit padding), then the payload:
+ *   the nine planes f_i - w_i (f_i for F64) of the current post-collision
+ *   state f*^n, [9][ny][nx] in the storage type (2, 4 or 8 bytes; F32X2 as
+ *   the (hi, lo) FP32 pairs), then the same for the previous step's f*^(n-1)
+ *   (at step 0 the unrelaxed f^0), from which the fields at step n are read;
+ *   the temperature T^n, [ny][nx], FP32 (8 bytes for F64 and F32X2);
+ *   the residual snapshot u, v of the last residual check, [2][ny][nx] FP64.
+ * The CRCs are CRC-32 of the ISO-HDLC polynomial (reflected 0xEDB88320, the
+ * one zlib's crc32 computes). */
+typedef struct {
+    char magic[8];              /* "LBMFVMC1" */
+    uint32_t version;           /* 1 */
+    uint32_t header_bytes;      /* 256 */
+    int32_t nx, ny, store, reserved;
+    int64_t steps;              /* steps since set_state */
+    int32_t bc[4];              /* lbmfvm_grid_t.bc */
+    double t_wall[4], u_lid;    /* lbmfvm_grid_t.t_wall, u_lid */
+    double tau, alpha, gbeta, t_ref, force[2]; /* lattice parameters */
+    uint64_t payload_bytes;
+    uint32_t code_crc;          /* CRC-32 of the handle's node codes (geometry, mask) */
+    uint32_t payload_crc;       /* CRC-32 of the payload */
+    uint8_t pad[92];            /* zero */
+    uint32_t header_crc;        /* CRC-32 of the 252 bytes before it */
+} lbmfvm_checkpoint_header_t;
+
+/* Write the state of h (after all work enqueued on its stream) to the file
+ * at path.  Single-cavity handles only.  Synchronises.  LBMFVM_ERR_IO if the
+ * file cannot be written; LBMFVM_ERR_TIMEOUT if an earlier step reported a
+ * wait that ran out (the state is then not written). */
+int lbmfvm_save(lbmfvm_t *h, const char *path);
+
+/* Replace the state of h by the one saved at path: populations,
+ * temperature, residual snapshot and step count.  The handle must have the
+ * grid, node codes, storage type and lattice parameters the file was saved
+ * with (LBMFVM_ERR_ARG otherwise); the file must be complete with matching
+ * CRCs (LBMFVM_ERR_IO otherwise).  Nothing on the device changes on an
+ * error.  Continuing from a loaded state gives bit for bit the results of
+ * the run that saved it.  Synchronises. */
+int lbmfvm_load(lbmfvm_t *h, const char *path);
+
+/* Read and verify the checkpoint at path without a GPU: fills *header after
+ * checking the magic, version, sizes and all three CRCs (LBMFVM_ERR_IO on
+ * any mismatch, a short file or a read error; LBMFVM_ERR_ARG for NULL
+ * arguments). */
+int lbmfvm_checkpoint_info(const char *path, lbmfvm_checkpoint_header_t *header);
 
 /* Release the handle and any memory the library allocated.  NULL is a no-op. */
 void lbmfvm_destroy(lbmfvm_t *h);

@@ -26,6 +26,7 @@ LBMFVM_ERR_CUDA = -3
 LBMFVM_ERR_DIVERGED = -4
 LBMFVM_ERR_TIMEOUT = -5
 LBMFVM_ERR_NOMEM = -6
+LBMFVM_ERR_IO = -7
 # Sides
 LBMFVM_SIDE_W, LBMFVM_SIDE_E, LBMFVM_SIDE_S, LBMFVM_SIDE_N = 0, 1, 2, 3
 # Boundary kinds
@@ -44,6 +45,7 @@ EXPORTS = (
     "lbmfvm_opts_default", "lbmfvm_workspace_bytes", "lbmfvm_create", "lbmfvm_create_lattice",
     "lbmfvm_set_state", "lbmfvm_step", "lbmfvm_inject_stall", "lbmfvm_step_count", "lbmfvm_fields", "lbmfvm_fields_f32",
     "lbmfvm_nusselt", "lbmfvm_residual", "lbmfvm_run_to_steady", "lbmfvm_copy_state", "lbmfvm_launch_count", "lbmfvm_kernel_info", "lbmfvm_params", "lbmfvm_residual_noalloc",
+    "lbmfvm_save", "lbmfvm_load", "lbmfvm_checkpoint_info",
     "lbmfvm_destroy", "lbmfvm_last_error", "lbmfvm_batch_create", "lbmfvm_batch_set_state", "lbmfvm_batch_step",
     "lbmfvm_batch_residuals", "lbmfvm_batch_run", "lbmfvm_batch_fields", "lbmfvm_batch_nusselt", "lbmfvm_batch_info",
     "lbmfvm_batch_set_polish", "lbmfvm_batch_kernel_info", "lbmfvm_batch_precision", "lbmfvm_batch_destroy", "lbmfvm_batch_last_error",
@@ -60,6 +62,16 @@ class lbmfvm_opts_t(ctypes.Structure):
                 ("tma_config", ctypes.c_int32), ("t_ref", ctypes.c_double),
                 ("cuda_stream", ctypes.c_void_p), ("workspace", ctypes.c_void_p),
                 ("workspace_bytes", ctypes.c_size_t)]
+
+
+class lbmfvm_checkpoint_header_t(ctypes.Structure):
+    _fields_ = [("magic", ctypes.c_char * 8), ("version", ctypes.c_uint32), ("header_bytes", ctypes.c_uint32),
+                ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("store", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("steps", ctypes.c_int64), ("bc", ctypes.c_int32 * 4),
+                ("t_wall", ctypes.c_double * 4), ("u_lid", ctypes.c_double), ("tau", ctypes.c_double),
+                ("alpha", ctypes.c_double), ("gbeta", ctypes.c_double), ("t_ref", ctypes.c_double),
+                ("force", ctypes.c_double * 2), ("payload_bytes", ctypes.c_uint64), ("code_crc", ctypes.c_uint32),
+                ("payload_crc", ctypes.c_uint32), ("pad", ctypes.c_uint8 * 92), ("header_crc", ctypes.c_uint32)]
 
 
 class LbmfvmError(RuntimeError):
@@ -104,6 +116,9 @@ def lib() -> ctypes.CDLL:
                 "lbmfvm_launch_count": (ctypes.c_int, [vp, i64p]),
                 "lbmfvm_params": (ctypes.c_int, [vp, dp, dp, dp, dp]),
                 "lbmfvm_residual_noalloc": (ctypes.c_int, [vp, vp, vp, vp, vp, i64, vp, dp]),
+                "lbmfvm_save": (ctypes.c_int, [vp, ctypes.c_char_p]),
+                "lbmfvm_load": (ctypes.c_int, [vp, ctypes.c_char_p]),
+                "lbmfvm_checkpoint_info": (ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(lbmfvm_checkpoint_header_t)]),
                 "lbmfvm_destroy": (None, [vp]),
                 "lbmfvm_last_error": (ctypes.c_char_p, [vp]),
                 "lbmfvm_batch_create": (ctypes.c_int, [i32, G, vp, dp, dp, dp, O, pp]),
@@ -263,6 +278,24 @@ def lbmfvm_residual_noalloc(u, v, u_prev, v_prev, select=None, n=None, stream=No
     return r.value
 
 
+def lbmfvm_save(h, path):
+    _check(lib().lbmfvm_save(h, os.fsencode(path)), h)
+
+
+def lbmfvm_load(h, path):
+    _check(lib().lbmfvm_load(h, os.fsencode(path)), h)
+
+
+def lbmfvm_checkpoint_info(path) -> dict:
+    """Header of the checkpoint at path, after its magic, sizes and CRCs are
+    verified (no GPU needed)."""
+    hd = lbmfvm_checkpoint_header_t()
+    _check(lib().lbmfvm_checkpoint_info(os.fsencode(path), ctypes.byref(hd)))
+    return dict(nx=hd.nx, ny=hd.ny, store=hd.store, steps=hd.steps, bc=tuple(hd.bc), t_wall=tuple(hd.t_wall),
+                u_lid=hd.u_lid, tau=hd.tau, alpha=hd.alpha, gbeta=hd.gbeta, t_ref=hd.t_ref, force=tuple(hd.force),
+                payload_bytes=hd.payload_bytes, code_crc=hd.code_crc, payload_crc=hd.payload_crc)
+
+
 def lbmfvm_destroy(h):
     if h:
         lib().lbmfvm_destroy(h)
@@ -363,6 +396,15 @@ class Cavity:
         """Take ``other``'s state (populations, temperature, step count,
         residual snapshot), converted to this cavity's storage precision."""
         lbmfvm_copy_state(self.h, other.h)
+
+    def save(self, path):
+        """Write this cavity's state to a checkpoint file."""
+        lbmfvm_save(self.h, path)
+
+    def load(self, path):
+        """Resume from a checkpoint saved by a cavity of the same geometry,
+        storage and parameters."""
+        lbmfvm_load(self.h, path)
 
 
 def _bcheck(code: int, b):

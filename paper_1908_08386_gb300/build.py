@@ -18,7 +18,7 @@ INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "liblbmfvm.so")
 SOURCES = [os.path.join(CSRC, "lbmfvm.cu"), os.path.join(CSRC, "residual_noalloc.cu"),
            os.path.join(CSRC, "surrogate.cu")]
-DEPS = SOURCES + [os.path.join(CSRC, "kernels.cuh"), os.path.join(CSRC, "batch.inl"),
+DEPS = SOURCES + [os.path.join(CSRC, "kernels.cuh"), os.path.join(CSRC, "batch.inl"), os.path.join(CSRC, "checkpoint.inl"),
                   os.path.join(INCLUDE, "lbmfvm.h"), os.path.join(INCLUDE, "surrogate.h")]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 

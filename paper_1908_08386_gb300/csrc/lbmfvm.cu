@@ -10,6 +10,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <map>
@@ -204,6 +205,10 @@ std::vector<uint8_t> classify(const lbmfvm_grid_t &g, const uint8_t *mask, int p
     return code;
 }
 
+// CRC-32 of n bytes continued from crc (0 to start); defined with the
+// checkpoint code.
+uint32_t crc32_update(uint32_t crc, const void *data, size_t n);
+
 // Face flags (FF_* bits) of every node of the given cavity rectangles of a
 // stored-code plane: the finite-volume update's control volume is clipped to
 // its cavity, and a face is open when the neighbour across it lies in the
@@ -257,6 +262,7 @@ struct lbmfvm {
     CUtensorMap map_fo[2], map_To[2];  // output-tile boxes of the TMA tile kernel
     int tma_blocks_per_sm;
     int ntiles;       // tiles of the TMA kernel
+    uint32_t code_crc; // CRC-32 of the node codes, identifies the geometry in checkpoints
     int tile_w, tile_h;
     // Several cavities packed in one grid (batch handles); empty for one cavity.
     std::vector<CavityDesc> atlas_cavs;
@@ -965,6 +971,7 @@ int create_impl(const lbmfvm_grid_t *grid, const uint8_t *mask, double nu, doubl
         rects[0].ny = grid->ny;
     }
     const std::vector<uint8_t> fflags = face_flags(code, L.pitch, rects);
+    h->code_crc = crc32_update(0, code.data(), code.size());
     if (join_in(h)) return bail(LBMFVM_ERR_CUDA);
     if (cudaMemsetAsync(h->base, 0, L.total, h->s) != cudaSuccess ||
         cudaMemcpyAsync(h->base + L.code, code.data(), code.size(), cudaMemcpyHostToDevice, h->s) != cudaSuccess ||
@@ -1241,3 +1248,4 @@ const char *lbmfvm_last_error(const lbmfvm_t *h) { return h ? h->err : g_err; }
 }  // extern "C"
 
 #include "batch.inl"
+#include "checkpoint.inl"
