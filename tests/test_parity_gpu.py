@@ -248,6 +248,25 @@ def test_full_size_cavity_sampled_against_oracle(store):
     assert d["du"] <= tol and d["dT"] <= tol, d
 
 
+def test_full_size_cavity_over_graph_replays_against_oracle():
+    """1024^2 in FP64 over 131 steps (two 64-step graph replays and three
+    single launches): enough tiles that the last rounds of each launch are
+    drawn from the shared tile counter, through both counter parities."""
+    case = WL.config_large()
+    n = case.nx
+    u, v = WL.random_velocity(n, n, seed=23, amp=0.01)
+    T = WL.random_temperature(n, n, seed=24)
+    gpu, orc = pair(n, n, Ra=case.Ra, Pr=case.Pr, store="f64")
+    gpu.set_state(u.astype(np.float32), v.astype(np.float32), T.astype(np.float32))
+    orc.set_state(u.astype(np.float32).astype(np.float64), v.astype(np.float32).astype(np.float64),
+                  T.astype(np.float32).astype(np.float64))
+    gpu.step(1)
+    gpu.step(130)
+    orc.step(131)
+    d = compare(gpu, orc)
+    assert d["du"] <= 1e-12 and d["dT"] <= 1e-12, d
+
+
 @pytest.mark.parametrize("kernel", ["tma", "generic"])
 @pytest.mark.parametrize("store", ["f16", "bf16"])
 def test_reduced_precision_steady_nusselt(store, kernel):
