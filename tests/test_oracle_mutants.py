@@ -18,6 +18,8 @@ MUTANTS = {
     "tau_without_half": ("o->tau = nu / CS2 + 0.5;", "o->tau = nu / CS2 + 0.6;"),
     "stream_push_direction": ("int s = nbr(o, i, j, -EX[q], -EY[q]);", "int s = nbr(o, i, j, -EX[q], EY[q]);"),
     "nee_partner_velocity": ("feq(q, rf, o->uw[k], o->vw[k])", "feq(q, rf, uf, vf)"),
+    "nee_wall_density_unit": ("feq(q, rf, o->uw[k], o->vw[k])", "feq(q, 1.0, o->uw[k], o->vw[k])"),
+    "nee_equilibrium_only": ("+ o->f[q * n + p] - feq(q, rf, uf, vf);", ";"),
     "fv_convective_sign": ("acc += -Fl * Tf + alpha", "acc += Fl * Tf + alpha"),
     "fv_face_velocity_one_sided": ("(o->ux[k] + o->ux[m]) * dx", "(o->ux[k] + o->ux[k]) * dx"),
     "fv_half_cv_y": ("return 0.5 * (j > 0) + 0.5 * (j < o->ny - 1);", "return 1.0;"),

@@ -25,6 +25,7 @@ PINS = [
     P.quadratic_nusselt,
     P.eq112_conduction,
     P.homogeneous_in_f,
+    P.nee_wall_moments,
 ]
 
 
