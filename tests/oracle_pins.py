@@ -176,6 +176,25 @@ def energy_adiabatic(make, n=1000):
     return rel <= 1e-13 and moving > 1e-5, f"relative energy change = {rel:.3g} (max|u| = {moving:.3g})"
 
 
+def energy_adiabatic_obstacle(make, n=800):
+    """An insulated obstacle in an adiabatic box with buoyant flow: its
+    surface faces carry no flux (its nodes copy their partner's temperature
+    and take no part in the balance), so sum V_P T_P over the finite-volume
+    nodes stays constant to round-off."""
+    rng = np.random.default_rng(5)
+    mask = np.zeros((19, 24), np.uint8)
+    mask[6:11, 8:14] = 1
+    o = make(24, 19, bc=(ADI, ADI, ADI, ADI), mask=mask, nu=0.05, alpha=0.15, gbeta=2e-3, t_ref=0.5)
+    o.set_state(T=rng.random((19, 24)))
+    V = o.cv_volumes()
+    e0 = np.sum(V * o.fields()[3])
+    o.step(n)
+    _, u, _, T = o.fields()
+    rel = abs(np.sum(V * T) - e0) / e0
+    moving = np.abs(u).max()
+    return rel <= 1e-13 and moving > 1e-5, f"relative energy change = {rel:.3g} (max|u| = {moving:.3g})"
+
+
 def quadratic_nusselt(make, H=20):
     """Eq. 90 from the one-sided second-order stencil is exact for T quadratic
     in x: T = 1 - X + c(Y) X (X - 1) gives Nu(Y) = 1 + c(Y); with c linear in Y
@@ -279,6 +298,7 @@ QUICK = {
     "cosine_mode_y": cosine_mode_y,
     "advected_temperature": advected_temperature,
     "energy_adiabatic": energy_adiabatic,
+    "energy_adiabatic_obstacle": energy_adiabatic_obstacle,
     "quadratic_nusselt": quadratic_nusselt,
     "homogeneous_in_f": homogeneous_in_f,
     "nee_wall_moments": nee_wall_moments,

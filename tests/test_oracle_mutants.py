@@ -21,6 +21,8 @@ MUTANTS = {
     "nee_wall_density_unit": ("feq(q, rf, o->uw[k], o->vw[k])", "feq(q, 1.0, o->uw[k], o->vw[k])"),
     "nee_equilibrium_only": ("+ o->f[q * n + p] - feq(q, rf, uf, vf);", ";"),
     "fv_convective_sign": ("acc += -Fl * Tf + alpha", "acc += Fl * Tf + alpha"),
+    "fv_obstacle_faces_open": ("(o->therm[k] == TH_FV || o->therm[k] == TH_DIRICHLET)",
+                               "(o->therm[k] == TH_FV || o->therm[k] == TH_DIRICHLET || o->therm[k] == TH_OBSTACLE)"),
     "fv_face_velocity_one_sided": ("(o->ux[k] + o->ux[m]) * dx", "(o->ux[k] + o->ux[k]) * dx"),
     "fv_half_cv_y": ("return 0.5 * (j > 0) + 0.5 * (j < o->ny - 1);", "return 1.0;"),
     "fv_diffusion_area": ("alpha * A * (o->T[m] - TP)", "alpha * (o->T[m] - TP)"),

@@ -22,6 +22,7 @@ PINS = [
     P.cosine_mode_y,
     P.advected_temperature,
     P.energy_adiabatic,
+    P.energy_adiabatic_obstacle,
     P.quadratic_nusselt,
     P.eq112_conduction,
     P.homogeneous_in_f,
