@@ -176,6 +176,22 @@ def energy_adiabatic(make, n=1000):
     return rel <= 1e-13 and moving > 1e-5, f"relative energy change = {rel:.3g} (max|u| = {moving:.3g})"
 
 
+def uniform_buoyancy(make, n=100, T=0.7, t_ref=0.5, gbeta=1e-4):
+    """A periodic box at a uniform temperature T: the Boussinesq force of
+    Eqs. 18 and 81, G = g beta (T - T_ref) upward, is the same at every node,
+    the field stays uniform, the energy update leaves T unchanged, and the
+    force's momentum source sum_i e_i F_i = rho G makes v grow by exactly G
+    per step (rho = 1): v = n G after n steps from rest."""
+    o = make(16, 12, bc=(PER, PER, PER, PER), nu=0.05, alpha=0.1, gbeta=gbeta, t_ref=t_ref)
+    o.set_state(T=np.full((12, 16), T))
+    o.step(n)
+    _, u, v, Tn = o.fields()
+    G = gbeta * (T - t_ref)
+    rel = abs(v.mean() / (n * G) - 1)
+    ok = rel <= 1e-11 and np.ptp(v) <= 1e-18 and np.all(u == 0.0) and np.all(Tn == T)
+    return ok, f"v / (n G) - 1 = {rel:.3g}, spread of v {np.ptp(v):.3g}, max|u| = {np.abs(u).max():.3g}"
+
+
 def energy_adiabatic_obstacle(make, n=800):
     """An insulated obstacle in an adiabatic box with buoyant flow: its
     surface faces carry no flux (its nodes copy their partner's temperature
@@ -299,6 +315,7 @@ QUICK = {
     "advected_temperature": advected_temperature,
     "energy_adiabatic": energy_adiabatic,
     "energy_adiabatic_obstacle": energy_adiabatic_obstacle,
+    "uniform_buoyancy": uniform_buoyancy,
     "quadratic_nusselt": quadratic_nusselt,
     "homogeneous_in_f": homogeneous_in_f,
     "nee_wall_moments": nee_wall_moments,

@@ -14,6 +14,7 @@ MUTANTS = {
     "feq_drop_u2": ("- uu / (2.0 * CS2))", ")"),
     "force_drop_minus_u": ("(Gx * (EX[q] - ux) + Gy * (EY[q] - uy))", "(Gx * EX[q] + Gy * EY[q])"),
     "force_missing_cs2": ("* fe / (RHO0 * CS2);", "* fe / RHO0;"),
+    "force_without_reference_temperature": ("o->gbeta * (o->T[k] - o->t_ref)", "o->gbeta * o->T[k]"),
     "weight_diagonal": ("1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0}", "1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 35.0}"),
     "tau_without_half": ("o->tau = nu / CS2 + 0.5;", "o->tau = nu / CS2 + 0.6;"),
     "stream_push_direction": ("int s = nbr(o, i, j, -EX[q], -EY[q]);", "int s = nbr(o, i, j, -EX[q], EY[q]);"),

@@ -23,6 +23,7 @@ PINS = [
     P.advected_temperature,
     P.energy_adiabatic,
     P.energy_adiabatic_obstacle,
+    P.uniform_buoyancy,
     P.quadratic_nusselt,
     P.eq112_conduction,
     P.homogeneous_in_f,
