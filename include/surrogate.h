@@ -3,7 +3,7 @@
  * initial (u/U0, v/U0, T) for the LBM-FVM iteration, trained on steady fields
  * that the batched solver generates.  The paper has no such network; the
  * iteration started from the predicted state runs to the same residual as
- * from rest, so it is both the fallback and the judge of the prediction.
+ * from rest, so it is both the fallback and the measure of the prediction's error.
  *
  * Conventions (every entry point):
  * - BF16 tensors are passed as uint16_t pointers (IEEE bfloat16 bit
