@@ -94,6 +94,9 @@ def load_library(path: str):
     lib.orc_cv_volumes.argtypes = [vp, vp]
     lib.orc_params_from_groups.argtypes = [d, d, d, d, d, dp, dp, dp, dp]
     lib.orc_num_threads.restype = i
+    if hasattr(lib, "orc_set_fv"):
+        lib.orc_set_fv.restype = i
+        lib.orc_set_fv.argtypes = [vp, i, i]
     return lib
 
 
@@ -123,7 +126,8 @@ class Oracle:
 
     def __init__(self, nx, ny, *, bc=(BC_DIRICHLET, BC_DIRICHLET, BC_ADIABATIC, BC_ADIABATIC),
                  t_wall=(1.0, 0.0, 0.0, 0.0), u_lid=0.0, t_init=0.5, mask=None,
-                 nu, alpha, gbeta=0.0, t_ref=None, fx=0.0, fy=0.0, lib=None):
+                 nu, alpha, gbeta=0.0, t_ref=None, fx=0.0, fy=0.0, fv_scheme="central", fv_substeps=1,
+                 lib=None):
         lib = lib if lib is not None else _load()
         self.nx, self.ny = int(nx), int(ny)
         self.t_wall = tuple(float(t) for t in t_wall)
@@ -141,6 +145,11 @@ class Oracle:
             raise ValueError("oracle: invalid grid or boundary configuration")
         self._h = ctypes.c_void_p(h)
         self._lib = lib
+        if fv_scheme not in ("central", "quick"):
+            raise ValueError(f"oracle: fv_scheme must be 'central' or 'quick', not {fv_scheme!r}")
+        if (fv_scheme, fv_substeps) != ("central", 1):
+            if lib.orc_set_fv(self._h, int(fv_scheme == "quick"), int(fv_substeps)) != 0:
+                raise ValueError(f"oracle: fv_substeps must be >= 1 (got {fv_substeps})")
         self.nu, self.alpha, self.gbeta = float(nu), float(alpha), float(gbeta)
         self.t_init = float(t_init)
 

@@ -40,6 +40,17 @@
  *   - Obstacle wall nodes (solid nodes with a fluid 8-neighbour) take
  *     T^{n+1}(b) = T^n(x_f); faces to them carry no heat flux (adiabatic).
  *
+ * Options of the energy update (orc_set_fv; off by default):
+ *   - QUICK face values, the scheme Section 3.1 names for its finite-volume
+ *     solver (Leonard's quadratic upstream interpolation): on a face with
+ *     flow from U to D, T_f = 6/8 T_U + 3/8 T_D - 1/8 T_UU, UU the node
+ *     beyond U; where UU takes no part in the energy balance (a wall, an
+ *     obstacle, outside the box) the face keeps the central value.
+ *   - Sub-cycling: m explicit sub-steps of dt/m per lattice step with the
+ *     velocity u^{n+1} held, so that alpha up to m/4 stays inside the
+ *     explicit diffusion limit; obstacle wall nodes copy their partner's
+ *     temperature at every sub-step.
+ *
  * D2Q9 numbering used here (results do not depend on it): 0 rest, 1 E, 2 N,
  * 3 W, 4 S, 5 NE, 6 NW, 7 SW, 8 SE.  Weights from Eq. 9, c_s^2 = 1/3.
  *
@@ -90,6 +101,8 @@ typedef struct {
     double *rho, *ux, *uy; /* moments of f^n */
     double *su, *sv;       /* residual snapshot */
     long step;
+    int fv_quick;          /* QUICK face values instead of central ones */
+    int fv_substeps;       /* explicit FV sub-steps per lattice step (>= 1) */
 } orc_t;
 
 static int wrap(int i, int n) {
@@ -315,9 +328,20 @@ orc_t *orc_create(int nx, int ny, const int bc[4], const double t_wall[4], doubl
         orc_destroy(o);
         return NULL;
     }
+    o->fv_quick = 0;
+    o->fv_substeps = 1;
     classify(o, mask);
     orc_set_state(o, NULL, NULL, NULL, t_init);
     return o;
+}
+
+/* Energy-update options: quick = 1 for QUICK face values, substeps >= 1.
+ * Returns -1 (nothing changed) for substeps < 1. */
+int orc_set_fv(orc_t *o, int quick, int substeps) {
+    if (substeps < 1) return -1;
+    o->fv_quick = quick != 0;
+    o->fv_substeps = substeps;
+    return 0;
 }
 
 /* Control-volume extent of node (i, j) along x or y: the node-centred cell
@@ -393,36 +417,54 @@ static void step_once(orc_t *o) {
     /* 6. explicit FV energy balance on node-centred control volumes:
      *    V_P (T^{n+1} - T^n) = sum over open faces of
      *        -F_f T_f + alpha A_f (T_nb - T_P),
-     *    F_f = A_f u_face.n_out, u_face = (u_P + u_nb)/2, T_f = (T_P + T_nb)/2.
+     *    F_f = A_f u_face.n_out, u_face = (u_P + u_nb)/2, T_f = (T_P + T_nb)/2
+     *    (or the QUICK value, see the header).
      *    A face is open when both sides take part in the FV balance; box walls
-     *    and faces to obstacle/inert nodes carry no flux. */
+     *    and faces to obstacle/inert nodes carry no flux.  With m sub-steps
+     *    the balance is applied m times with dt = 1/m. */
+    const int m_sub = o->fv_substeps;
+    const double dt = 1.0 / m_sub;
+    for (int sub = 0; sub < m_sub; sub++) {
+        if (sub > 0) { double *t = o->T; o->T = o->Tn; o->Tn = t; }
 #pragma omp parallel for schedule(static) if (PARALLEL(o))
-    for (int j = 0; j < ny; j++)
-        for (int i = 0; i < nx; i++) {
-            long k = (long)j * nx + i;
-            int th = o->therm[k];
-            if (th == TH_FV) {
-                double ex = extent_x(o, i), ey = extent_y(o, j);
-                double V = ex * ey, TP = o->T[k], acc = 0.0;
-                /* faces E, N, W, S: outward normal (nx_, ny_), area */
-                static const int FD[4][2] = {{1, 0}, {0, 1}, {-1, 0}, {0, -1}};
-                for (int fc = 0; fc < 4; fc++) {
-                    int dx = FD[fc][0], dy = FD[fc][1];
-                    int m = nbr(o, i, j, dx, dy);
-                    if (!fv_member(o, m)) continue;
-                    double A = (dx != 0) ? ey : ex;
-                    double un = 0.5 * ((o->ux[k] + o->ux[m]) * dx + (o->uy[k] + o->uy[m]) * dy);
-                    double Fl = A * un;
-                    double Tf = 0.5 * (TP + o->T[m]);
-                    acc += -Fl * Tf + alpha * A * (o->T[m] - TP);
+        for (int j = 0; j < ny; j++)
+            for (int i = 0; i < nx; i++) {
+                long k = (long)j * nx + i;
+                int th = o->therm[k];
+                if (th == TH_FV) {
+                    double ex = extent_x(o, i), ey = extent_y(o, j);
+                    double V = ex * ey, TP = o->T[k], acc = 0.0;
+                    /* faces E, N, W, S: outward normal (nx_, ny_), area */
+                    static const int FD[4][2] = {{1, 0}, {0, 1}, {-1, 0}, {0, -1}};
+                    for (int fc = 0; fc < 4; fc++) {
+                        int dx = FD[fc][0], dy = FD[fc][1];
+                        int mm = nbr(o, i, j, dx, dy);
+                        if (!fv_member(o, mm)) continue;
+                        double A = (dx != 0) ? ey : ex;
+                        double un = 0.5 * ((o->ux[k] + o->ux[mm]) * dx + (o->uy[k] + o->uy[mm]) * dy);
+                        double Fl = A * un;
+                        double Tf = 0.5 * (TP + o->T[mm]);
+                        if (o->fv_quick) {
+                            /* upstream node U, downstream D, and UU beyond U */
+                            int up, down, far;
+                            if (un >= 0.0) {
+                                up = (int)k; down = mm; far = nbr(o, i, j, -dx, -dy);
+                            } else {
+                                up = mm; down = (int)k; far = nbr(o, i + dx, j + dy, dx, dy);
+                            }
+                            if (fv_member(o, far))
+                                Tf = 0.75 * o->T[up] + 0.375 * o->T[down] - 0.125 * o->T[far];
+                        }
+                        acc += -Fl * Tf + alpha * A * (o->T[mm] - TP);
+                    }
+                    o->Tn[k] = TP + dt * acc / V;
+                } else if (th == TH_OBSTACLE) {
+                    o->Tn[k] = o->T[o->partner[k]];
+                } else {
+                    o->Tn[k] = o->T[k]; /* Dirichlet value held, inert unchanged */
                 }
-                o->Tn[k] = TP + acc / V;
-            } else if (th == TH_OBSTACLE) {
-                o->Tn[k] = o->T[o->partner[k]];
-            } else {
-                o->Tn[k] = o->T[k]; /* Dirichlet value held, inert unchanged */
             }
-        }
+    }
     double *t = o->T; o->T = o->Tn; o->Tn = t;
     o->step++;
 }

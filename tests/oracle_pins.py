@@ -161,6 +161,74 @@ def advected_temperature(make, L=32, n=200, alpha=0.05):
     return err <= 1e-11, f"max error vs exact discrete mode = {err:.3g}"
 
 
+def _quick_factor(c, kappa):
+    """(T_f+ - T_f-) / T_P for a Fourier mode exp(i kappa j) under QUICK face
+    values (6/8 upstream, 3/8 downstream, -1/8 beyond upstream) with a
+    uniform velocity c along the axis: for c >= 0 the faces take their values
+    from the node behind them, for c < 0 from the node ahead (the mirror)."""
+    def qp(k):
+        e = np.exp(1j * k)
+        return (3 + 3 * e - 7 / e + 1 / (e * e)) / 8
+    return qp(kappa) if c >= 0 else -qp(-kappa)
+
+
+def quick_advected_mode(make, L=32, n=200, alpha=0.05, substeps=1):
+    """QUICK face values (Section 3.1's scheme, Leonard's quadratic upstream
+    interpolation) on a uniform stream (U, V) in a periodic box: the explicit
+    update multiplies the Fourier mode cos(k x + l y) by
+    g = (1 + L_h / m)^m per step, L_h = -4 alpha (sin^2(k/2) + sin^2(l/2))
+    - U Q(k) - V Q(l) with Q the QUICK flux-difference symbol and m the
+    sub-steps."""
+    U, V = 0.06, -0.03
+    o = make(L, L, bc=(PER, PER, PER, PER), nu=0.1, alpha=alpha, gbeta=0.0, fv_scheme="quick",
+             fv_substeps=substeps)
+    k = 2 * np.pi * 2 / L
+    l = 2 * np.pi * 1 / L
+    yy, xx = np.mgrid[0:L, 0:L]
+    o.set_state(u=np.full((L, L), U), v=np.full((L, L), V), T=0.5 + 0.1 * np.cos(k * xx + l * yy))
+    o.step(n)
+    Lh = -4 * alpha * (math.sin(k / 2) ** 2 + math.sin(l / 2) ** 2) - U * _quick_factor(U, k) - V * _quick_factor(V, l)
+    g = (1 + Lh / substeps) ** substeps
+    exact = 0.5 + 0.1 * np.real(g**n * np.exp(1j * (k * xx + l * yy)))
+    err = np.abs(o.fields()[3] - exact).max()
+    central = abs(1 - 4 * alpha * (math.sin(k / 2) ** 2 + math.sin(l / 2) ** 2)
+                  - 1j * (U * math.sin(k) + V * math.sin(l))) ** n
+    return err <= 1e-11, f"max error vs exact discrete mode = {err:.3g} (|g|^n {abs(g)**n:.6f}, central {central:.6f})"
+
+
+def subcycled_sine_mode(make, H=20, n=300, alpha=0.6, substeps=3):
+    """alpha = 0.6 exceeds the explicit limit 1/4 of one step; with m = 3
+    sub-steps of dt = 1/3 the Dirichlet sine mode decays by exactly
+    (1 - 4 (alpha/m) sin^2(pi/(2H)))^m per step."""
+    o = make(H + 1, 9, t_wall=(0, 0, 0, 0), nu=0.1, alpha=alpha, gbeta=0.0, fv_substeps=substeps)
+    x = np.arange(H + 1)
+    T0 = np.tile(np.sin(np.pi * x / H), (9, 1))
+    o.set_state(T=T0)
+    o.step(n)
+    g = (1 - 4 * (alpha / substeps) * math.sin(math.pi / (2 * H)) ** 2) ** substeps
+    err = np.abs(o.fields()[3] - g**n * T0).max()
+    return err <= 1e-12, f"max error vs exact discrete decay = {err:.3g} (factor {g**n:.6f})"
+
+
+def quick_energy_adiabatic(make, n=600):
+    """QUICK face values and two sub-steps in an adiabatic box with buoyant
+    flow and an insulated obstacle: every face's value is shared by its two
+    nodes, so sum V_P T_P stays constant to round-off."""
+    rng = np.random.default_rng(9)
+    mask = np.zeros((19, 24), np.uint8)
+    mask[6:11, 8:14] = 1
+    o = make(24, 19, bc=(ADI, ADI, ADI, ADI), mask=mask, nu=0.05, alpha=0.3, gbeta=2e-3, t_ref=0.5,
+             fv_scheme="quick", fv_substeps=2)
+    o.set_state(T=rng.random((19, 24)))
+    V = o.cv_volumes()
+    e0 = np.sum(V * o.fields()[3])
+    o.step(n)
+    _, u, _, T = o.fields()
+    rel = abs(np.sum(V * T) - e0) / e0
+    moving = np.abs(u).max()
+    return rel <= 1e-13 and moving > 1e-5, f"relative energy change = {rel:.3g} (max|u| = {moving:.3g})"
+
+
 def energy_adiabatic(make, n=1000):
     """All walls adiabatic, buoyant flow from a random T: the conservative
     flux form keeps sum V_P T_P constant to round-off."""
@@ -316,6 +384,10 @@ QUICK = {
     "energy_adiabatic": energy_adiabatic,
     "energy_adiabatic_obstacle": energy_adiabatic_obstacle,
     "uniform_buoyancy": uniform_buoyancy,
+    "quick_advected_mode": quick_advected_mode,
+    "quick_advected_mode_subcycled": lambda m: quick_advected_mode(m, n=100, substeps=2),
+    "subcycled_sine_mode": subcycled_sine_mode,
+    "quick_energy_adiabatic": lambda m: quick_energy_adiabatic(m, 300),
     "quadratic_nusselt": quadratic_nusselt,
     "homogeneous_in_f": homogeneous_in_f,
     "nee_wall_moments": nee_wall_moments,

@@ -22,11 +22,15 @@ MUTANTS = {
     "nee_wall_density_unit": ("feq(q, rf, o->uw[k], o->vw[k])", "feq(q, 1.0, o->uw[k], o->vw[k])"),
     "nee_equilibrium_only": ("+ o->f[q * n + p] - feq(q, rf, uf, vf);", ";"),
     "fv_convective_sign": ("acc += -Fl * Tf + alpha", "acc += Fl * Tf + alpha"),
+    "quick_downstream_weight": ("0.375 * o->T[down]", "0.25 * o->T[down]"),
+    "quick_upstream_side": ("if (un >= 0.0) {", "if (un < 0.0) {"),
+    "quick_far_node": ("far = nbr(o, i, j, -dx, -dy);", "far = nbr(o, i, j, dx, dy);"),
+    "subcycle_full_step": ("const double dt = 1.0 / m_sub;", "const double dt = 1.0;"),
     "fv_obstacle_faces_open": ("(o->therm[k] == TH_FV || o->therm[k] == TH_DIRICHLET)",
                                "(o->therm[k] == TH_FV || o->therm[k] == TH_DIRICHLET || o->therm[k] == TH_OBSTACLE)"),
-    "fv_face_velocity_one_sided": ("(o->ux[k] + o->ux[m]) * dx", "(o->ux[k] + o->ux[k]) * dx"),
+    "fv_face_velocity_one_sided": ("(o->ux[k] + o->ux[mm]) * dx", "(o->ux[k] + o->ux[k]) * dx"),
     "fv_half_cv_y": ("return 0.5 * (j > 0) + 0.5 * (j < o->ny - 1);", "return 1.0;"),
-    "fv_diffusion_area": ("alpha * A * (o->T[m] - TP)", "alpha * (o->T[m] - TP)"),
+    "fv_diffusion_area": ("alpha * A * (o->T[mm] - TP)", "alpha * (o->T[mm] - TP)"),
     "nusselt_first_order": ("(-3.0 * r[0] + 4.0 * r[1] - r[2]) / (2.0 * dT)", "(-r[0] + r[1]) / dT"),
     "nusselt_trapezoid": ("(j == 0 || j == ny - 1) ? 0.5 : 1.0", "1.0"),
 }

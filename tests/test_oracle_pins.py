@@ -24,6 +24,9 @@ PINS = [
     P.energy_adiabatic,
     P.energy_adiabatic_obstacle,
     P.uniform_buoyancy,
+    P.quick_advected_mode,
+    P.subcycled_sine_mode,
+    P.quick_energy_adiabatic,
     P.quadratic_nusselt,
     P.eq112_conduction,
     P.homogeneous_in_f,
@@ -69,3 +72,15 @@ def test_thread_count_does_not_change_results():
             import numpy as np
             outs.append(np.load(path))
         assert (outs[0] == outs[1]).all()
+
+
+def test_quick_with_subcycling_matches_its_closed_form():
+    ok, detail = P.quick_advected_mode(make, n=100, substeps=2)
+    assert ok, detail
+
+
+def test_fv_options_are_checked():
+    with pytest.raises(ValueError):
+        oracle.Oracle(8, 8, nu=0.1, alpha=0.1, fv_scheme="upwind")
+    with pytest.raises(ValueError):
+        oracle.Oracle(8, 8, nu=0.1, alpha=0.1, fv_substeps=0)
