@@ -104,16 +104,20 @@ def poiseuille(make, Hs=(8, 16, 32)):
 
 def conduction_linear(make, H=16):
     """Pure conduction between T = 1 (west) and T = 0 (east), adiabatic top
-    and bottom: the steady field is T = 1 - x/H to round-off and the one-sided
-    Nusselt number is exactly 1."""
+    and bottom: the steady field is T = 1 - x/H to round-off, and the
+    one-sided Nusselt number and the heat through every vertical face line
+    (normalised by alpha dT) are exactly 1."""
     o = make(H + 1, H + 1, nu=0.1, alpha=0.2, gbeta=0.0)
     o.step(6000)
     T = o.fields()[3]
     x = np.arange(H + 1) / H
     err = np.abs(T - (1 - x)[None, :]).max()
     nh, _, nc, _ = o.nusselt()
-    ok = err <= 1e-12 and abs(nh - 1) <= 1e-12 and abs(nc - 1) <= 1e-12
-    return ok, f"max|T - (1 - x/H)| = {err:.3g}, Nu hot - 1 = {nh - 1:.3g}, Nu cold - 1 = {nc - 1:.3g}"
+    # the heat through every vertical face line is alpha dT (H/H): Nu = 1
+    fl = np.abs(o.flux_nusselt() - 1).max()
+    ok = err <= 1e-12 and abs(nh - 1) <= 1e-12 and abs(nc - 1) <= 1e-12 and fl <= 1e-12
+    return ok, (f"max|T - (1 - x/H)| = {err:.3g}, Nu hot - 1 = {nh - 1:.3g}, Nu cold - 1 = {nc - 1:.3g}, "
+                f"max|flux Nu - 1| = {fl:.3g}")
 
 
 def sine_mode_x(make, H=20, n=500, alpha=0.2):
@@ -371,6 +375,52 @@ def nee_wall_moments(make, u_lid=0.04):
     return ok, f"max|rho_b - rho_f| = {drho:.3g}, max|u_b - u_w| = {du:.3g} over {len(walls)} wall nodes"
 
 
+def residual_shear_wave(make, K=200):
+    """Residual ||u^{n+K} - u^n|| / ||u^{n+K}|| of a decaying periodic shear
+    wave u_x = A sin(k y): every node's velocity shrinks by the same factor
+    g = exp(-nu k^2 K) over K steps (Eq. 15), so the residual is the closed
+    form (1 - g)/g.  A residual without the square roots gives its square, one
+    normalised by the earlier snapshot gives 1 - g."""
+    L, nu, A = 64, 0.1, 1e-4
+    o = make(3, L, bc=(PER, PER, PER, PER), nu=nu, alpha=0.1, gbeta=0.0)
+    y = np.arange(L)
+    o.set_state(u=np.tile(A * np.sin(2 * np.pi * y / L)[:, None], (1, 3)))
+    o.step(300)  # the non-equilibrium part settles in a few relaxation times
+    o.residual()  # snapshot at step 300
+    o.step(K)
+    r = o.residual()
+    k = 2 * np.pi / L
+    g = math.exp(-nu * k * k * K)
+    want = (1 - g) / g
+    rel = abs(r / want - 1)
+    return rel <= 0.005, f"residual {r:.6g} against (1 - g)/g = {want:.6g} (rel. {rel:.3g})"
+
+
+def residual_cavity_fluid_nodes(make, K=150):
+    """Residual of a lid-driven buoyant cavity with an obstacle against the
+    definition evaluated from two field snapshots over the fluid nodes only:
+    wall nodes (the lid moves at u_lid, obstacle surfaces rest) take no part,
+    so including them would change the denominator."""
+    ny, nx = 24, 30
+    mask = np.zeros((ny, nx), np.uint8)
+    mask[9:14, 11:17] = 1
+    o = make(nx, ny, bc=(DIR, DIR, ADI, MOV), u_lid=0.05, mask=mask, nu=0.06, alpha=0.08, gbeta=4e-4)
+    o.step(100)
+    o.residual()
+    _, u0, v0, _ = o.fields()
+    o.step(K)
+    r = o.residual()
+    _, u1, v1, _ = o.fields()
+    fluid = o.classes()[0] == 0
+    num = np.sum((u1 - u0)[fluid] ** 2 + (v1 - v0)[fluid] ** 2)
+    den = np.sum(u1[fluid] ** 2 + v1[fluid] ** 2)
+    want = math.sqrt(num) / math.sqrt(den)
+    lid_share = np.sum(u1[~fluid] ** 2) / den
+    rel = abs(r / want - 1)
+    ok = rel <= 1e-12 and want > 1e-3 and lid_share > 1e-2
+    return ok, f"residual {r:.9g} against {want:.9g} from two snapshots (rel. {rel:.3g}; walls would add {lid_share:.3g} of the denominator)"
+
+
 QUICK = {
     "rest_state": rest_state,
     "mass_periodic": lambda m: mass_periodic(m, 2000),
@@ -391,4 +441,6 @@ QUICK = {
     "quadratic_nusselt": quadratic_nusselt,
     "homogeneous_in_f": homogeneous_in_f,
     "nee_wall_moments": nee_wall_moments,
+    "residual_shear_wave": residual_shear_wave,
+    "residual_cavity_fluid_nodes": residual_cavity_fluid_nodes,
 }

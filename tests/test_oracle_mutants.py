@@ -33,6 +33,12 @@ MUTANTS = {
     "fv_diffusion_area": ("alpha * A * (o->T[mm] - TP)", "alpha * (o->T[mm] - TP)"),
     "nusselt_first_order": ("(-3.0 * r[0] + 4.0 * r[1] - r[2]) / (2.0 * dT)", "(-r[0] + r[1]) / dT"),
     "nusselt_trapezoid": ("(j == 0 || j == ny - 1) ? 0.5 : 1.0", "1.0"),
+    "flux_nusselt_diffusion_area": ("Qs += A * un * Tf - o->alpha * A * (o->T[m] - o->T[k]);",
+                                    "Qs += A * un * Tf - o->alpha * (o->T[m] - o->T[k]);"),
+    "residual_without_square_roots": ("return sqrt(num) / sqrt(den);", "return num / den;"),
+    "residual_normalised_by_snapshot": ("den += o->ux[k] * o->ux[k] + o->uy[k] * o->uy[k];",
+                                        "den += o->su[k] * o->su[k] + o->sv[k] * o->sv[k];"),
+    "residual_walls_included": ("if (o->kind[k] != K_FLUID) continue;\n        double du", "if (o->kind[k] == K_SOLID) continue;\n        double du"),
 }
 
 

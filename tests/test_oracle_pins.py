@@ -31,6 +31,8 @@ PINS = [
     P.eq112_conduction,
     P.homogeneous_in_f,
     P.nee_wall_moments,
+    P.residual_shear_wave,
+    P.residual_cavity_fluid_nodes,
 ]
 
 
