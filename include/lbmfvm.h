@@ -238,9 +238,9 @@ int lbmfvm_params(const lbmfvm_t *h, double *nu, double *alpha, double *gbeta, d
 
 /* The residual of lbmfvm_residual computed on caller arrays without any
  * device allocation (the paper has no counterpart; this is a service for
- * callers that cannot allocate: code running under CUDA graph capture, code
- * whose device memory belongs to another allocator, loops that cannot pay for
- * cudaMalloc's implicit synchronisation).
+ * callers that cannot allocate: code whose device memory belongs to another
+ * allocator, such as a framework's caching allocator or a fixed arena, and
+ * loops that cannot pay for cudaMalloc's implicit synchronisation).
  *   r = ||(u, v) - (u_prev, v_prev)||_2 / ||(u, v)||_2 in FP64 over the nodes
  *   with select[i] != 0 (all n nodes if select is NULL).
  * u, v, u_prev, v_prev: device arrays of n doubles; select: device array of n
@@ -250,8 +250,9 @@ int lbmfvm_params(const lbmfvm_t *h, double *nu, double *alpha, double *gbeta, d
  * partial sums + 2 totals) that every GPU loading the library keeps until the
  * process exits; n is limited to [1, 2^30] (LBMFVM_ERR_ARG beyond).  The first
  * call on a device looks up the array's device address with
- * cudaGetSymbolAddress (with that device current), so make that first call
- * before any stream capture.  Every call shares the array: calls that overlap
+ * cudaGetSymbolAddress (with that device current); make that first call
+ * before any stream capture begins.  The call synchronises `stream` and copies
+ * the two totals to the host before it returns.  Every call shares the array: calls that overlap
  * on the GPU (on different streams, or from several host threads) race and
  * must be serialised by the caller.  Calls no cudaMalloc, cudaFree or other
  * allocating routine.  Returns LBMFVM_ERR_DIVERGED if a sum is not finite. */

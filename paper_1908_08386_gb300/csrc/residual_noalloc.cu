@@ -1,15 +1,16 @@
 // lbmfvm_residual_noalloc: the steady-state residual reduction on caller
 // arrays, for callers that cannot allocate device memory.
 //
-// Some callers of this library cannot call cudaMalloc: code that runs while a
-// CUDA graph is being captured (allocation calls are not allowed there),
-// code whose device memory is entirely owned by another allocator (a
-// framework's caching allocator or a fixed arena handed out at start-up), and
-// latency-critical loops that cannot afford the implicit device-wide
-// synchronisation of cudaMalloc/cudaFree.  This entry point allocates
-// nothing: the reduction's scratch (per-block partial sums) lives in a
-// file-scope __device__ array of fixed size that every GPU loading the
-// library holds until the process exits.
+// Some callers of this library cannot call cudaMalloc: code whose device
+// memory is entirely owned by another allocator (a framework's caching
+// allocator, or a fixed arena handed out at start-up, where a stray
+// cudaMalloc would fail or fragment the pool) and latency-critical loops that
+// cannot afford the implicit device-wide synchronisation of
+// cudaMalloc/cudaFree.  This entry point allocates nothing: the reduction's
+// scratch (per-block partial sums) lives in a file-scope __device__ array of
+// fixed size that every GPU loading the library holds until the process
+// exits.  The call waits for its stream and copies the two totals to the
+// host before it returns.
 #include <cuda_runtime.h>
 
 #include <cmath>

@@ -1,6 +1,6 @@
 """lbmfvm_residual_noalloc: the residual reduction without any device
-allocation, for callers that cannot allocate (graph capture, memory owned by
-another allocator, loops that cannot afford cudaMalloc's synchronisation).
+allocation, for callers that cannot allocate (device memory owned by another
+allocator, loops that cannot afford cudaMalloc's synchronisation).
 
 Checked through the C-ABI against the handle's own lbmfvm_residual on two
 calls in a row, within the FP64 tolerance of two reductions that add the same
