@@ -355,9 +355,11 @@ typedef struct {
 } lbmfvm_checkpoint_header_t;
 
 /* Write the state of h (after all work enqueued on its stream) to the file
- * at path.  Single-cavity handles only.  Synchronises.  LBMFVM_ERR_IO if the
- * file cannot be written; LBMFVM_ERR_TIMEOUT if an earlier step reported a
- * wait that ran out (the state is then not written). */
+ * at path.  Single-cavity handles only.  Synchronises.  The file is written
+ * as path.tmp, flushed to the disk and then renamed over path, so a save that
+ * fails part-way leaves any earlier checkpoint at path intact.  LBMFVM_ERR_IO
+ * if the file cannot be written; LBMFVM_ERR_TIMEOUT if an earlier step
+ * reported a wait that ran out (the state is then not written). */
 int lbmfvm_save(lbmfvm_t *h, const char *path);
 
 /* Replace the state of h by the one saved at path: populations,

@@ -170,12 +170,21 @@ int lbmfvm_save(lbmfvm_t *h, const char *path) {
     hd.payload_crc = crc32_update(0, payload.data(), payload.size());
     hd.header_crc = crc32_update(0, &hd, offsetof(lbmfvm_checkpoint_header_t, header_crc));
 
-    FILE *f = std::fopen(path, "wb");
-    if (!f) return fail(h, LBMFVM_ERR_IO, "cannot open %s for writing", path);
-    const bool ok = std::fwrite(&hd, 1, sizeof(hd), f) == sizeof(hd) &&
-                    std::fwrite(payload.data(), 1, payload.size(), f) == payload.size();
-    const bool closed = std::fclose(f) == 0;
-    if (!ok || !closed) return fail(h, LBMFVM_ERR_IO, "writing checkpoint %s failed", path);
+    // Written to path.tmp, flushed to the disk, then renamed over path: a
+    // save that fails part-way (a full disk, a killed process) leaves the
+    // previous checkpoint at path intact.
+    const std::string tmp = std::string(path) + ".tmp";
+    FILE *f = std::fopen(tmp.c_str(), "wb");
+    if (!f) return fail(h, LBMFVM_ERR_IO, "cannot open %s for writing", tmp.c_str());
+    bool ok = std::fwrite(&hd, 1, sizeof(hd), f) == sizeof(hd) &&
+              std::fwrite(payload.data(), 1, payload.size(), f) == payload.size();
+    ok = ok && std::fflush(f) == 0 && fsync(fileno(f)) == 0;
+    ok = std::fclose(f) == 0 && ok;
+    if (ok) ok = std::rename(tmp.c_str(), path) == 0;
+    if (!ok) {
+        std::remove(tmp.c_str());
+        return fail(h, LBMFVM_ERR_IO, "writing checkpoint %s failed (any earlier file there is unchanged)", path);
+    }
     return join_out(h);
 }
 

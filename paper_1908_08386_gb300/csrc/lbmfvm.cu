@@ -16,8 +16,11 @@
 #include <map>
 #include <mutex>
 #include <new>
+#include <string>
 #include <type_traits>
 #include <vector>
+
+#include <unistd.h>
 
 #include "kernels.cuh"
 #include "lbmfvm.h"

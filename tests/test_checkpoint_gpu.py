@@ -99,3 +99,23 @@ def test_saving_to_an_unwritable_path_is_an_io_error(tmp_path):
     with pytest.raises(L.LbmfvmError) as e:
         a.save(tmp_path / "no_such_dir" / "x.ckpt")
     assert e.value.code == L.LBMFVM_ERR_IO
+
+
+def test_failed_save_leaves_the_earlier_checkpoint(tmp_path):
+    """A save that cannot complete (here: its temporary file cannot be
+    created) returns LBMFVM_ERR_IO and leaves the checkpoint already at the
+    path loadable and unchanged."""
+    path = tmp_path / "keep.ckpt"
+    a = cavity("f32")
+    a.step(120)
+    a.save(path)
+    before = path.read_bytes()
+    (tmp_path / "keep.ckpt.tmp").mkdir()  # fopen of the temporary file fails
+    a.step(80)
+    with pytest.raises(L.LbmfvmError) as e:
+        a.save(path)
+    assert e.value.code == L.LBMFVM_ERR_IO
+    assert path.read_bytes() == before
+    b = cavity("f32")
+    b.load(path)
+    assert L.lbmfvm_step_count(b.h) == 120
