@@ -15,6 +15,10 @@
  *     equation Eq. 76), with face velocities interpolated from the new u;
  *   - relaxes toward the equilibrium of Eq. 8 with the Boussinesq buoyancy
  *     force of Eqs. 18 and 81 evaluated with the new T, and stores the result.
+ * Two options of the energy update (lbmfvm_opts_t.fv_scheme, fv_substeps):
+ * QUICK face temperatures stay in the fused launch; m > 1 explicit sub-steps
+ * per lattice step take m + 2 launches per step (the new velocity into two
+ * planes, m sub-steps with it held, then the collision with the final T).
  *
  * Conventions shared by every entry point:
  *   - Every function returns an int status: LBMFVM_OK (0) or a negative
@@ -81,6 +85,12 @@ extern "C" {
 #define LBMFVM_KERNEL_TMA 2
 #define LBMFVM_TMA_AUTOTUNE (-1)
 
+/* Face temperatures of the explicit energy update (lbmfvm_opts_t.fv_scheme)
+ * and automatic sub-steps (lbmfvm_opts_t.fv_substeps). */
+#define LBMFVM_FV_CENTRAL 0
+#define LBMFVM_FV_QUICK 1
+#define LBMFVM_FV_SUBSTEPS_AUTO 0
+
 /* Storage precision of the distributions.  F32/F16/BF16 store f - w_i and
  * compute in FP32 with FP32 temperature; F64 stores and computes in FP64.
  * F32X2 ("double-single") stores f - w_i and T as pairs of FP32 numbers
@@ -110,14 +120,17 @@ typedef struct {
     int32_t tile_y;         /* rows per thread block of the generic step kernel:
                                0 = default, else one of 4, 8, 16 */
     int32_t kernel;         /* LBMFVM_KERNEL_*; default AUTO */
-    int32_t tma_config;     /* tile shape of the TMA kernel, 0..3, or
+    int32_t tma_config;     /* tile shape of the TMA kernel, 0..4, or
                                LBMFVM_TMA_AUTOTUNE.  32- and 16-bit storage
                                (width x height, threads, input stages at 32 / 16
                                bit): 64x16, 1024, 3/3; 64x16, 512, 3/3 (the
                                default, 1); 64x8, 512, 2/3 (two blocks per SM);
-                               128x8, 1024, 2/3.  64-bit storage: 64x8, 256, 2;
-                               32x8, 256, 3; 32x16, 512, 2; 32x8, 256, 2 (two
-                               blocks per SM).  LBMFVM_TMA_AUTOTUNE times every
+                               128x8, 1024, 2/3; 64x16, 512 + 128 ring threads
+                               (four warps that take the one-node ring's moments
+                               and issue the copies), 3/3.  64-bit storage:
+                               64x8, 256, 2; 32x8, 256, 3; 32x16, 512, 2; 32x8,
+                               256, 2 (two blocks per SM); 32x8, 256 + 64 ring
+                               threads, 3.  LBMFVM_TMA_AUTOTUNE times every
                                shape on the handle's own grid at create and keeps
                                the fastest (remembered per storage precision and
                                power-of-two size class for the process); shapes
@@ -130,6 +143,24 @@ typedef struct {
                                256-byte aligned, owned by the caller and kept alive
                                until lbmfvm_destroy; NULL = the library allocates */
     size_t workspace_bytes; /* size of workspace */
+    int32_t fv_scheme;      /* face temperatures of the energy update:
+                               LBMFVM_FV_CENTRAL (default; the mean of the two
+                               nodes) or LBMFVM_FV_QUICK (quadratic upstream
+                               interpolation, the scheme Section 3.1 names for
+                               its finite-volume solver; the face keeps the
+                               central value where the far upstream node takes
+                               no part in the energy balance) */
+    int32_t fv_substeps;    /* explicit energy-update sub-steps m per lattice
+                               step, each of dt = 1/m with the velocity u^{n+1}
+                               held (Section 5.1's energy update taken in m
+                               explicit steps): 1 (default), m >= 2, or
+                               LBMFVM_FV_SUBSTEPS_AUTO = 0, the fewest with
+                               alpha/m <= 0.2 and U0^2/m <= 1.8 alpha (U0 from
+                               Ma; lbmfvm_create_lattice uses alpha only).  The
+                               stability limits become alpha/m <= 1/4 and
+                               U0^2/m <= 2 alpha.  QUICK and m != 1 need the TMA
+                               kernel (walls on every side); they fix its tile
+                               shape to 1 (no autotuning). */
 } lbmfvm_opts_t;
 
 /* Fill *opts with the defaults listed above. */
@@ -233,6 +264,11 @@ int lbmfvm_launch_count(const lbmfvm_t *h, int64_t *launches);
  * tile shape (-1 for the generic kernel); either pointer may be NULL. */
 int lbmfvm_kernel_info(const lbmfvm_t *h, int32_t *kernel, int32_t *tma_config);
 
+/* Energy update of the handle: LBMFVM_FV_CENTRAL or LBMFVM_FV_QUICK, and the
+ * sub-steps per lattice step (lbmfvm_opts_t.fv_substeps resolved); either
+ * pointer may be NULL. */
+int lbmfvm_fv_info(const lbmfvm_t *h, int32_t *scheme, int32_t *substeps);
+
 /* Derived lattice parameters: nu, alpha, gbeta, tau (any may be NULL). */
 int lbmfvm_params(const lbmfvm_t *h, double *nu, double *alpha, double *gbeta, double *tau);
 
@@ -311,6 +347,9 @@ int lbmfvm_batch_nusselt(lbmfvm_batch_t *b, int32_t i, double *mean_hot, double 
 /* Steps since set_state, whether cavity i is still stepped, and its lattice
  * parameters nu, alpha, gbeta, tau (params: 4 doubles or NULL). */
 int lbmfvm_batch_info(const lbmfvm_batch_t *b, int32_t i, int64_t *steps, int32_t *active, double *params);
+/* Energy-update sub-steps per lattice step of cavity i (lbmfvm_opts_t.fv_substeps
+ * resolved for that cavity). */
+int lbmfvm_batch_substeps(const lbmfvm_batch_t *b, int32_t i, int32_t *substeps);
 /* Ladder switch for cavities stepped in precision prec (a level below the
  * top of this batch's ladder, LBMFVM_ERR_ARG otherwise): the residual below
  * which lbmfvm_batch_run moves them one level up, and the number of checks
@@ -350,7 +389,9 @@ typedef struct {
     uint64_t payload_bytes;
     uint32_t code_crc;          /* CRC-32 of the handle's node codes (geometry, mask) */
     uint32_t payload_crc;       /* CRC-32 of the payload */
-    uint8_t pad[92];            /* zero */
+    int32_t fv_scheme;          /* LBMFVM_FV_* of the energy update */
+    int32_t fv_substeps;        /* its sub-steps per lattice step (0 is read as 1) */
+    uint8_t pad[84];            /* zero */
     uint32_t header_crc;        /* CRC-32 of the 252 bytes before it */
 } lbmfvm_checkpoint_header_t;
 

@@ -39,16 +39,20 @@ LBMFVM_TMA_AUTOTUNE = -1
 LBMFVM_F64, LBMFVM_F32, LBMFVM_F16, LBMFVM_BF16, LBMFVM_F32X2 = 0, 1, 2, 3, 4
 PRECISIONS = {"f64": LBMFVM_F64, "f32": LBMFVM_F32, "f16": LBMFVM_F16, "bf16": LBMFVM_BF16,
               "f32x2": LBMFVM_F32X2}
+# Energy-update face temperatures and automatic sub-steps
+LBMFVM_FV_CENTRAL, LBMFVM_FV_QUICK = 0, 1
+FV_SCHEMES = {"central": LBMFVM_FV_CENTRAL, "quick": LBMFVM_FV_QUICK}
+LBMFVM_FV_SUBSTEPS_AUTO = 0
 
 # Every entry point the header declares (checked by the test-suite).
 EXPORTS = (
     "lbmfvm_opts_default", "lbmfvm_workspace_bytes", "lbmfvm_create", "lbmfvm_create_lattice",
     "lbmfvm_set_state", "lbmfvm_step", "lbmfvm_inject_stall", "lbmfvm_step_count", "lbmfvm_fields", "lbmfvm_fields_f32",
-    "lbmfvm_nusselt", "lbmfvm_residual", "lbmfvm_run_to_steady", "lbmfvm_copy_state", "lbmfvm_launch_count", "lbmfvm_kernel_info", "lbmfvm_params", "lbmfvm_residual_noalloc",
+    "lbmfvm_nusselt", "lbmfvm_residual", "lbmfvm_run_to_steady", "lbmfvm_copy_state", "lbmfvm_launch_count", "lbmfvm_kernel_info", "lbmfvm_fv_info", "lbmfvm_params", "lbmfvm_residual_noalloc",
     "lbmfvm_save", "lbmfvm_load", "lbmfvm_checkpoint_info",
     "lbmfvm_destroy", "lbmfvm_last_error", "lbmfvm_batch_create", "lbmfvm_batch_set_state", "lbmfvm_batch_step",
     "lbmfvm_batch_residuals", "lbmfvm_batch_run", "lbmfvm_batch_fields", "lbmfvm_batch_nusselt", "lbmfvm_batch_info",
-    "lbmfvm_batch_set_polish", "lbmfvm_batch_kernel_info", "lbmfvm_batch_precision", "lbmfvm_batch_destroy", "lbmfvm_batch_last_error",
+    "lbmfvm_batch_substeps", "lbmfvm_batch_set_polish", "lbmfvm_batch_kernel_info", "lbmfvm_batch_precision", "lbmfvm_batch_destroy", "lbmfvm_batch_last_error",
 )
 
 
@@ -61,7 +65,7 @@ class lbmfvm_opts_t(ctypes.Structure):
     _fields_ = [("store", ctypes.c_int32), ("tile_y", ctypes.c_int32), ("kernel", ctypes.c_int32),
                 ("tma_config", ctypes.c_int32), ("t_ref", ctypes.c_double),
                 ("cuda_stream", ctypes.c_void_p), ("workspace", ctypes.c_void_p),
-                ("workspace_bytes", ctypes.c_size_t)]
+                ("workspace_bytes", ctypes.c_size_t), ("fv_scheme", ctypes.c_int32), ("fv_substeps", ctypes.c_int32)]
 
 
 class lbmfvm_checkpoint_header_t(ctypes.Structure):
@@ -71,7 +75,8 @@ class lbmfvm_checkpoint_header_t(ctypes.Structure):
                 ("t_wall", ctypes.c_double * 4), ("u_lid", ctypes.c_double), ("tau", ctypes.c_double),
                 ("alpha", ctypes.c_double), ("gbeta", ctypes.c_double), ("t_ref", ctypes.c_double),
                 ("force", ctypes.c_double * 2), ("payload_bytes", ctypes.c_uint64), ("code_crc", ctypes.c_uint32),
-                ("payload_crc", ctypes.c_uint32), ("pad", ctypes.c_uint8 * 92), ("header_crc", ctypes.c_uint32)]
+                ("payload_crc", ctypes.c_uint32), ("fv_scheme", ctypes.c_int32), ("fv_substeps", ctypes.c_int32),
+                ("pad", ctypes.c_uint8 * 84), ("header_crc", ctypes.c_uint32)]
 
 
 class LbmfvmError(RuntimeError):
@@ -113,6 +118,7 @@ def lib() -> ctypes.CDLL:
                 "lbmfvm_run_to_steady": (ctypes.c_int, [vp, d, i64, i64, i64p, dp]),
                 "lbmfvm_copy_state": (ctypes.c_int, [vp, vp]),
                 "lbmfvm_kernel_info": (ctypes.c_int, [vp, ctypes.POINTER(i32), ctypes.POINTER(i32)]),
+                "lbmfvm_fv_info": (ctypes.c_int, [vp, ctypes.POINTER(i32), ctypes.POINTER(i32)]),
                 "lbmfvm_launch_count": (ctypes.c_int, [vp, i64p]),
                 "lbmfvm_params": (ctypes.c_int, [vp, dp, dp, dp, dp]),
                 "lbmfvm_residual_noalloc": (ctypes.c_int, [vp, vp, vp, vp, vp, i64, vp, dp]),
@@ -129,6 +135,7 @@ def lib() -> ctypes.CDLL:
                 "lbmfvm_batch_fields": (ctypes.c_int, [vp, i32, vp, vp, vp, vp]),
                 "lbmfvm_batch_nusselt": (ctypes.c_int, [vp, i32, dp, vp, dp]),
                 "lbmfvm_batch_info": (ctypes.c_int, [vp, i32, i64p, ctypes.POINTER(i32), vp]),
+                "lbmfvm_batch_substeps": (ctypes.c_int, [vp, i32, ctypes.POINTER(i32)]),
                 "lbmfvm_batch_set_polish": (ctypes.c_int, [vp, i32, d, i32]),
                 "lbmfvm_batch_precision": (ctypes.c_int, [vp, i32, ctypes.POINTER(i32)]),
                 "lbmfvm_batch_kernel_info": (ctypes.c_int, [vp, i32, ctypes.POINTER(i32)]),
@@ -255,6 +262,13 @@ def lbmfvm_kernel_info(h):
     return k.value, c.value
 
 
+def lbmfvm_fv_info(h):
+    """(scheme, sub-steps) of the handle's energy update."""
+    sc, m = ctypes.c_int32(), ctypes.c_int32()
+    _check(lib().lbmfvm_fv_info(h, ctypes.byref(sc), ctypes.byref(m)), h)
+    return sc.value, m.value
+
+
 def _tma_config(cfg):
     return LBMFVM_TMA_AUTOTUNE if cfg == "auto" else int(cfg)
 
@@ -293,7 +307,8 @@ def lbmfvm_checkpoint_info(path) -> dict:
     _check(lib().lbmfvm_checkpoint_info(os.fsencode(path), ctypes.byref(hd)))
     return dict(nx=hd.nx, ny=hd.ny, store=hd.store, steps=hd.steps, bc=tuple(hd.bc), t_wall=tuple(hd.t_wall),
                 u_lid=hd.u_lid, tau=hd.tau, alpha=hd.alpha, gbeta=hd.gbeta, t_ref=hd.t_ref, force=tuple(hd.force),
-                payload_bytes=hd.payload_bytes, code_crc=hd.code_crc, payload_crc=hd.payload_crc)
+                payload_bytes=hd.payload_bytes, code_crc=hd.code_crc, payload_crc=hd.payload_crc,
+                fv_scheme=hd.fv_scheme, fv_substeps=max(1, hd.fv_substeps))
 
 
 def lbmfvm_destroy(h):
@@ -318,7 +333,7 @@ class Cavity:
                  mask=None, store="f32", bc=(LBMFVM_BC_DIRICHLET, LBMFVM_BC_DIRICHLET, LBMFVM_BC_ADIABATIC,
                                              LBMFVM_BC_ADIABATIC),
                  t_wall=(1.0, 0.0, 0.0, 0.0), u_lid=0.0, t_init=0.5, t_ref=None, tile_y=0, kernel="auto",
-                 tma_config=1, device=None):
+                 tma_config=1, fv_scheme="central", fv_substeps=1, device=None):
         import torch
 
         self.nx, self.ny = int(nx), int(ny)
@@ -329,6 +344,8 @@ class Cavity:
         self.opts.kernel = KERNELS[kernel] if isinstance(kernel, str) else int(kernel)
         self.opts.tma_config = _tma_config(tma_config)
         self.opts.t_ref = math.nan if t_ref is None else float(t_ref)
+        self.opts.fv_scheme = FV_SCHEMES[fv_scheme] if isinstance(fv_scheme, str) else int(fv_scheme)
+        self.opts.fv_substeps = int(fv_substeps)
         dev = torch.device("cuda" if device is None else device)
         self.device = dev
         nbytes = lbmfvm_workspace_bytes(self.grid, self.opts)
@@ -392,6 +409,11 @@ class Cavity:
         """TMA tile shape in use (-1 on the generic kernel)."""
         return lbmfvm_kernel_info(self.h)[1]
 
+    @property
+    def substeps(self):
+        """Energy-update sub-steps per lattice step."""
+        return lbmfvm_fv_info(self.h)[1]
+
     def copy_state_from(self, other: "Cavity"):
         """Take ``other``'s state (populations, temperature, step count,
         residual snapshot), converted to this cavity's storage precision."""
@@ -422,7 +444,7 @@ class Batch:
     PyTorch's current stream.
     """
 
-    def __init__(self, cases, store="f32", tma_config="auto", device=None):
+    def __init__(self, cases, store="f32", tma_config="auto", fv_scheme="central", fv_substeps=1, device=None):
         import torch
 
         self.n = len(cases)
@@ -438,6 +460,8 @@ class Batch:
         self.opts = lbmfvm_opts_default()
         self.opts.store = PRECISIONS[store] if isinstance(store, str) else int(store)
         self.opts.tma_config = _tma_config(tma_config)
+        self.opts.fv_scheme = FV_SCHEMES[fv_scheme] if isinstance(fv_scheme, str) else int(fv_scheme)
+        self.opts.fv_substeps = int(fv_substeps)
         dev = torch.device("cuda" if device is None else device)
         self.opts.cuda_stream = torch.cuda.current_stream(dev).cuda_stream
         self.b = ctypes.c_void_p()
@@ -498,6 +522,12 @@ class Batch:
         _bcheck(lib().lbmfvm_batch_info(self.b, int(i), ctypes.byref(steps), ctypes.byref(active), _addr(params)),
                 self.b)
         return steps.value, bool(active.value), tuple(params)
+
+    def substeps(self, i):
+        """Energy-update sub-steps per lattice step of cavity i."""
+        m = ctypes.c_int32()
+        _bcheck(lib().lbmfvm_batch_substeps(self.b, int(i), ctypes.byref(m)), self.b)
+        return m.value
 
     def set_polish(self, prec, r_switch, stall_checks=0):
         """Ladder switch of the cavities stepped in ``prec``: the residual

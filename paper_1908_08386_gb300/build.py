@@ -1,7 +1,7 @@
 """Build the sm_103a CUDA library ``liblbmfvm.so`` in place with nvcc.
 
-Three translation units, one ``-gencode`` (compute_103a / sm_103a), static CUDA
-runtime, so the library loads on a machine without a GPU driver (the driver
+Four translation units compiled in parallel, one ``-gencode`` (compute_103a /
+sm_103a), static CUDA runtime, so the library loads on a machine without a GPU driver (the driver
 is only needed at the first CUDA call).
 """
 
@@ -16,8 +16,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "liblbmfvm.so")
-SOURCES = [os.path.join(CSRC, "lbmfvm.cu"), os.path.join(CSRC, "residual_noalloc.cu"),
-           os.path.join(CSRC, "surrogate.cu")]
+SOURCES = [os.path.join(CSRC, "lbmfvm.cu"), os.path.join(CSRC, "fv_modes.cu"),
+           os.path.join(CSRC, "residual_noalloc.cu"), os.path.join(CSRC, "surrogate.cu")]
 DEPS = SOURCES + [os.path.join(CSRC, "kernels.cuh"), os.path.join(CSRC, "batch.inl"), os.path.join(CSRC, "checkpoint.inl"),
                   os.path.join(INCLUDE, "lbmfvm.h"), os.path.join(INCLUDE, "surrogate.h")]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
@@ -30,12 +30,34 @@ def nvcc() -> str:
     raise RuntimeError("nvcc not found: the CUDA toolkit is required to build liblbmfvm.so")
 
 
+FLAGS = ["-O3", "-std=c++17", ARCH, "-lineinfo", "-Xcompiler", "-fPIC"]
+
+
 def command(out: str = LIB, verbose_ptxas: bool = False) -> list[str]:
-    cmd = [nvcc(), "-O3", "-std=c++17", ARCH, "-lineinfo", "-Xcompiler", "-fPIC", "-shared",
-           "-I" + INCLUDE, "-o", out] + SOURCES
+    """One nvcc command that compiles and links every source (sequentially)."""
+    cmd = [nvcc()] + FLAGS + ["-shared", "-I" + INCLUDE, "-o", out] + SOURCES
     if verbose_ptxas:
         cmd.insert(1, "-Xptxas=-v")
     return cmd
+
+
+def _compile_parallel(out: str, verbose_ptxas: bool) -> None:
+    """Each translation unit compiled by its own nvcc process, then linked."""
+    import tempfile
+
+    with tempfile.TemporaryDirectory(prefix="lbmfvm_build_") as tmp:
+        objs, procs = [], []
+        for src in SOURCES:
+            obj = os.path.join(tmp, os.path.basename(src) + ".o")
+            cmd = [nvcc()] + FLAGS + ["-I" + INCLUDE, "-c", src, "-o", obj]
+            if verbose_ptxas:
+                cmd.insert(1, "-Xptxas=-v")
+            procs.append(subprocess.Popen(cmd, cwd=ROOT))
+            objs.append(obj)
+        failed = [p.args for p in procs if p.wait() != 0]
+        if failed:
+            raise subprocess.CalledProcessError(1, failed[0])
+        subprocess.run([nvcc(), ARCH, "-shared", "-o", out] + objs, check=True, cwd=ROOT)
 
 
 def stale() -> bool:
@@ -49,7 +71,7 @@ def build(force: bool = False, verbose_ptxas: bool = False) -> str:
     """Compile liblbmfvm.so if missing or older than its sources; return its path."""
     if force or stale():
         tmp = LIB + ".tmp"
-        subprocess.run(command(tmp, verbose_ptxas), check=True, cwd=ROOT)
+        _compile_parallel(tmp, verbose_ptxas)
         os.replace(tmp, LIB)
     return LIB
 

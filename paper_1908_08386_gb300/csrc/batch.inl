@@ -33,6 +33,7 @@ struct lbmfvm_batch {
         lbmfvm_grid_t grid;
         int x0, y0;
         double nu, alpha, gbeta, tau, t_ref;
+        int substeps;     // energy-update sub-steps per lattice step
         int64_t steps;    // steps since this cavity's last set_state
         int parity;       // buffer of the state while frozen
         bool active;
@@ -372,8 +373,13 @@ int lbmfvm_batch_create(int32_t n, const lbmfvm_grid_t *grids, const uint8_t *co
         c.gbeta = U0 * U0 / (H * dT);
         c.tau = 3.0 * c.nu + 0.5;
         c.t_ref = (opts && !std::isnan(opts->t_ref)) ? opts->t_ref : g.t_wall[LBMFVM_SIDE_E];
-        const char *why = Ma[i] > 0.3 ? "Ma > 0.3" : c.tau < 0.51 ? "tau < 0.51" : c.alpha > 0.25 ? "alpha > 0.25"
-                          : U0 * U0 > 2 * c.alpha ? "U0^2 > 2 alpha" : nullptr;
+        const int req = opts ? opts->fv_substeps : 1;
+        if (req < 0 || req > 256) {
+            delete b;
+            return fail_thread(LBMFVM_ERR_ARG, "fv_substeps = %d is outside [0, 256]", req);
+        }
+        c.substeps = substeps_for(req, c.alpha, U0);
+        const char *why = Ma[i] > 0.3 ? "Ma > 0.3" : c.tau < 0.51 ? "tau < 0.51" : fv_unstable(c.alpha, U0, c.substeps);
         if (why) {
             delete b;
             return fail_thread(LBMFVM_ERR_UNSTABLE, "cavity %d: %s", i, why);
@@ -437,6 +443,7 @@ int lbmfvm_batch_create(int32_t n, const lbmfvm_grid_t *grids, const uint8_t *co
         cd.alpha = c.alpha;
         cd.gbeta = c.gbeta;
         cd.t_ref = c.t_ref;
+        cd.substeps = c.substeps;
         for (int s = 0; s < 4; s++) {
             const bool moving = c.grid.bc[s] == LBMFVM_BC_MOVING;
             cd.wall_u[s] = moving && s >= 2 ? c.grid.u_lid : 0.0;
@@ -662,6 +669,13 @@ int lbmfvm_batch_info(const lbmfvm_batch_t *b, int32_t i, int64_t *steps, int32_
         params[2] = c.gbeta;
         params[3] = c.tau;
     }
+    return LBMFVM_OK;
+}
+
+int lbmfvm_batch_substeps(const lbmfvm_batch_t *b, int32_t i, int32_t *substeps) {
+    if (!b || !substeps) return fail_thread(LBMFVM_ERR_ARG, "batch or substeps is NULL");
+    if (i < 0 || i >= (int)b->cav.size()) return fail_thread(LBMFVM_ERR_ARG, "cavity index %d out of range", i);
+    *substeps = b->cav[i].substeps;
     return LBMFVM_OK;
 }
 

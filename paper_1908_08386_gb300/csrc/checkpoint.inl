@@ -167,6 +167,8 @@ int lbmfvm_save(lbmfvm_t *h, const char *path) {
     hd.force[1] = h->force[1];
     hd.payload_bytes = payload.size();
     hd.code_crc = h->code_crc;
+    hd.fv_scheme = h->fv_quick ? LBMFVM_FV_QUICK : LBMFVM_FV_CENTRAL;
+    hd.fv_substeps = h->fv_sub;
     hd.payload_crc = crc32_update(0, payload.data(), payload.size());
     hd.header_crc = crc32_update(0, &hd, offsetof(lbmfvm_checkpoint_header_t, header_crc));
 
@@ -204,6 +206,9 @@ int lbmfvm_load(lbmfvm_t *h, const char *path) {
              hd.force[1] != h->force[1] || !(hd.t_ref == h->t_ref))
         diff = "lattice parameters";
     else if (hd.u_lid != h->grid.u_lid) diff = "lid velocity";
+    else if (hd.fv_scheme != (h->fv_quick ? LBMFVM_FV_QUICK : LBMFVM_FV_CENTRAL) ||
+             (hd.fv_substeps < 1 ? 1 : hd.fv_substeps) != h->fv_sub)
+        diff = "energy-update scheme or sub-steps";
     for (int s = 0; s < 4 && !diff; s++)
         if (hd.bc[s] != h->grid.bc[s] || hd.t_wall[s] != h->grid.t_wall[s]) diff = "boundary conditions";
     if (diff) return fail(h, LBMFVM_ERR_ARG, "checkpoint %s was saved with other %s", path, diff);
@@ -222,9 +227,7 @@ int lbmfvm_load(lbmfvm_t *h, const char *path) {
                             cudaMemcpyHostToDevice, h->s));
     src += n * ts;
     CU(h, cudaMemcpyAsync(h->base + h->L.snap, src, 2 * n * sizeof(double), cudaMemcpyHostToDevice, h->s));
-    // a step of parity p clears the tile counter of parity 1 - p for the next
-    // step; restarting at parity 0 clears both here
-    CU(h, cudaMemsetAsync(h->base + h->L.tiles + sizeof(int), 0, 2 * sizeof(int), h->s));
+    if (int r = clear_tile_counters(h)) return r;
     CU(h, cudaStreamSynchronize(h->s));
     h->parity = 0;
     h->steps = hd.steps;

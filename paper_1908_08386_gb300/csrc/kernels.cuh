@@ -179,6 +179,8 @@ struct CavityDesc {
     double omega, alpha, gbeta, t_ref, fx, fy;
     double wall_u[4], wall_v[4];    // box-wall velocity per side W, E, S, N
     float wall_uf[4], wall_vf[4];   // the same in FP32
+    int substeps;                   // finite-volume sub-steps per lattice step (>= 1)
+    int pad;
 };
 
 // One tile of the TMA path: what a block needs to know about it.  A tile
@@ -189,10 +191,11 @@ struct CavityDesc {
 // host, so that no kernel converts (FP64 conversions are slow on this GPU):
 // FP64, FP32, and the low parts that make (FP32, low) the double-single value.
 struct TileHeader {
-    int x0, y0, ox, oy, nx, ny, cav, pad;  // origin; origin relative to the cavity; cavity size
+    int x0, y0, ox, oy, nx, ny, cav;  // origin; origin relative to the cavity; cavity size; cavity
+    int substeps;                     // finite-volume sub-steps per lattice step of the cavity (>= 1)
     double omega, alpha, gbeta, t_ref, fx, fy;
-    float omega_f, alpha_f, gbeta_f, t_ref_f, fx_f, fy_f, pad1, pad2;
-    float omega_lo, alpha_lo, gbeta_lo, t_ref_lo, fx_lo, fy_lo, pad3, pad4;
+    float omega_f, alpha_f, gbeta_f, t_ref_f, fx_f, fy_f, dt_f, pad2;       // dt = 1 / substeps
+    float omega_lo, alpha_lo, gbeta_lo, t_ref_lo, fx_lo, fy_lo, dt_lo, pad4;
 };
 static_assert(sizeof(TileHeader) == 144, "tile headers are 144-byte bulk copies");
 
@@ -309,6 +312,40 @@ __device__ __forceinline__ C fv_update(C TP, C uP, C vP, C ex, C ey, C alpha, bo
     // 1/(ex ey) is a power of two (ex, ey in {1/2, 1}): the product is exact.
     const C inv_v = (ex < C(1) ? C(2) : C(1)) * (ey < C(1) ? C(2) : C(1));
     return TP + (ey * (fe + fw) + ex * (fn + fs)) * inv_v;
+}
+
+// QUICK face value (Leonard's quadratic upstream interpolation, the scheme
+// Section 3.1 names for its finite-volume solver).  un: the face's normal
+// velocity, outward from P; Tn: the neighbour across the face.  With U the
+// upstream node, D the downstream one and UU the node beyond U,
+// T_f = 6/8 T_U + 3/8 T_D - 1/8 T_UU; where UU takes no part in the energy
+// balance (farP / farN false) the face keeps the central value.  farP, TfarP:
+// the node beyond P (upstream P); farN, TfarN: the node beyond the neighbour.
+template <class C>
+__device__ __forceinline__ C quick_face(C un, C TP, C Tn, bool farP, C TfarP, bool farN, C TfarN) {
+    if (!(un < C(0))) {
+        if (farP) return C(0.75) * TP + C(0.375) * Tn - C(0.125) * TfarP;
+    } else if (farN) {
+        return C(0.75) * Tn + C(0.375) * TP - C(0.125) * TfarN;
+    }
+    return C(0.5) * (TP + Tn);
+}
+
+// Explicit finite-volume update with given face temperatures (QUICK) and a
+// time step dt (1/m for m sub-steps): V_P (T' - T_P) = dt sum over open faces
+// of [-F_f T_f + alpha A_f (T_nb - T_P)], F_f = A_f u_face.n, u_face the mean
+// of the two node velocities.
+template <class C>
+__device__ __forceinline__ C fv_update_faces(C TP, C uP, C vP, C ex, C ey, C alpha, C dt, bool oE, C TE, C uE, C TfE,
+                                             bool oN, C TN, C vN, C TfN, bool oW, C TW, C uW, C TfW, bool oS, C TS,
+                                             C vS, C TfS) {
+    const C h = C(0.5);
+    const C fe = oE ? alpha * (TE - TP) - h * (uP + uE) * TfE : C(0);
+    const C fw = oW ? alpha * (TW - TP) + h * (uP + uW) * TfW : C(0);
+    const C fn = oN ? alpha * (TN - TP) - h * (vP + vN) * TfN : C(0);
+    const C fs = oS ? alpha * (TS - TP) + h * (vP + vS) * TfS : C(0);
+    const C inv_v = (ex < C(1) ? C(2) : C(1)) * (ey < C(1) ? C(2) : C(1));
+    return TP + dt * ((ey * (fe + fw) + ex * (fn + fs)) * inv_v);
 }
 
 __host__ __device__ __forceinline__ bool fv_open(uint8_t code) { return (code >> 6) <= TH_DIRICHLET; }
@@ -571,17 +608,28 @@ __device__ __forceinline__ void load_2d(void *dst, const CUtensorMap *map, uint6
 // (x0, y0), NPT of them per thread; the staged input box reaches 3 nodes
 // beyond it in y and XOFF (>= 4, one 16-byte TMA granule) in x, enough for the
 // pull stencil of the one-node ring and of any wall partner on that ring.
+// The temperature box reaches THALO rows beyond the tile (1 for central face
+// values, 2 for QUICK's far upstream node) and 4 columns.
 // Once a tile's moments are taken, its staged populations are dead and the
 // same bytes receive the tile's results, which one TMA bulk store writes back.
-template <class S, int TW_, int TH_, int STAGES_, int THREADS_, int MINB_ = 1>
+//
+// RING_THREADS > 0 adds that many threads (whole warps) to the block for the
+// one-node ring's moments, and the first of them issues the TMA copies, so
+// the THREADS compute threads all carry the same load into each tile's block
+// barrier; with 0 the first compute threads also take the ring and thread 0
+// issues.
+template <class S, int TW_, int TH_, int STAGES_, int THREADS_, int MINB_ = 1, int THALO_ = 1, int RT_ = 0>
 struct TmaTile {
     using TC = typename Compute<S>::type;  // temperature and ring element
     static constexpr int TW = TW_, TH = TH_, STAGES = STAGES_, THREADS = THREADS_;
+    static constexpr int RING_THREADS = RT_;
+    static constexpr int BLOCK = THREADS_ + RT_;       // threads per block
     static constexpr int MINB = MINB_;             // blocks per SM the register budget must allow
+    static constexpr int THALO = THALO_;
     static constexpr int NPT = TW * TH / THREADS;  // own nodes per thread
     static constexpr int XOFF = 16 / (int)sizeof(S) < 4 ? 4 : 16 / (int)sizeof(S);
     static constexpr int FW = TW + 2 * XOFF, FH = TH + 6;  // population box
-    static constexpr int TWD = TW + 8, THT = TH + 2;       // temperature box (x0-4, y0-1)
+    static constexpr int TWD = TW + 8, THT = TH + 2 * THALO;  // temperature box (x0-4, y0-THALO)
     static constexpr int CWD = TW + 32, CHT = TH + 2;      // code box (x0-16, y0-1), codes then face flags
     static constexpr int RW = TW + 2, RH = TH + 2;         // tile + ring
     static constexpr int NRING = 2 * RW + 2 * TH;          // ring nodes
@@ -609,9 +657,48 @@ struct TmaTile {
                   "TMA boxes need 16-byte inner extents");
     static_assert(TW % 16 == 0, "tile origins must stay 16-byte aligned for every box");
     static_assert(TW >= 32 && TH >= 8, "tile lists are sized for tiles of at least 32 x 8 nodes");
-    static_assert(NPT >= 1 && NPT * THREADS == TW * TH && NRING <= THREADS, "thread mapping");
+    static_assert(NPT >= 1 && NPT * THREADS == TW * TH && (RT_ > 0 || NRING <= THREADS), "thread mapping");
+    static_assert(RT_ % 32 == 0 && THREADS % 32 == 0, "whole warps");
     static_assert(STAGES >= 2, "the pipeline needs two stages");
+    static_assert(THALO == 1 || THALO == 2, "temperature halo of one or two rows");
+    // the same tile with a temperature box of h halo rows
+    template <int h>
+    using WithTHalo = TmaTile<S, TW_, TH_, STAGES_, THREADS_, MINB_, h, RT_>;
 };
+
+// Energy update of a launch of the TMA kernel: the central face values of
+// the fused step, QUICK face values in the fused step, or none (the
+// temperature of the new step comes from a plane that the finite-volume
+// sub-step kernels wrote, and the kernel only collides with it).
+enum : int { FV_CENTRAL = 0, FV_QUICK = 1, FV_GIVEN = 2 };
+
+// Tile shapes of the TMA kernel (tile width x height, pipeline stages,
+// threads), selected by lbmfvm_opts_t.tma_config.  Stages are as many as the
+// 227 KB of shared memory allow for 32-bit storage; 16-bit storage halves the
+// population box and takes one more stage where it fits.
+template <class S, int CFG> struct TmaConfig;
+template <class S> struct TmaConfig<S, 0> { using G = TmaTile<S, 64, 16, 3, 1024>; };
+template <class S> struct TmaConfig<S, 1> { using G = TmaTile<S, 64, 16, 3, 512>; };
+template <class S> struct TmaConfig<S, 2> { using G = TmaTile<S, 64, 8, sizeof(S) == 4 ? 2 : 3, 512, 2>; };
+template <class S> struct TmaConfig<S, 3> { using G = TmaTile<S, 128, 8, sizeof(S) == 4 ? 2 : 3, 1024>; };
+// 64 x 16 with four ring warps (which also issue the copies)
+template <class S> struct TmaConfig<S, 4> { using G = TmaTile<S, 64, 16, 3, 512, 1, 1, 128>; };
+// 64-bit storage: a 32 x 8 tile stages 43 KB, a 64 x 8 tile 78 KB.
+template <> struct TmaConfig<double, 0> { using G = TmaTile<double, 64, 8, 2, 256>; };
+template <> struct TmaConfig<double, 1> { using G = TmaTile<double, 32, 8, 3, 256>; };
+template <> struct TmaConfig<double, 2> { using G = TmaTile<double, 32, 16, 2, 512>; };
+template <> struct TmaConfig<double, 3> { using G = TmaTile<double, 32, 8, 2, 256, 2>; };
+template <> struct TmaConfig<double, 4> { using G = TmaTile<double, 32, 8, 3, 256, 1, 1, 64>; };
+// double-single storage: 8-byte elements like FP64, the same shapes
+template <> struct TmaConfig<dsf, 0> { using G = TmaTile<dsf, 64, 8, 2, 256>; };
+template <> struct TmaConfig<dsf, 1> { using G = TmaTile<dsf, 32, 8, 3, 256>; };
+template <> struct TmaConfig<dsf, 2> { using G = TmaTile<dsf, 32, 16, 2, 512>; };
+template <> struct TmaConfig<dsf, 3> { using G = TmaTile<dsf, 32, 8, 2, 256, 2>; };
+template <> struct TmaConfig<dsf, 4> { using G = TmaTile<dsf, 32, 8, 3, 256, 1, 1, 64>; };
+constexpr int kTmaConfigs = 5;
+// QUICK face values and the sub-step path use shape 1 (FV_QUICK with a
+// temperature box of two halo rows).
+constexpr int kTmaConfigFv = 1;
 
 constexpr uint64_t kWaitLimitNs = 1000000000ull;  // 1 s per wait
 constexpr int kErrTimeout = 1;
@@ -660,8 +747,8 @@ __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wa
 // A wait that runs out raises a shared abort flag that every thread checks
 // after the barrier, so the block leaves together and a device status word
 // tells the host.
-template <class S, class G>
-__global__ void __launch_bounds__(G::THREADS, G::MINB)
+template <class S, class G, int MODE = FV_CENTRAL>
+__global__ void __launch_bounds__(G::BLOCK, G::MINB)
     step_tma_kernel(const StepArgs<S> a, const CavityDesc *__restrict__ cavs, const TileHeader *__restrict__ tiles,
                     const int *__restrict__ ntiles_p, const __grid_constant__ CUtensorMap map_f,
                     const __grid_constant__ CUtensorMap map_T, const __grid_constant__ CUtensorMap map_c,
@@ -679,6 +766,11 @@ __global__ void __launch_bounds__(G::THREADS, G::MINB)
 
     const int tid = threadIdx.x;
     const int ntiles = *ntiles_p;
+    // compute threads hold NPT own nodes; with ring threads, the first of
+    // them issues the copies (PROD), else thread 0 does
+    constexpr int RT = G::RING_THREADS;
+    const bool computes = RT == 0 || tid < G::THREADS;
+    const int PROD = RT ? G::THREADS : 0;
     auto fixed_tile = [&](int k) {
         const int t = (int)blockIdx.x + k * (int)gridDim.x;
         return t < ntiles ? t : -1;
@@ -700,7 +792,7 @@ __global__ void __launch_bounds__(G::THREADS, G::MINB)
         tma::mbar_arrive_expect_tx(&bars[s], G::TX_BYTES + (uint32_t)sizeof(TileHeader));
         tma::load_bytes(&hdrs[s], tiles + t, sizeof(TileHeader), &bars[s]);
         tma::load_3d(stg + G::F_OFF, &map_f, &bars[s], x0 - XOFF, y0 - 3, 0);
-        tma::load_2d(stg + G::T_OFF, &map_T, &bars[s], x0 - 4, y0 - 1);
+        tma::load_2d(stg + G::T_OFF, &map_T, &bars[s], x0 - 4, y0 - G::THALO);
         tma::load_3d(stg + G::C_OFF, &map_c, &bars[s], x0 - 16, y0 - 1, 0);
     };
     auto store_tile = [&](int k) {
@@ -727,11 +819,11 @@ __global__ void __launch_bounds__(G::THREADS, G::MINB)
     // Without a programmatic predecessor the wait returns at once.
     if (tid == 0) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     asm volatile("griddepcontrol.wait;" ::: "memory");
-    // thread 0: the next tile to load (index, origin), the ticket in flight,
-    // loads issued
+    // the issuing thread: the next tile to load (index, origin), the ticket
+    // in flight, loads issued
     int pre_t = -1, ticket = -1, issued = 0;
     int2 pre_o = make_int2(0, 0);
-    if (tid == 0) {
+    if (tid == PROD) {
         if (blockIdx.x == 0) *ctr_next = 0;
         int k = 0;
         for (; k < G::STAGES && fixed_tile(k) >= 0; k++) {
@@ -781,7 +873,7 @@ __global__ void __launch_bounds__(G::THREADS, G::MINB)
         C *RU = reinterpret_cast<C *>(smem + G::RING_OFF + (k & 1) * G::RING_BYTES), *RV = RU + G::RH * RW;
         // staged-box index of node (lx, ly) relative to the tile origin
         auto fidx = [&](int lx, int ly) { return (ly + 3) * FW + (lx + XOFF); };
-        auto tidx = [&](int lx, int ly) { return (ly + 1) * G::TWD + (lx + 4); };
+        auto tidx = [&](int lx, int ly) { return (ly + G::THALO) * G::TWD + (lx + 4); };
         auto cidx = [&](int lx, int ly) { return (ly + 1) * G::CWD + (lx + 16); };
         auto pull = [&](int lx, int ly, C g[9]) {
             const S *p = F + fidx(lx, ly);
@@ -823,30 +915,38 @@ __global__ void __launch_bounds__(G::THREADS, G::MINB)
         // buffer), the ring's u, v.
         C g[NPT][9], dr[NPT], uu[NPT], vv[NPT];
         uint8_t cc[NPT];
+        if (computes) {
 #pragma unroll
-        for (int j = 0; j < NPT; j++) {
-            const int i = tid + j * G::THREADS;
-            const int ly = i / TW, lx = i - ly * TW;
-            cc[j] = decode(CC[cidx(lx, ly)]);
-            state(lx, ly, cc[j], g[j], dr[j], uu[j], vv[j]);
-            const int r = (ly + 1) * RW + (lx + 1);
-            RU[r] = uu[j];
-            RV[r] = vv[j];
+            for (int j = 0; j < NPT; j++) {
+                const int i = tid + j * G::THREADS;
+                const int ly = i / TW, lx = i - ly * TW;
+                cc[j] = decode(CC[cidx(lx, ly)]);
+                state(lx, ly, cc[j], g[j], dr[j], uu[j], vv[j]);
+                if constexpr (MODE != FV_GIVEN) {
+                    const int r = (ly + 1) * RW + (lx + 1);
+                    RU[r] = uu[j];
+                    RV[r] = vv[j];
+                }
+            }
         }
-        if (tid < G::NRING) {
-            int rx, ry;
-            if (tid < RW) { rx = tid; ry = 0; }
-            else if (tid < 2 * RW) { rx = tid - RW; ry = TH + 1; }
-            else { const int h = tid - 2 * RW; rx = (h & 1) ? RW - 1 : 0; ry = 1 + (h >> 1); }
-            const uint8_t c = decode(CC[cidx(rx - 1, ry - 1)]);
-            C hg[9], hd, hu, hv;
-            state(rx - 1, ry - 1, c, hg, hd, hu, hv);
-            RU[ry * RW + rx] = hu;
-            RV[ry * RW + rx] = hv;
+        // the ring's velocities feed the energy update's faces only
+        if (MODE != FV_GIVEN) {
+            const int first = RT ? tid - G::THREADS : tid, stride = RT ? RT : G::NRING;
+            for (int hr = first; hr >= 0 && hr < G::NRING; hr += stride) {
+                int rx, ry;
+                if (hr < RW) { rx = hr; ry = 0; }
+                else if (hr < 2 * RW) { rx = hr - RW; ry = TH + 1; }
+                else { const int h = hr - 2 * RW; rx = (h & 1) ? RW - 1 : 0; ry = 1 + (h >> 1); }
+                const uint8_t c = decode(CC[cidx(rx - 1, ry - 1)]);
+                C hg[9], hd, hu, hv;
+                state(rx - 1, ry - 1, c, hg, hd, hu, hv);
+                RU[ry * RW + rx] = hu;
+                RV[ry * RW + rx] = hv;
+            }
         }
         __syncthreads();
         if (*abort_flag) {
-            if (tid == 0) {
+            if (tid == PROD) {
                 // let the copies already in flight land before the block exits
                 for (int j = k + 1; j < issued; j++)
                     tma::mbar_wait_bounded(&bars[j % G::STAGES], (uint32_t)(j / G::STAGES) & 1u, kWaitLimitNs / 2);
@@ -854,7 +954,7 @@ __global__ void __launch_bounds__(G::THREADS, G::MINB)
             }
             return;
         }
-        if (tid == 0 && k > 0) store_tile(k - 1);
+        if (tid == PROD && k > 0) store_tile(k - 1);
 
         // Phase B: energy balance and collision of the own nodes; results go
         // to the stage's (now dead) population bytes.  Inert nodes keep T.
@@ -862,6 +962,7 @@ __global__ void __launch_bounds__(G::THREADS, G::MINB)
         C *OT = reinterpret_cast<C *>(stg + G::F_OFF + G::OT_OFF);
 #pragma unroll
         for (int j = 0; j < NPT; j++) {
+            if (!computes) break;
             const int i = tid + j * G::THREADS;
             const int ly = i / TW, lx = i - ly * TW;
             const uint8_t c = cc[j];
@@ -877,14 +978,36 @@ __global__ void __launch_bounds__(G::THREADS, G::MINB)
             const int r = (ly + 1) * RW + (lx + 1);
             const int th = c >> 6;
             C Tn = TP;
-            if (th == TH_FV) {
+            if (MODE == FV_GIVEN) {
+                // T^{n+1} of every node comes from the sub-step kernels
+            } else if (th == TH_FV) {
                 // control volume clipped to the cavity; faces beyond it are closed
                 const uint8_t ff = CF[cidx(lx, ly)];
                 const C ex = ((ff & FF_IN_W) ? C(0.5) : C(0)) + ((ff & FF_IN_E) ? C(0.5) : C(0));
                 const C ey = ((ff & FF_IN_S) ? C(0.5) : C(0)) + ((ff & FF_IN_N) ? C(0.5) : C(0));
-                Tn = fv_update<C>(TP, uu[j], vv[j], ex, ey, alpha, ff & FF_OPEN_E, TT[t + 1], RU[r + 1], ff & FF_OPEN_N,
-                                  TT[t + G::TWD], RV[r + RW], ff & FF_OPEN_W, TT[t - 1], RU[r - 1], ff & FF_OPEN_S,
-                                  TT[t - G::TWD], RV[r - RW]);
+                if constexpr (MODE == FV_QUICK) {
+                    // far upstream nodes: beyond P (P's own flags) or beyond
+                    // the neighbour (the neighbour's flag on the same side)
+                    const int W2 = G::TWD;
+                    const C uP = uu[j], vP = vv[j], TP_ = TP;
+                    const C TE = TT[t + 1], TW = TT[t - 1], TN = TT[t + W2], TS = TT[t - W2];
+                    const C uE = RU[r + 1], uW = RU[r - 1], vN = RV[r + RW], vS = RV[r - RW];
+                    const C TfE = quick_face<C>(uP + uE, TP_, TE, ff & FF_OPEN_W, TW,
+                                                CF[cidx(lx + 1, ly)] & FF_OPEN_E, TT[t + 2]);
+                    const C TfW = quick_face<C>(-(uP + uW), TP_, TW, ff & FF_OPEN_E, TE,
+                                                CF[cidx(lx - 1, ly)] & FF_OPEN_W, TT[t - 2]);
+                    const C TfN = quick_face<C>(vP + vN, TP_, TN, ff & FF_OPEN_S, TS,
+                                                CF[cidx(lx, ly + 1)] & FF_OPEN_N, TT[t + 2 * W2]);
+                    const C TfS = quick_face<C>(-(vP + vS), TP_, TS, ff & FF_OPEN_N, TN,
+                                                CF[cidx(lx, ly - 1)] & FF_OPEN_S, TT[t - 2 * W2]);
+                    Tn = fv_update_faces<C>(TP_, uP, vP, ex, ey, alpha, C(1), ff & FF_OPEN_E, TE, uE, TfE,
+                                            ff & FF_OPEN_N, TN, vN, TfN, ff & FF_OPEN_W, TW, uW, TfW, ff & FF_OPEN_S,
+                                            TS, vS, TfS);
+                } else {
+                    Tn = fv_update<C>(TP, uu[j], vv[j], ex, ey, alpha, ff & FF_OPEN_E, TT[t + 1], RU[r + 1],
+                                      ff & FF_OPEN_N, TT[t + G::TWD], RV[r + RW], ff & FF_OPEN_W, TT[t - 1], RU[r - 1],
+                                      ff & FF_OPEN_S, TT[t - G::TWD], RV[r - RW]);
+                }
             } else if (th == TH_OBSTACLE) {
                 const int d = partner_dir(c);
                 Tn = TT[tidx(lx + cx_rt(d), ly + cy_rt(d))];
@@ -893,7 +1016,7 @@ __global__ void __launch_bounds__(G::THREADS, G::MINB)
             const C Gy = fy + gbeta * (Tn - t_ref);
             collide<C>(g[j], dr[j], uu[j], vv[j], omega, fx, Gy, [&](int q, C v) { st(of + q * OPLANE, v); });
         }
-        if (tid == 0 && k > 0 && pre_t >= 0) {
+        if (tid == PROD && k > 0 && pre_t >= 0) {
             tma::bulk_wait_read();  // the results of tile k-1 have left its stage
             issue(k - 1 + G::STAGES, pre_t, pre_o);
             issued = k + G::STAGES;
@@ -915,9 +1038,170 @@ __global__ void __launch_bounds__(G::THREADS, G::MINB)
     }
     const int count = *known;
     __syncthreads();
-    if (tid == 0 && count > 0) {
+    if (tid == PROD && count > 0) {
         store_tile(count - 1);
         tma::bulk_wait_all();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Energy update in sub-steps (and QUICK face values beside them).  With m
+// explicit sub-steps of dt = 1/m per lattice step, each sub-step reads the
+// previous one's temperature of the neighbours, so the update leaves the
+// fused kernel: per lattice step
+//   uv_kernel            u^{n+1}, v^{n+1} of every node of the active tiles
+//                        (pull, wall extrapolation, moments) into two planes;
+//   fv_substep_kernel    M launches (M = the largest m of the list's
+//                        cavities): T_s = T_{s-1} + dt (flux balance) with the
+//                        velocity held at u^{n+1}; launch s takes the tiles of
+//                        the cavities with m >= s (the list is sorted by m,
+//                        largest first), and each cavity's chain of sub-steps
+//                        alternates between two scratch planes so that its
+//                        last one lands in the plane X;
+//   step_tma_kernel      FV_GIVEN: pull, extrapolation, moments, and the
+//                        collision with the final sub-step's T^{n+1}.
+// Both helper kernels take one tile of the TMA kernel's list per block and
+// read global memory directly (their planes are small next to the
+// populations and stay in L2).
+// ---------------------------------------------------------------------------
+
+// Tile parameters of the helper kernels in the arithmetic precision C.
+template <class C> struct TileParams;
+template <> struct TileParams<float> {
+    __device__ static float alpha(const TileHeader &h) { return h.alpha_f; }
+    __device__ static float dt(const TileHeader &h) { return h.dt_f; }
+};
+template <> struct TileParams<double> {
+    __device__ static double alpha(const TileHeader &h) { return h.alpha; }
+    __device__ static double dt(const TileHeader &h) { return 1.0 / (double)h.substeps; }
+};
+template <> struct TileParams<dsf> {
+    __device__ static dsf alpha(const TileHeader &h) { return dsf(h.alpha_f, h.alpha_lo); }
+    __device__ static dsf dt(const TileHeader &h) { return dsf(h.dt_f, h.dt_lo); }
+};
+
+// u^{n+1}, v^{n+1} of every node of the active tiles (tile shape tw x th):
+// the same pull, extrapolation and moments as phase A of the step kernel.
+// Nodes outside every cavity and inert nodes get 0.
+template <class S>
+__global__ void __launch_bounds__(256)
+    uv_kernel(const S *__restrict__ fin, long long plane, int pitch, int gnx, int gny,
+              const TileHeader *__restrict__ tiles, int ntiles, const CavityDesc *__restrict__ cavs,
+              const uint8_t *__restrict__ code, typename Compute<S>::type *U, typename Compute<S>::type *V, int tw,
+              int th) {
+    using C = typename Compute<S>::type;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int x0 = tiles[t].x0, y0 = tiles[t].y0, ox = tiles[t].ox, oy = tiles[t].oy, cnx = tiles[t].nx;
+        const CavityDesc *cvp = cavs + tiles[t].cav;
+        for (int i = threadIdx.x; i < tw * th; i += blockDim.x) {
+            const int ly = i / tw, lx = i - ly * tw;
+            const int x = x0 + lx, y = y0 + ly;
+            if (x >= gnx || y >= gny) continue;
+            const long long k = (long long)y * pitch + x;
+            const uint8_t c = decode(code[k]);
+            const int kind = c & 3;
+            C g[9], drho = C(-1), ux = C(0), uy = C(0);
+            if (kind != KIND_SOLID) {
+                int sx = x, sy = y;
+                if (kind == KIND_WALL) {
+                    const int d = partner_dir(c);
+                    sx += cx_rt(d);
+                    sy += cy_rt(d);
+                }
+                // a fluid node and a wall partner lie inside their cavity, so
+                // the pull stays on the grid; the clamp only guards the reads
+                // against a corrupt code
+                sx = min(max(sx, 1), gnx - 2);
+                sy = min(max(sy, 1), gny - 2);
+                const S *p = fin + (long long)sy * pitch + sx;
+#pragma unroll
+                for (int q = 0; q < 9; q++) g[q] = ld(p + q * plane - cy(q) * pitch - cx(q));
+                moments<C>(g, drho, ux, uy);
+                if (kind == KIND_WALL) {
+                    C uw = C(0), vw = C(0);
+                    if ((c >> 6) != TH_OBSTACLE) {
+                        const int px = ox + lx, py = oy + ly;
+                        const int side = px == 0 ? 0 : (px == cnx - 1 ? 1 : (py == 0 ? 2 : 3));
+                        if constexpr (std::is_same<C, float>::value) {
+                            uw = cvp->wall_uf[side];
+                            vw = cvp->wall_vf[side];
+                        } else {
+                            uw = C(cvp->wall_u[side]);
+                            vw = C(cvp->wall_v[side]);
+                        }
+                    }
+                    nee<C>(g, drho, ux, uy, uw, vw);
+                }
+            }
+            U[k] = ux;
+            V[k] = uy;
+        }
+    }
+}
+
+// Sub-step s (1-based) of the energy update on the first ntiles tiles of a
+// list (cavities with m >= s sub-steps): the new temperature from the
+// previous sub-step's with the velocity planes U, V held (finite-volume
+// nodes), the partner's temperature (obstacle surface nodes), unchanged
+// otherwise.  A cavity's sub-step s reads T0 (s = 1) or the plane its
+// sub-step s - 1 wrote, and writes X when m - s is even, else Y, so its last
+// sub-step writes X.
+template <class C, bool QUICK>
+__global__ void __launch_bounds__(256)
+    fv_substep_kernel(const C *__restrict__ T0, C *X, C *Y, const C *__restrict__ U, const C *__restrict__ V,
+                      const uint8_t *__restrict__ code, const uint8_t *__restrict__ fflags, int pitch, int gnx, int gny,
+                      const TileHeader *__restrict__ tiles, int ntiles, int tw, int th, int s) {
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const TileHeader &hd = tiles[t];
+        const int x0 = hd.x0, y0 = hd.y0;
+        const bool to_x = ((hd.substeps - s) & 1) == 0;
+        C *Tout = to_x ? X : Y;
+        const C *Tin = s == 1 ? T0 : (to_x ? Y : X);
+        if (s > hd.substeps) continue;  // not in this sub-step (the host passes none)
+        const C alpha = TileParams<C>::alpha(hd), dt = TileParams<C>::dt(hd);
+        for (int i = threadIdx.x; i < tw * th; i += blockDim.x) {
+            const int ly = i / tw, lx = i - ly * tw;
+            const int x = x0 + lx, y = y0 + ly;
+            if (x >= gnx || y >= gny) continue;
+            const long long k = (long long)y * pitch + x;
+            const C TP = Tin[k];
+            const uint8_t c = decode(code[k]);
+            const int role = c >> 6;
+            C Tn = TP;
+            if (role == TH_OBSTACLE && (c & 3) == KIND_WALL) {
+                const int d = partner_dir(c);
+                Tn = Tin[k + (long long)cy_rt(d) * pitch + cx_rt(d)];
+            } else if (role == TH_FV) {
+                // open faces name neighbours inside the cavity, and a far
+                // node's flag is read only from a node inside it
+                const uint8_t ff = fflags[k];
+                const bool oE = ff & FF_OPEN_E, oW = ff & FF_OPEN_W, oN = ff & FF_OPEN_N, oS = ff & FF_OPEN_S;
+                const C ex = ((ff & FF_IN_W) ? C(0.5) : C(0)) + ((ff & FF_IN_E) ? C(0.5) : C(0));
+                const C ey = ((ff & FF_IN_S) ? C(0.5) : C(0)) + ((ff & FF_IN_N) ? C(0.5) : C(0));
+                const C uP = U[k], vP = V[k];
+                const C TE = oE ? Tin[k + 1] : C(0), TW = oW ? Tin[k - 1] : C(0);
+                const C TN = oN ? Tin[k + pitch] : C(0), TS = oS ? Tin[k - pitch] : C(0);
+                const C uE = oE ? U[k + 1] : C(0), uW = oW ? U[k - 1] : C(0);
+                const C vN = oN ? V[k + pitch] : C(0), vS = oS ? V[k - pitch] : C(0);
+                C TfE, TfW, TfN, TfS;
+                if constexpr (QUICK) {
+                    const bool eE = oE && (fflags[k + 1] & FF_OPEN_E), wW = oW && (fflags[k - 1] & FF_OPEN_W);
+                    const bool nN = oN && (fflags[k + pitch] & FF_OPEN_N), sS = oS && (fflags[k - pitch] & FF_OPEN_S);
+                    TfE = quick_face<C>(uP + uE, TP, TE, oW, TW, eE, eE ? Tin[k + 2] : C(0));
+                    TfW = quick_face<C>(-(uP + uW), TP, TW, oE, TE, wW, wW ? Tin[k - 2] : C(0));
+                    TfN = quick_face<C>(vP + vN, TP, TN, oS, TS, nN, nN ? Tin[k + 2 * (long long)pitch] : C(0));
+                    TfS = quick_face<C>(-(vP + vS), TP, TS, oN, TN, sS, sS ? Tin[k - 2 * (long long)pitch] : C(0));
+                } else {
+                    TfE = C(0.5) * (TP + TE);
+                    TfW = C(0.5) * (TP + TW);
+                    TfN = C(0.5) * (TP + TN);
+                    TfS = C(0.5) * (TP + TS);
+                }
+                Tn = fv_update_faces<C>(TP, uP, vP, ex, ey, alpha, dt, oE, TE, uE, TfE, oN, TN, vN, TfN, oW, TW, uW,
+                                        TfW, oS, TS, vS, TfS);
+            }
+            Tout[k] = Tn;
+        }
     }
 }
 
@@ -1091,7 +1375,7 @@ __global__ void __launch_bounds__(256) residual_kernel(const StepArgs<S> a, int 
 }
 
 // Residual, pass 2: one warp sums the block partials in a fixed order.
-__global__ void residual_finish_kernel(const double *partials, int nblocks, double *out) {
+static __global__ void residual_finish_kernel(const double *partials, int nblocks, double *out) {
     double v[kResidualSums] = {};
     for (int b = threadIdx.x; b < nblocks; b += 32)
 #pragma unroll
@@ -1174,3 +1458,46 @@ __global__ void __launch_bounds__(256) nusselt_kernel(const StepArgs<S> a, doubl
 }
 
 }  // namespace lbmfvm_dev
+
+// ---------------------------------------------------------------------------
+// Host launchers of the energy-update options (QUICK face values, sub-steps),
+// compiled in their own translation unit (fv_modes.cu) for every storage
+// type; the handle code fills the arguments.
+// ---------------------------------------------------------------------------
+namespace lbmfvm_fv {
+
+// Arguments of one launch of step_tma_kernel over one tile list.
+template <class S>
+struct TmaLaunch {
+    lbmfvm_dev::StepArgs<S> a;
+    const lbmfvm_dev::CavityDesc *cavs;
+    const lbmfvm_dev::TileHeader *tiles;  // first header of the list
+    const int *count;                     // the list's count slot
+    const CUtensorMap *map_f, *map_T, *map_c, *map_fo, *map_To;
+    int *ctr, *ctr_next;                  // the list's tile counters of this step and the next
+    int nfix, blocks;
+    cudaStream_t stream;
+};
+
+// Shared-memory limits of the QUICK (two temperature halo rows) and the
+// given-temperature kernels of shape kTmaConfigFv; blocks per SM of each.
+template <class S>
+cudaError_t prepare_modes(int *blocks_quick, int *blocks_given);
+// Fused step with QUICK face values, and the collision with a given T^{n+1}.
+template <class S>
+cudaError_t launch_quick(const TmaLaunch<S> &l);
+template <class S>
+cudaError_t launch_given(const TmaLaunch<S> &l);
+// u^{n+1}, v^{n+1} of the tiles of a list into U, V.
+template <class S>
+cudaError_t launch_uv(const S *fin, long long plane, int pitch, int gnx, int gny,
+                      const lbmfvm_dev::TileHeader *tiles, int ntiles, const lbmfvm_dev::CavityDesc *cavs,
+                      const uint8_t *code, typename lbmfvm_dev::Compute<S>::type *U,
+                      typename lbmfvm_dev::Compute<S>::type *V, int tw, int th, cudaStream_t stream);
+// Sub-step s of the first ntiles tiles of a list (fv_substep_kernel).
+template <class C>
+cudaError_t launch_substep(bool quick, const C *T0, C *X, C *Y, const C *U, const C *V, const uint8_t *code,
+                           const uint8_t *fflags, int pitch, int gnx, int gny, const lbmfvm_dev::TileHeader *tiles,
+                           int ntiles, int tw, int th, int s, cudaStream_t stream);
+
+}  // namespace lbmfvm_fv

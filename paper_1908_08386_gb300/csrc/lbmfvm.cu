@@ -73,10 +73,14 @@ struct Layout {
     int pitch;
     long long plane;
     size_t f[2], T[2], code, fflags, snap, stage, red, err, cav, tiles, cavres, twall, total;
-    size_t tile_cap;  // headers the tile list holds
+    size_t tile_cap;  // headers the tile lists hold
+    // energy update in sub-steps: velocity planes U, V and the two scratch
+    // temperature planes X, Y (0 when the handle takes no sub-steps)
+    size_t uv[2], tx[2];
+    bool split;
 };
 
-Layout make_layout(const lbmfvm_grid_t &g, int prec, int ncav = 1) {
+Layout make_layout(const lbmfvm_grid_t &g, int prec, int ncav = 1, bool split = false) {
     Layout L{};
     L.pitch = (int)align_up((size_t)g.nx, 64);
     L.plane = (long long)g.ny * L.pitch;
@@ -91,6 +95,12 @@ Layout make_layout(const lbmfvm_grid_t &g, int prec, int ncav = 1) {
     L.f[1] = take(9 * (size_t)L.plane * ss);
     L.T[0] = take((size_t)L.plane * cs);
     L.T[1] = take((size_t)L.plane * cs);
+    L.split = split;
+    if (split)
+        for (int i = 0; i < 2; i++) {
+            L.uv[i] = take((size_t)L.plane * cs);
+            L.tx[i] = take((size_t)L.plane * cs);
+        }
     L.code = take((size_t)L.plane);
     L.fflags = take((size_t)L.plane);  // face flags of the finite-volume update
     L.snap = take(2 * (size_t)g.nx * g.ny * sizeof(double));
@@ -105,7 +115,8 @@ Layout make_layout(const lbmfvm_grid_t &g, int prec, int ncav = 1) {
     // enough for the smallest tile shape (32 x 8) of every configuration
     const size_t max_tiles = ((size_t)g.nx + 31) / 32 * (((size_t)g.ny + 7) / 8);
     L.tile_cap = max_tiles;
-    L.tiles = take((max_tiles + 1) * sizeof(TileHeader));  // count slot, then the headers
+    // two lists (fused step; sub-step path), each a count slot and its headers
+    L.tiles = take((max_tiles + 2) * sizeof(TileHeader));
     L.total = off;
     return L;
 }
@@ -255,7 +266,6 @@ struct lbmfvm {
     int parity;       // buffer holding the current post-collision state
     int64_t steps;    // steps since set_state
     cudaGraphExec_t graph;
-    int graph_blocks; // grid of the TMA launches the graph holds
     int64_t launches; // step-kernel launches issued (a graph replay counts its kernel nodes)
     bool use_tma;     // persistent TMA kernel (walled domains, 32/16-bit storage)
     bool stall_next;  // test hook armed by lbmfvm_inject_stall
@@ -264,7 +274,16 @@ struct lbmfvm {
     CUtensorMap map_f[2], map_T[2], map_c;
     CUtensorMap map_fo[2], map_To[2];  // output-tile boxes of the TMA tile kernel
     int tma_blocks_per_sm;
-    int ntiles;       // tiles of the TMA kernel
+    int ntiles;       // tiles of the fused list (cavities with one energy update per step)
+    int ntiles_split; // tiles of the sub-step list
+    // tiles of the sub-step list taking part in sub-step s + 1 (the list is
+    // sorted by sub-steps, largest first); its size is the largest count
+    std::vector<int> split_tiles_at;
+    bool fv_quick;    // QUICK face values instead of central ones
+    int fv_sub;       // sub-steps of a single cavity (batches: per cavity)
+    int blocks_quick, blocks_given;  // blocks per SM of the QUICK and given-temperature kernels
+    CUtensorMap map_TX;              // temperature box of the sub-steps' result plane X
+    uint64_t tiles_gen, graph_gen;   // tile-list generation, and the one the graph was captured with
     uint32_t code_crc; // CRC-32 of the node codes, identifies the geometry in checkpoints
     int tile_w, tile_h;
     // Several cavities packed in one grid (batch handles); empty for one cavity.
@@ -329,32 +348,26 @@ void launch_step_ty(const lbmfvm_t *h, int cur, cudaStream_t s) {
     step_kernel<S, TY><<<grid, block, 0, s>>>(a);
 }
 
-// Tile shapes of the TMA kernel (tile width x height, pipeline stages,
-// threads), selected by lbmfvm_opts_t.tma_config.  Stages are as many as the
-// 227 KB of shared memory allow for 32-bit storage; 16-bit storage halves the
-// population box and takes one more stage where it fits.
-template <class S, int CFG> struct TmaConfig;
-template <class S> struct TmaConfig<S, 0> { using G = TmaTile<S, 64, 16, 3, 1024>; };
-template <class S> struct TmaConfig<S, 1> { using G = TmaTile<S, 64, 16, 3, 512>; };
-template <class S> struct TmaConfig<S, 2> { using G = TmaTile<S, 64, 8, sizeof(S) == 4 ? 2 : 3, 512, 2>; };
-template <class S> struct TmaConfig<S, 3> { using G = TmaTile<S, 128, 8, sizeof(S) == 4 ? 2 : 3, 1024>; };
-// 64-bit storage: a 32 x 8 tile stages 43 KB, a 64 x 8 tile 78 KB.
-template <> struct TmaConfig<double, 0> { using G = TmaTile<double, 64, 8, 2, 256>; };
-template <> struct TmaConfig<double, 1> { using G = TmaTile<double, 32, 8, 3, 256>; };
-template <> struct TmaConfig<double, 2> { using G = TmaTile<double, 32, 16, 2, 512>; };
-template <> struct TmaConfig<double, 3> { using G = TmaTile<double, 32, 8, 2, 256, 2>; };
-// double-single storage: 8-byte elements like FP64, the same shapes
-template <> struct TmaConfig<dsf, 0> { using G = TmaTile<dsf, 64, 8, 2, 256>; };
-template <> struct TmaConfig<dsf, 1> { using G = TmaTile<dsf, 32, 8, 3, 256>; };
-template <> struct TmaConfig<dsf, 2> { using G = TmaTile<dsf, 32, 16, 2, 512>; };
-template <> struct TmaConfig<dsf, 3> { using G = TmaTile<dsf, 32, 8, 2, 256, 2>; };
-constexpr int kTmaConfigs = 4;
+
+// The handle's two tile lists, one after the other in the workspace: the
+// cavities stepped by the fused kernel (one energy update per step), then
+// those whose energy update takes sub-steps (sorted by their number, largest
+// first).  Each list starts with a count slot, whose next two words are the
+// step kernel's tile counters (one per step parity).
+struct TileList {
+    size_t slot;  // workspace offset of the count slot; the headers follow
+    int n;        // tiles
+};
+TileList list_fused(const lbmfvm_t *h) { return {h->L.tiles, h->ntiles}; }
+TileList list_split(const lbmfvm_t *h) {
+    return {h->L.tiles + (size_t)(h->ntiles + 1) * sizeof(TileHeader), h->ntiles_split};
+}
 
 // Persistent grid of the TMA kernel: one block per resident slot, or one per
 // tile when there are fewer tiles.
-int tma_grid(const lbmfvm_t *h) {
-    const int resident = h->num_sms * h->tma_blocks_per_sm;
-    return h->ntiles < resident ? h->ntiles : resident;
+int tma_grid_for(const lbmfvm_t *h, int ntiles, int per_sm) {
+    const int resident = h->num_sms * per_sm;
+    return ntiles < resident ? ntiles : resident;
 }
 
 // Tiles a block of the TMA kernel takes in a fixed order before it draws the
@@ -365,25 +378,45 @@ int fixed_tiles(int ntiles, int blocks, int stages) {
     return std::max(stages + 1, per - kTilesDrawn);
 }
 
+// Launch arguments of the TMA kernel over one tile list at step parity cur,
+// its temperature box loaded through map_T.
+template <class S>
+lbmfvm_fv::TmaLaunch<S> tma_args(const lbmfvm_t *h, int cur, TileList list, const CUtensorMap *map_T, int per_sm,
+                                 int stages, cudaStream_t s, bool stall) {
+    lbmfvm_fv::TmaLaunch<S> l{};
+    l.a = args_for<S>(h, cur);
+    l.a.stall = stall ? 1 : 0;
+    l.cavs = reinterpret_cast<const CavityDesc *>(h->base + h->L.cav);
+    // the count sits at a fixed address in front of the list, so that a
+    // captured graph reads the current count after the list has changed
+    int *count = reinterpret_cast<int *>(h->base + list.slot);
+    l.count = count;
+    l.tiles = reinterpret_cast<const TileHeader *>(h->base + list.slot) + 1;
+    l.map_f = &h->map_f[cur];
+    l.map_T = map_T;
+    l.map_c = &h->map_c;
+    l.map_fo = &h->map_fo[cur ^ 1];
+    l.map_To = &h->map_To[cur ^ 1];
+    l.ctr = count + 1 + cur;
+    l.ctr_next = count + 1 + (cur ^ 1);
+    l.blocks = tma_grid_for(h, list.n, per_sm);
+    l.nfix = fixed_tiles(list.n, l.blocks, stages);
+    l.stream = s;
+    return l;
+}
+
 template <class S, int CFG>
 void launch_tma_cfg(const lbmfvm_t *h, int cur, cudaStream_t s, bool stall) {
     using G = typename TmaConfig<S, CFG>::G;
-    StepArgs<S> a = args_for<S>(h, cur);
-    a.stall = stall ? 1 : 0;
-    const int blocks = tma_grid(h);
-    if (blocks < 1) return;  // no active tile
-    const CavityDesc *cavs = reinterpret_cast<const CavityDesc *>(h->base + h->L.cav);
-    // the count sits at a fixed address in front of the list, so that a
-    // captured graph reads the current count after the list has changed;
-    // the two tile counters (one per step parity) follow it
-    int *count = reinterpret_cast<int *>(h->base + h->L.tiles);
-    const TileHeader *tiles = reinterpret_cast<const TileHeader *>(h->base + h->L.tiles) + 1;
+    const lbmfvm_fv::TmaLaunch<S> l =
+        tma_args<S>(h, cur, list_fused(h), &h->map_T[cur], h->tma_blocks_per_sm, G::STAGES, s, stall);
+    if (l.blocks < 1) return;  // no active tile
     // launched with programmatic stream serialisation: a step overlaps its
     // launch and prologue with the previous step's last tiles (the kernel
     // waits for the previous grid before touching the state)
     cudaLaunchConfig_t lc = {};
-    lc.gridDim = dim3(blocks);
-    lc.blockDim = dim3(G::THREADS);
+    lc.gridDim = dim3(l.blocks);
+    lc.blockDim = dim3(G::BLOCK);
     lc.dynamicSmemBytes = G::SMEM_BYTES;
     lc.stream = s;
     cudaLaunchAttribute attr[1];
@@ -391,19 +424,51 @@ void launch_tma_cfg(const lbmfvm_t *h, int cur, cudaStream_t s, bool stall) {
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     lc.attrs = attr;
     lc.numAttrs = 1;
-    cudaLaunchKernelEx(&lc, step_tma_kernel<S, G>, a, cavs, tiles, (const int *)count, h->map_f[cur], h->map_T[cur],
-                       h->map_c, h->map_fo[cur ^ 1], h->map_To[cur ^ 1], count + 1 + cur, count + 1 + (cur ^ 1),
-                       fixed_tiles(h->ntiles, blocks, G::STAGES));
+    cudaLaunchKernelEx(&lc, step_tma_kernel<S, G>, l.a, l.cavs, l.tiles, l.count, *l.map_f, *l.map_T, *l.map_c,
+                       *l.map_fo, *l.map_To, l.ctr, l.ctr_next, l.nfix);
+}
+
+// The cavities of the sub-step list: velocity pass, the sub-steps, then the
+// collision with the temperature the last sub-step left in plane X.
+template <class S>
+void launch_split(const lbmfvm_t *h, int cur, cudaStream_t s) {
+    using C = typename Compute<S>::type;
+    using G = typename TmaConfig<S, kTmaConfigFv>::G;
+    const TileList list = list_split(h);
+    if (list.n < 1) return;
+    const TileHeader *tiles = reinterpret_cast<const TileHeader *>(h->base + list.slot) + 1;
+    const CavityDesc *cavs = reinterpret_cast<const CavityDesc *>(h->base + h->L.cav);
+    C *U = reinterpret_cast<C *>(h->base + h->L.uv[0]);
+    C *V = reinterpret_cast<C *>(h->base + h->L.uv[1]);
+    C *X = reinterpret_cast<C *>(h->base + h->L.tx[0]);
+    C *Y = reinterpret_cast<C *>(h->base + h->L.tx[1]);
+    const C *T0 = reinterpret_cast<const C *>(h->base + h->L.T[cur]);
+    const S *fin = reinterpret_cast<const S *>(h->base + h->L.f[cur]);
+    lbmfvm_fv::launch_uv<S>(fin, h->L.plane, h->L.pitch, h->grid.nx, h->grid.ny, tiles, list.n, cavs,
+                            h->base + h->L.code, U, V, h->tile_w, h->tile_h, s);
+    for (int sub = 1; sub <= (int)h->split_tiles_at.size(); sub++)
+        lbmfvm_fv::launch_substep<C>(h->fv_quick, T0, X, Y, U, V, h->base + h->L.code, h->base + h->L.fflags,
+                                     h->L.pitch, h->grid.nx, h->grid.ny, tiles, h->split_tiles_at[sub - 1],
+                                     h->tile_w, h->tile_h, sub, s);
+    lbmfvm_fv::launch_given<S>(tma_args<S>(h, cur, list, &h->map_TX, h->blocks_given, G::STAGES, s, false));
 }
 
 template <class S>
 void launch_step_tma(const lbmfvm_t *h, int cur, cudaStream_t s, bool stall) {
-    switch (h->tma_config) {
-        case 0: launch_tma_cfg<S, 0>(h, cur, s, stall); break;
-        case 2: launch_tma_cfg<S, 2>(h, cur, s, stall); break;
-        case 3: launch_tma_cfg<S, 3>(h, cur, s, stall); break;
-        default: launch_tma_cfg<S, 1>(h, cur, s, stall); break;
+    if (h->fv_quick) {
+        using G = typename TmaConfig<S, kTmaConfigFv>::G;
+        lbmfvm_fv::launch_quick<S>(
+            tma_args<S>(h, cur, list_fused(h), &h->map_T[cur], h->blocks_quick, G::STAGES, s, stall));
+    } else {
+        switch (h->tma_config) {
+            case 0: launch_tma_cfg<S, 0>(h, cur, s, stall); break;
+            case 2: launch_tma_cfg<S, 2>(h, cur, s, stall); break;
+            case 3: launch_tma_cfg<S, 3>(h, cur, s, stall); break;
+            case 4: launch_tma_cfg<S, 4>(h, cur, s, stall); break;
+            default: launch_tma_cfg<S, 1>(h, cur, s, stall); break;
+        }
     }
+    if (h->L.split) launch_split<S>(h, cur, s);
 }
 
 template <class S>
@@ -453,7 +518,7 @@ int build_graph(lbmfvm_t *h) {
         h->graph = nullptr;
         return fail(h, LBMFVM_ERR_CUDA, "graph instantiation failed: %s", cudaGetErrorString(e));
     }
-    h->graph_blocks = h->use_tma ? tma_grid(h) : 0;
+    h->graph_gen = h->tiles_gen;
     return LBMFVM_OK;
 }
 
@@ -533,6 +598,8 @@ void launch_rescale(lbmfvm_t *h) {
         }                                                             \
     } while (0)
 
+int clear_tile_counters(lbmfvm_t *h);
+
 int set_state_impl(lbmfvm_t *h, const float *u, const float *v, const float *T) {
     const size_t n = (size_t)h->grid.nx * h->grid.ny;
     float *stage = reinterpret_cast<float *>(h->base + h->L.stage);
@@ -549,9 +616,7 @@ int set_state_impl(lbmfvm_t *h, const float *u, const float *v, const float *T) 
     CU(h, cudaGetLastError());
     h->parity = 0;
     h->steps = 0;
-    // a step of parity p clears the tile counter of parity 1 - p for the next
-    // step; restarting at parity 0 clears both here
-    CU(h, cudaMemsetAsync(h->base + h->L.tiles + sizeof(int), 0, 2 * sizeof(int), h->s));
+    if (int r = clear_tile_counters(h)) return r;
     DISPATCH(h, launch_residual, h, 1);  // snapshot := u^0
     CU(h, cudaGetLastError());
     // The host copy of the wall temperatures and the staged inputs must stay
@@ -618,7 +683,7 @@ template <> constexpr CUtensorMapDataType tmap_type<__half>() { return CU_TENSOR
 template <> constexpr CUtensorMapDataType tmap_type<__nv_bfloat16>() { return CU_TENSOR_MAP_DATA_TYPE_BFLOAT16; }
 
 template <class S>
-int encode_maps(lbmfvm_t *h, int fw, int fh, int tw, int th, int cw, int ch);
+int encode_maps(lbmfvm_t *h, int fw, int fh, int tw, int th, int cw, int ch, size_t t_plane = 0);
 int upload_tiles(lbmfvm_t *h, int tw, int th);
 CavityDesc single_cavity_desc(const lbmfvm_t *h);
 
@@ -631,33 +696,50 @@ int setup_tma_cfg(lbmfvm_t *h) {
         h->map_fo[b] = h->map_f[b];
         h->map_To[b] = h->map_T[b];
     }
-    if (int r = encode_maps<S>(h, G::FW, G::FH, G::TWD, G::THT, G::CWD, G::CHT)) return r;
+    if (h->L.split) {
+        // the given-temperature kernel loads plane X with the central box
+        if (int r = encode_maps<S>(h, G::FW, G::FH, G::TWD, G::THT, G::CWD, G::CHT, h->L.tx[0])) return r;
+        h->map_TX = h->map_T[0];
+    }
+    // QUICK's fused kernel reaches two rows beyond the tile for temperatures
+    const int tht = h->fv_quick ? G::template WithTHalo<2>::THT : G::THT;
+    if (int r = encode_maps<S>(h, G::FW, G::FH, G::TWD, tht, G::CWD, G::CHT)) return r;
     auto kern = step_tma_kernel<S, G>;
     CU(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM_BYTES));
     int dev = 0, per_sm = 0;
     CU(h, cudaGetDevice(&dev));
     CU(h, cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev));
-    CU(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, G::THREADS, G::SMEM_BYTES));
+    CU(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, G::BLOCK, G::SMEM_BYTES));
     if (per_sm < 1) return fail(h, LBMFVM_ERR_CUDA, "TMA tile kernel does not fit on an SM");
     h->tma_blocks_per_sm = per_sm;
+    if (h->fv_quick || h->L.split) {
+        CU(h, lbmfvm_fv::prepare_modes<S>(&h->blocks_quick, &h->blocks_given));
+        if (h->blocks_quick < 1 || h->blocks_given < 1)
+            return fail(h, LBMFVM_ERR_CUDA, "TMA tile kernel of the energy-update options does not fit on an SM");
+    }
     h->tile_w = G::TW;
     h->tile_h = G::TH;
     return upload_tiles(h, G::TW, G::TH);
 }
 
-// Tile list of the TMA kernel (row by row over every active cavity) and the
-// cavity table, uploaded on the handle's stream.
+// Tile lists of the TMA kernel (row by row over every active cavity) and the
+// cavity table, uploaded on the handle's stream: cavities with one energy
+// update per step in the fused list, those with sub-steps in the second list,
+// ordered by their number of sub-steps (largest first).
 int upload_tiles(lbmfvm_t *h, int tw, int th) {
-    std::vector<TileHeader> tl;
+    std::vector<TileHeader> fused, split;
     std::vector<CavityDesc> table;
     if (!h->atlas_cavs.empty()) table = h->atlas_cavs;
     else table.push_back(single_cavity_desc(h));
-    // the count, read by the kernel, in front of the list; its y0 and ox are
-    // the step kernel's tile counters (parity 0 and 1), cleared here
-    tl.push_back(TileHeader{});
-    for (size_t c = 0; c < table.size(); c++) {
+    std::vector<size_t> order(table.size());
+    for (size_t c = 0; c < order.size(); c++) order[c] = c;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](size_t p, size_t q) { return table[p].substeps > table[q].substeps; });
+    for (size_t c : order) {
         if (!h->atlas_cavs.empty() && !h->atlas_active[c]) continue;
         const CavityDesc &cd = table[c];
+        const int m = cd.substeps < 1 ? 1 : cd.substeps;
+        std::vector<TileHeader> &tl = m > 1 ? split : fused;
         for (int y0 = cd.y0; y0 < cd.y0 + cd.ny; y0 += th)
             for (int x0 = cd.x0; x0 < cd.x0 + cd.nx; x0 += tw) {
                 TileHeader t{};
@@ -668,6 +750,7 @@ int upload_tiles(lbmfvm_t *h, int tw, int th) {
                 t.nx = cd.nx;
                 t.ny = cd.ny;
                 t.cav = (int)c;
+                t.substeps = m;
                 t.omega = cd.omega;
                 t.alpha = cd.alpha;
                 t.gbeta = cd.gbeta;
@@ -680,6 +763,8 @@ int upload_tiles(lbmfvm_t *h, int tw, int th) {
                 t.t_ref_f = (float)cd.t_ref;
                 t.fx_f = (float)cd.fx;
                 t.fy_f = (float)cd.fy;
+                const double dt = 1.0 / m;
+                t.dt_f = (float)dt;
                 auto lo = [](double d) { return (float)(d - (double)(float)d); };
                 t.omega_lo = lo(cd.omega);
                 t.alpha_lo = lo(cd.alpha);
@@ -687,19 +772,48 @@ int upload_tiles(lbmfvm_t *h, int tw, int th) {
                 t.t_ref_lo = lo(cd.t_ref);
                 t.fx_lo = lo(cd.fx);
                 t.fy_lo = lo(cd.fy);
+                t.dt_lo = lo(dt);
                 tl.push_back(t);
             }
     }
-    if (tl.size() - 1 > h->L.tile_cap)
-        return fail(h, LBMFVM_ERR_ARG, "%zu tiles exceed the list's %zu entries", tl.size() - 1, h->L.tile_cap);
-    h->ntiles = (int)tl.size() - 1;
-    tl[0].x0 = h->ntiles;
+    if (!split.empty() && !h->L.split)
+        return fail(h, LBMFVM_ERR_ARG, "a cavity takes energy sub-steps but the workspace has no room for them");
+    if (fused.size() + split.size() > h->L.tile_cap)
+        return fail(h, LBMFVM_ERR_ARG, "%zu tiles exceed the lists' %zu entries", fused.size() + split.size(),
+                    h->L.tile_cap);
+    h->ntiles = (int)fused.size();
+    h->ntiles_split = (int)split.size();
+    h->split_tiles_at.clear();
+    for (size_t i = 0; i < split.size(); i++) {
+        const int m = split[i].substeps;
+        if ((int)h->split_tiles_at.size() < m) h->split_tiles_at.resize(m, 0);
+        for (int sub = 0; sub < m; sub++) h->split_tiles_at[sub] = (int)i + 1;
+    }
+    // count slots (their tile counters cleared), each followed by its headers
+    std::vector<TileHeader> all;
+    TileHeader slot{};
+    slot.x0 = h->ntiles;
+    all.push_back(slot);
+    all.insert(all.end(), fused.begin(), fused.end());
+    slot.x0 = h->ntiles_split;
+    all.push_back(slot);
+    all.insert(all.end(), split.begin(), split.end());
+    h->tiles_gen++;
     // on the handle's stream, after the workspace has been cleared
-    CU(h, cudaMemcpyAsync(h->base + h->L.tiles, tl.data(), tl.size() * sizeof(TileHeader), cudaMemcpyHostToDevice,
+    CU(h, cudaMemcpyAsync(h->base + h->L.tiles, all.data(), all.size() * sizeof(TileHeader), cudaMemcpyHostToDevice,
                           h->s));
     CU(h, cudaMemcpyAsync(h->base + h->L.cav, table.data(), table.size() * sizeof(CavityDesc),
                           cudaMemcpyHostToDevice, h->s));
     CU(h, cudaStreamSynchronize(h->s));
+    return LBMFVM_OK;
+}
+
+// Clears the tile counters of both lists (a step of parity p clears the
+// counter of parity 1 - p for the next step; restarting at parity 0 clears
+// both).
+int clear_tile_counters(lbmfvm_t *h) {
+    CU(h, cudaMemsetAsync(h->base + list_fused(h).slot + sizeof(int), 0, 2 * sizeof(int), h->s));
+    CU(h, cudaMemsetAsync(h->base + list_split(h).slot + sizeof(int), 0, 2 * sizeof(int), h->s));
     return LBMFVM_OK;
 }
 
@@ -715,6 +829,7 @@ CavityDesc single_cavity_desc(const lbmfvm_t *h) {
     cd.t_ref = h->t_ref;
     cd.fx = h->force[0];
     cd.fy = h->force[1];
+    cd.substeps = h->fv_sub;
     for (int sd = 0; sd < 4; sd++) {
         const bool moving = h->grid.bc[sd] == LBMFVM_BC_MOVING;
         cd.wall_u[sd] = moving && sd >= 2 ? h->grid.u_lid : 0.0;
@@ -728,8 +843,10 @@ CavityDesc single_cavity_desc(const lbmfvm_t *h) {
 // Tensor maps of both population buffers (box fw x fh x 9), both
 // temperature planes (tw x th) and the node codes (cw x ch); the grid's x
 // extent is nx, so boxes reaching past it (or below zero) are zero-filled.
+// A non-zero t_plane maps that temperature plane into map_T[0] and map_T[1]
+// instead.
 template <class S>
-int encode_maps(lbmfvm_t *h, int fw, int fh, int tw, int th, int cw, int ch) {
+int encode_maps(lbmfvm_t *h, int fw, int fh, int tw, int th, int cw, int ch, size_t t_plane) {
     EncodeTiledFn enc = encode_tiled();
     if (!enc) return fail(h, LBMFVM_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
     const cuuint64_t nx = (cuuint64_t)h->grid.nx, ny = (cuuint64_t)h->grid.ny, pitch = (cuuint64_t)h->L.pitch;
@@ -746,7 +863,7 @@ int encode_maps(lbmfvm_t *h, int fw, int fh, int tw, int th, int cw, int ch) {
         using C = typename Compute<S>::type;
         const cuuint64_t strides2[1] = {pitch * sizeof(C)};
         const cuuint32_t box2[2] = {(cuuint32_t)tw, (cuuint32_t)th};
-        r = enc(&h->map_T[b], tmap_type<C>(), 2, h->base + h->L.T[b], dims2, strides2, box2, one,
+        r = enc(&h->map_T[b], tmap_type<C>(), 2, h->base + (t_plane ? t_plane : h->L.T[b]), dims2, strides2, box2, one,
                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) return fail(h, LBMFVM_ERR_CUDA, "tensor map of the temperature failed (%d)", (int)r);
@@ -768,6 +885,7 @@ int setup_tma(lbmfvm_t *h) {
         case 0: return setup_tma_cfg<S, 0>(h);
         case 2: return setup_tma_cfg<S, 2>(h);
         case 3: return setup_tma_cfg<S, 3>(h);
+        case 4: return setup_tma_cfg<S, 4>(h);
         default: return setup_tma_cfg<S, 1>(h);
     }
 }
@@ -884,6 +1002,25 @@ struct AtlasSpec {
     std::vector<uint8_t> codes;  // stored codes, ny * pitch of the packed grid
 };
 
+// Sub-steps of the energy update for a cavity: the requested number, or
+// (LBMFVM_FV_SUBSTEPS_AUTO) the fewest with alpha/m <= 0.2 and, when the
+// velocity scale U0 is known (> 0), U0^2/m <= 1.8 alpha.
+int substeps_for(int requested, double alpha, double U0) {
+    if (requested != LBMFVM_FV_SUBSTEPS_AUTO) return requested;
+    int m = (int)std::ceil(alpha / 0.2 - 1e-12);
+    if (U0 > 0.0) m = std::max(m, (int)std::ceil(U0 * U0 / (1.8 * alpha) - 1e-12));
+    return std::max(m, 1);
+}
+
+// Stability limits of the explicit energy update with m sub-steps: diffusion
+// alpha dt (1/dx^2 + 1/dy^2) <= 1/2 and central advection (U dt)^2 <= 2 alpha dt,
+// dt = 1/m.  Returns why a cavity fails them, or nullptr.
+const char *fv_unstable(double alpha, double U0, int m) {
+    if (alpha / m > 0.25) return "alpha / substeps exceeds the explicit diffusion limit 0.25";
+    if (U0 > 0.0 && U0 * U0 > 2.0 * alpha * m) return "U0^2 / substeps exceeds 2 alpha (explicit central advection limit)";
+    return nullptr;
+}
+
 int create_impl(const lbmfvm_grid_t *grid, const uint8_t *mask, double nu, double alpha, double gbeta,
                 const double *force, const lbmfvm_opts_t *opts_in, lbmfvm_t **out, const AtlasSpec *atlas = nullptr) {
     if (!out) return fail_thread(LBMFVM_ERR_ARG, "out is NULL");
@@ -909,10 +1046,23 @@ int create_impl(const lbmfvm_grid_t *grid, const uint8_t *mask, double nu, doubl
         return fail_thread(LBMFVM_ERR_ARG, "nu and alpha must be positive and finite, gbeta finite");
     const double tau = 3.0 * nu + 0.5;
     if (tau < 0.51) return fail_thread(LBMFVM_ERR_UNSTABLE, "tau = %.6g < 0.51", tau);
-    if (alpha > 0.25)
-        return fail_thread(LBMFVM_ERR_UNSTABLE, "alpha = %.6g exceeds the explicit diffusion limit 0.25", alpha);
+    if (opts.fv_scheme != LBMFVM_FV_CENTRAL && opts.fv_scheme != LBMFVM_FV_QUICK)
+        return fail_thread(LBMFVM_ERR_ARG, "fv_scheme = %d is not a LBMFVM_FV_* value", opts.fv_scheme);
+    if (opts.fv_substeps < 0 || opts.fv_substeps > 256)
+        return fail_thread(LBMFVM_ERR_ARG, "fv_substeps = %d is outside [0, 256]", opts.fv_substeps);
+    // a single cavity's sub-steps (a batch's come with its cavity table)
+    const int m = atlas ? 1 : substeps_for(opts.fv_substeps, alpha, 0.0);
+    if (!atlas)
+        if (const char *why = fv_unstable(alpha, 0.0, m))
+            return fail_thread(LBMFVM_ERR_UNSTABLE, "alpha = %.6g, %d sub-step(s): %s", alpha, m, why);
+    bool split = m > 1;
+    if (atlas)
+        for (const CavityDesc &cd : atlas->cavs) split |= cd.substeps > 1;
+    const bool fv_opt = split || opts.fv_scheme == LBMFVM_FV_QUICK;
+    if (fv_opt && (!tma_ok || opts.kernel == LBMFVM_KERNEL_GENERIC))
+        return fail_thread(LBMFVM_ERR_ARG, "QUICK face values and energy sub-steps need the TMA kernel (walls on every side)");
     if (atlas && !tma_ok) return fail_thread(LBMFVM_ERR_ARG, "a batch needs walls on every side");
-    const Layout L = make_layout(*grid, opts.store, atlas ? (int)atlas->cavs.size() : 1);
+    const Layout L = make_layout(*grid, opts.store, atlas ? (int)atlas->cavs.size() : 1, split);
     if (opts.workspace && opts.workspace_bytes < L.total)
         return fail_thread(LBMFVM_ERR_NOMEM, "workspace of %zu bytes is smaller than the %zu needed",
                            opts.workspace_bytes, L.total);
@@ -926,6 +1076,9 @@ int create_impl(const lbmfvm_grid_t *grid, const uint8_t *mask, double nu, doubl
     h->tile_y = opts.tile_y ? opts.tile_y : 8;
     h->use_tma = tma_ok && opts.kernel != LBMFVM_KERNEL_GENERIC;
     h->tma_config = opts.tma_config == LBMFVM_TMA_AUTOTUNE ? 1 : opts.tma_config;
+    h->fv_quick = opts.fv_scheme == LBMFVM_FV_QUICK;
+    h->fv_sub = m;
+    if (fv_opt) h->tma_config = kTmaConfigFv;  // the options' kernels come in this shape
     h->L = L;
     h->nu = nu;
     h->alpha = alpha;
@@ -984,7 +1137,7 @@ int create_impl(const lbmfvm_grid_t *grid, const uint8_t *mask, double nu, doubl
         return bail(LBMFVM_ERR_CUDA);
     }
     if (int r = setup_kernels(h)) return bail(r);
-    if (h->use_tma && opts.tma_config == LBMFVM_TMA_AUTOTUNE)
+    if (h->use_tma && opts.tma_config == LBMFVM_TMA_AUTOTUNE && !fv_opt)
         if (int r = autotune(h)) return bail(r);
     if (!atlas)
         if (int r = set_state_impl(h, nullptr, nullptr, nullptr)) return bail(r);
@@ -1018,8 +1171,9 @@ namespace {
 // lbmfvm_step without the joins with the caller's stream: the launches of
 // n steps on the handle's own stream.
 int step_impl(lbmfvm_t *h, int64_t n) {
-    // a tile list that changed size since the capture needs another grid
-    if (h->graph && h->use_tma && h->graph_blocks != tma_grid(h)) {
+    // tile lists that changed since the capture need other grids and
+    // sub-step launches
+    if (h->graph && h->use_tma && h->graph_gen != h->tiles_gen) {
         CU(h, cudaGraphExecDestroy(h->graph));
         h->graph = nullptr;
     }
@@ -1054,6 +1208,8 @@ void lbmfvm_opts_default(lbmfvm_opts_t *o) {
     o->tile_y = 0;
     o->kernel = LBMFVM_KERNEL_AUTO;
     o->t_ref = NAN;
+    o->fv_scheme = LBMFVM_FV_CENTRAL;
+    o->fv_substeps = 1;
 }
 
 int lbmfvm_workspace_bytes(const lbmfvm_grid_t *grid, const lbmfvm_opts_t *opts, size_t *bytes) {
@@ -1061,7 +1217,9 @@ int lbmfvm_workspace_bytes(const lbmfvm_grid_t *grid, const lbmfvm_opts_t *opts,
     if (int r = check_grid(grid)) return r;
     const int prec = opts ? opts->store : LBMFVM_F32;
     if (prec < LBMFVM_F64 || prec > LBMFVM_F32X2) return fail_thread(LBMFVM_ERR_ARG, "invalid store precision");
-    *bytes = make_layout(*grid, prec).total;
+    // sub-steps (or the automatic choice, which may take them) need the planes
+    const bool split = opts && opts->fv_substeps != 1;
+    *bytes = make_layout(*grid, prec, 1, split).total;
     return LBMFVM_OK;
 }
 
@@ -1080,10 +1238,16 @@ int lbmfvm_create(const lbmfvm_grid_t *grid, const uint8_t *mask, double Ra, dou
     const double nu = U0 * H * std::sqrt(Pr / Ra);
     const double alpha = U0 * H / std::sqrt(Ra * Pr);
     const double gbeta = U0 * U0 / (H * dT);
-    if (U0 * U0 > 2.0 * alpha)
-        return fail_thread(LBMFVM_ERR_UNSTABLE,
-                           "U0^2 = %.6g exceeds 2 alpha = %.6g (explicit central advection limit)", U0 * U0, 2 * alpha);
-    return create_impl(grid, mask, nu, alpha, gbeta, nullptr, opts, out);
+    lbmfvm_opts_t o;
+    lbmfvm_opts_default(&o);
+    if (opts) o = *opts;
+    if (o.fv_substeps < 0 || o.fv_substeps > 256)
+        return fail_thread(LBMFVM_ERR_ARG, "fv_substeps = %d is outside [0, 256]", o.fv_substeps);
+    o.fv_substeps = substeps_for(o.fv_substeps, alpha, U0);
+    if (const char *why = fv_unstable(alpha, U0, o.fv_substeps))
+        return fail_thread(LBMFVM_ERR_UNSTABLE, "U0 = %.6g, alpha = %.6g, %d sub-step(s): %s", U0, alpha,
+                           o.fv_substeps, why);
+    return create_impl(grid, mask, nu, alpha, gbeta, nullptr, &o, out);
 }
 
 int lbmfvm_create_lattice(const lbmfvm_grid_t *grid, const uint8_t *mask, double nu, double alpha, double gbeta,
@@ -1103,6 +1267,13 @@ int lbmfvm_step(lbmfvm_t *h, int64_t n) {
     if (int r = join_in(h)) return r;
     if (int r = step_impl(h, n)) return r;
     return join_out(h);
+}
+
+int lbmfvm_fv_info(const lbmfvm_t *h, int32_t *scheme, int32_t *substeps) {
+    if (!h) return fail_thread(LBMFVM_ERR_ARG, "handle is NULL");
+    if (scheme) *scheme = h->fv_quick ? LBMFVM_FV_QUICK : LBMFVM_FV_CENTRAL;
+    if (substeps) *substeps = h->fv_sub;
+    return LBMFVM_OK;
 }
 
 int lbmfvm_inject_stall(lbmfvm_t *h) {

@@ -36,6 +36,9 @@ class CavityCase:
     mask: np.ndarray | None = field(default=None, repr=False)
     t_init: float = 0.5
     name: str = ""
+    # energy-update sub-steps per lattice step: 1, or 0 for the library's
+    # automatic choice (cavities drawn at U0 = 0.1 whatever their diffusivity)
+    substeps: int = 1
 
 
 def config_small() -> CavityCase:
@@ -95,14 +98,21 @@ def random_obstacles(rng: np.random.Generator, nx: int, ny: int, N: int, kmax: i
 
 
 def cavity_batch(count: int, seed: int, sizes=(64, 96, 128, 192, 256, 384, 512), obstacles: bool = True,
-                 aspect=(1, 2)) -> list[CavityCase]:
+                 aspect=(1, 2), velocity: str = "capped") -> list[CavityCase]:
     """Uneven cavities: side N from `sizes`, aspect ratio 1 or 2 (ny = N,
     nx = a (N - 1) + 1), log10 Ra uniform in [3, 6], Pr in {0.71, 7.0}, up to
-    three obstacles.  U0 = min(0.1, 0.2 sqrt(Ra Pr)/H, 1.8 H/sqrt(Ra Pr))
-    keeps the thermal diffusivity alpha = U0 H/sqrt(Ra Pr) at or below 0.2 and
-    U0^2 below 2 alpha (the stability conditions of the explicit central FV
-    update); a size whose relaxation time would fall below 0.51 is redrawn
-    from the larger sizes."""
+    three obstacles.  The velocity scale:
+      "capped"    U0 = min(0.1, 0.2 sqrt(Ra Pr)/H, 1.8 H/sqrt(Ra Pr)) keeps
+                  the thermal diffusivity alpha = U0 H/sqrt(Ra Pr) at or below
+                  0.2 and U0^2 below 2 alpha (the stability conditions of one
+                  explicit central FV step per lattice step);
+      "substeps"  U0 = 0.1 for every cavity, and the energy update takes the
+                  sub-steps that keep alpha/m <= 0.2 and U0^2/m <= 1.8 alpha
+                  (substeps = 0: the library's automatic choice).
+    A size whose relaxation time would fall below 0.51 is redrawn from the
+    larger sizes."""
+    if velocity not in ("capped", "substeps"):
+        raise ValueError(f"velocity must be 'capped' or 'substeps', not {velocity!r}")
     rng = np.random.default_rng(seed)
     out = []
     sizes = sorted(sizes)
@@ -114,7 +124,10 @@ def cavity_batch(count: int, seed: int, sizes=(64, 96, 128, 192, 256, 384, 512),
         Pr = float(rng.choice([0.71, 7.0]))
         while True:
             H = N - 1
-            U0 = min(0.1, 0.2 * math.sqrt(Ra * Pr) / H, 1.8 * H / math.sqrt(Ra * Pr))
+            if velocity == "capped":
+                U0 = min(0.1, 0.2 * math.sqrt(Ra * Pr) / H, 1.8 * H / math.sqrt(Ra * Pr))
+            else:
+                U0 = 0.1
             tau = 3.0 * U0 * H * math.sqrt(Pr / Ra) + 0.5
             bigger = [s for s in sizes if s > N]
             if tau >= 0.51 or not bigger:
@@ -126,7 +139,8 @@ def cavity_batch(count: int, seed: int, sizes=(64, 96, 128, 192, 256, 384, 512),
             shapes = random_obstacles(rng, nx, ny, N)
             if shapes:
                 mask = rasterize(shapes, nx, ny)
-        out.append(CavityCase(nx, ny, Ra, Pr, U0 * math.sqrt(3.0), 0, mask, 0.5, name=f"c{i}_N{N}_a{a}"))
+        out.append(CavityCase(nx, ny, Ra, Pr, U0 * math.sqrt(3.0), 0, mask, 0.5, name=f"c{i}_N{N}_a{a}",
+                              substeps=1 if velocity == "capped" else 0))
     return out
 
 
@@ -134,7 +148,7 @@ def warm_start_cases(count: int = 2000, seed: int = 20190823) -> list[CavityCase
     """Training cavities of the learned warm start: the uneven-batch recipe at
     N = 128 with aspect ratio 1 (Ra log-uniform in [1e3, 1e6], Pr in
     {0.71, 7.0}, up to three obstacles)."""
-    return cavity_batch(count, seed, sizes=(128,), aspect=(1,))
+    return cavity_batch(count, seed, sizes=(128,), aspect=(1,), velocity="capped")
 
 
 def surrogate_init(widths=(32, 64, 96, 160), seed: int = 0, cin: int = 3, cout: int = 3) -> list[np.ndarray]:

@@ -96,7 +96,7 @@ def test_null_handle_calls_fail_cleanly():
     lib.lbmfvm_destroy(None)
 
 
-@pytest.mark.parametrize("cfg", [-2, 4, 99])
+@pytest.mark.parametrize("cfg", [-2, 5, 99])
 def test_rejects_unknown_tile_shapes(cfg):
     o = L.lbmfvm_opts_default()
     o.tma_config = cfg
@@ -134,3 +134,47 @@ def test_surrogate_entry_points_check_shapes_without_a_gpu():
     assert lib.lbmfvm_sg_conv3x3(16, 16, 16, None, 16, 32, None, 0, 1, 12, 16, 16, 32, 1, None) == -1
     assert "tile rules" in lib.lbmfvm_sg_last_error().decode()
     assert lib.lbmfvm_sg_adam(None, None, None, None, None, 10, 1e-3, 0.9, 0.999, 1e-8, 1, None) == -1
+
+
+def test_energy_update_options_are_checked_before_any_device_work():
+    g = L.make_grid(64, 64)
+    o = L.lbmfvm_opts_default()
+    assert (o.fv_scheme, o.fv_substeps) == (L.LBMFVM_FV_CENTRAL, 1)
+    o.fv_scheme = 2
+    with pytest.raises(L.LbmfvmError) as e:
+        L.lbmfvm_create_lattice(g, None, 0.1, 0.1, 0.0, None, o)
+    assert e.value.code == L.LBMFVM_ERR_ARG
+    o = L.lbmfvm_opts_default()
+    o.fv_substeps = -1
+    with pytest.raises(L.LbmfvmError) as e:
+        L.lbmfvm_create_lattice(g, None, 0.1, 0.1, 0.0, None, o)
+    assert e.value.code == L.LBMFVM_ERR_ARG
+    # alpha / m must stay within the explicit diffusion limit 1/4
+    o = L.lbmfvm_opts_default()
+    o.fv_substeps = 2
+    with pytest.raises(L.LbmfvmError) as e:
+        L.lbmfvm_create_lattice(g, None, 0.1, 0.55, 0.0, None, o)
+    assert e.value.code == L.LBMFVM_ERR_UNSTABLE
+    # and U0^2 / m within 2 alpha: Ra = 1e6, Pr = 7 on 64^2 at U0 = 0.1 has
+    # alpha = 0.0024, so one step is refused
+    with pytest.raises(L.LbmfvmError) as e:
+        L.lbmfvm_create(g, None, 1e6, 7.0, 0.1 * 3**0.5)
+    assert e.value.code == L.LBMFVM_ERR_UNSTABLE
+    # QUICK and sub-steps run on the TMA kernel only (walls on every side)
+    per = L.make_grid(64, 64, bc=(L.LBMFVM_BC_PERIODIC, L.LBMFVM_BC_PERIODIC, 1, 1))
+    for scheme, m in ((L.LBMFVM_FV_QUICK, 1), (L.LBMFVM_FV_CENTRAL, 2)):
+        o = L.lbmfvm_opts_default()
+        o.fv_scheme, o.fv_substeps = scheme, m
+        with pytest.raises(L.LbmfvmError) as e:
+            L.lbmfvm_create_lattice(per, None, 0.1, 0.1, 0.0, None, o)
+        assert e.value.code == L.LBMFVM_ERR_ARG
+
+
+def test_workspace_holds_the_substep_planes():
+    g = L.make_grid(70, 33)
+    o = L.lbmfvm_opts_default()
+    one = L.lbmfvm_workspace_bytes(g, o)
+    o.fv_substeps = 3
+    more = L.lbmfvm_workspace_bytes(g, o)
+    # velocity planes u, v and two scratch temperature planes, FP32
+    assert more - one >= 4 * 33 * 128 * 4

@@ -98,3 +98,27 @@ def test_random_fields_are_seeded_and_bounded():
     assert np.array_equal(T, WL.random_temperature(5, 7, seed=1))
     u, v = WL.random_velocity(5, 7, seed=2, amp=0.01)
     assert np.abs(u).max() <= 0.01 and np.abs(v).max() <= 0.01 and not np.array_equal(u, v)
+
+
+def test_substep_recipe_keeps_u0_and_the_relaxation_time():
+    capped = WL.cavity_batch(64, 20190822)
+    sub = WL.cavity_batch(64, 20190822, velocity="substeps")
+    # the same groups, drawn from the same stream (a capped U0 lowers tau and
+    # may move a cavity to a larger size)
+    assert [(c.Ra, c.Pr) for c in capped] == [(c.Ra, c.Pr) for c in sub]
+    assert all(c.ny >= d.ny for c, d in zip(capped, sub))
+    slowed = 0
+    for c, d in zip(capped, sub):
+        assert math.isclose(d.Ma / math.sqrt(3.0), 0.1) and d.substeps == 0 and c.substeps == 1
+        H = d.ny - 1
+        nu = 0.1 * H * math.sqrt(d.Pr / d.Ra)
+        assert 3 * nu + 0.5 >= 0.51 or d.ny == 512
+        # the cap slows exactly the cavities one explicit step cannot take at
+        # U0 = 0.1 (they are the ones that get sub-steps)
+        if c.ny == d.ny:
+            a01 = 0.1 * H / math.sqrt(d.Ra * d.Pr)
+            assert (c.Ma < d.Ma - 1e-15) == (a01 > 0.2 or 0.01 > 1.8 * a01)
+        slowed += c.Ma < d.Ma - 1e-15
+    assert slowed > 0
+    with pytest.raises(ValueError):
+        WL.cavity_batch(2, 1, velocity="fast")
