@@ -97,6 +97,9 @@ def load_library(path: str):
     if hasattr(lib, "orc_set_fv"):
         lib.orc_set_fv.restype = i
         lib.orc_set_fv.argtypes = [vp, i, i]
+    if hasattr(lib, "orc_set_energy"):
+        lib.orc_set_energy.restype = i
+        lib.orc_set_energy.argtypes = [vp, i]
     return lib
 
 
@@ -127,7 +130,7 @@ class Oracle:
     def __init__(self, nx, ny, *, bc=(BC_DIRICHLET, BC_DIRICHLET, BC_ADIABATIC, BC_ADIABATIC),
                  t_wall=(1.0, 0.0, 0.0, 0.0), u_lid=0.0, t_init=0.5, mask=None,
                  nu, alpha, gbeta=0.0, t_ref=None, fx=0.0, fy=0.0, fv_scheme="central", fv_substeps=1,
-                 lib=None):
+                 energy="fv", lib=None):
         lib = lib if lib is not None else _load()
         self.nx, self.ny = int(nx), int(ny)
         self.t_wall = tuple(float(t) for t in t_wall)
@@ -150,6 +153,11 @@ class Oracle:
         if (fv_scheme, fv_substeps) != ("central", 1):
             if lib.orc_set_fv(self._h, int(fv_scheme == "quick"), int(fv_substeps)) != 0:
                 raise ValueError(f"oracle: fv_substeps must be >= 1 (got {fv_substeps})")
+        if energy not in ("fv", "lbm"):
+            raise ValueError(f"oracle: energy must be 'fv' or 'lbm', not {energy!r}")
+        if energy == "lbm" and lib.orc_set_energy(self._h, 1) != 0:
+            raise ValueError("oracle: the D2Q5 energy populations could not be set up")
+        self.energy = energy
         self.nu, self.alpha, self.gbeta = float(nu), float(alpha), float(gbeta)
         self.t_init = float(t_init)
 

@@ -51,8 +51,21 @@
  *     explicit diffusion limit; obstacle wall nodes copy their partner's
  *     temperature at every sub-step.
  *
+ * Energy solver option (orc_set_energy; the finite-volume update is the
+ * default): the D2Q5 thermal lattice-Boltzmann model of Section 2.4, the
+ * paper's "LBM" comparison column.  Energy populations g_i (rest, E, N, W, S)
+ * relax toward g_eq = T w_i (1 + e_i.u / c_s^2) (Eqs. 19, 21, weights of
+ * Eq. 22) with tau_T = alpha / c_s^2 + 1/2 (Eq. 20), stream like f, and give
+ * T = sum g (Eq. 23).  Wall nodes are rebuilt by non-equilibrium
+ * extrapolation, g_b = g_eq(T_b, u_b) + g(x_f) - g_eq(T_f, u_f) (Eq. 95), with
+ * T_b the wall temperature on Dirichlet sides and T_b = T(x_f) on adiabatic
+ * sides and obstacle surfaces (zero normal gradient).  One step collides g
+ * with T^n and u^n beside f, streams both, extrapolates both at walls, then
+ * takes rho, u and T of the new step.
+ *
  * D2Q9 numbering used here (results do not depend on it): 0 rest, 1 E, 2 N,
- * 3 W, 4 S, 5 NE, 6 NW, 7 SW, 8 SE.  Weights from Eq. 9, c_s^2 = 1/3.
+ * 3 W, 4 S, 5 NE, 6 NW, 7 SW, 8 SE.  Weights from Eq. 9, c_s^2 = 1/3.  The
+ * D2Q5 set is the first five of these directions.
  *
  * Arrays are row-major [ny][nx] with x fastest and j = 0 the bottom row;
  * distributions are [9][ny][nx].
@@ -72,6 +85,8 @@ enum { SIDE_W = 0, SIDE_E = 1, SIDE_S = 2, SIDE_N = 3 };
 enum { BC_DIRICHLET = 0, BC_ADIABATIC = 1, BC_PERIODIC = 2, BC_MOVING = 3 };
 enum { K_FLUID = 0, K_WALL = 1, K_SOLID = 2 };
 enum { TH_FV = 0, TH_DIRICHLET = 1, TH_OBSTACLE = 2, TH_INERT = 3 };
+enum { ENERGY_FV = 0, ENERGY_LBM = 1 };
+#define Q5 5
 
 static const int EX[Q] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
 static const int EY[Q] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
@@ -79,6 +94,9 @@ static const int EY[Q] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
 static const double W[Q] = {4.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0, 1.0 / 9.0,
                             1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};
 static const double CS2 = 1.0 / 3.0;
+/* Eq. 22: 1/3 for the rest population of D2Q5, 1/6 for the four axis ones
+ * (their second moment gives the same c_s^2 = 1/3). */
+static const double W5[Q5] = {1.0 / 3.0, 1.0 / 6.0, 1.0 / 6.0, 1.0 / 6.0, 1.0 / 6.0};
 /* Reference density of the Boussinesq model: the p of Eq. 18 is read as the
  * reference pressure RHO0 cs^2, so the momentum source sum_i e_i F_i equals
  * rho G, the force density rho g beta (T - T_ref) of Eq. 75. */
@@ -103,6 +121,9 @@ typedef struct {
     long step;
     int fv_quick;          /* QUICK face values instead of central ones */
     int fv_substeps;       /* explicit FV sub-steps per lattice step (>= 1) */
+    int energy;            /* ENERGY_FV or ENERGY_LBM (D2Q5 populations) */
+    double tau_T;          /* relaxation time of g (Eq. 20) */
+    double *g, *gs;        /* D2Q5 populations [5][ny][nx] and post-collision scratch */
 } orc_t;
 
 static int wrap(int i, int n) {
@@ -132,6 +153,11 @@ static double feq(int q, double rho, double ux, double uy) {
     return rho * W[q] * (1.0 + eu / CS2 + eu * eu / (2.0 * CS2 * CS2) - uu / (2.0 * CS2));
 }
 
+/* Eq. 21: D2Q5 equilibrium of the energy populations. */
+static double geq(int q, double T, double ux, double uy) {
+    return T * W5[q] * (1.0 + (EX[q] * ux + EY[q] * uy) / CS2);
+}
+
 /* Eqs. 16-17 at node k. */
 static void moments(const orc_t *o, const double *f, long k, double *rho, double *ux, double *uy) {
     long n = (long)o->nx * o->ny;
@@ -152,6 +178,7 @@ void orc_destroy(orc_t *o) {
     free(o->kind); free(o->therm); free(o->partner); free(o->uw); free(o->vw);
     free(o->f); free(o->fs); free(o->T); free(o->Tn);
     free(o->rho); free(o->ux); free(o->uy); free(o->su); free(o->sv);
+    free(o->g); free(o->gs);
     free(o);
 }
 
@@ -270,6 +297,15 @@ static void compute_moments(orc_t *o) {
         }
 }
 
+/* Energy populations at equilibrium with the current T and u (Eq. 21);
+ * inert nodes hold none. */
+static void init_g(orc_t *o) {
+    long n = (long)o->nx * o->ny;
+    for (long k = 0; k < n; k++)
+        for (int q = 0; q < Q5; q++)
+            o->g[q * n + k] = (o->kind[k] == K_SOLID) ? 0.0 : geq(q, o->T[k], o->ux[k], o->uy[k]);
+}
+
 /* Initial state: f = f_eq(1, u0) at every non-inert node (Eq. 8), T = T0 with
  * Dirichlet nodes set to their wall value.  u0, v0, T0 may be NULL (rest, t_init). */
 int orc_set_state(orc_t *o, const double *u0, const double *v0, const double *T0, double t_init) {
@@ -288,6 +324,7 @@ int orc_set_state(orc_t *o, const double *u0, const double *v0, const double *T0
     o->step = 0;
     compute_moments(o);
     for (long k = 0; k < n; k++) { o->su[k] = o->ux[k]; o->sv[k] = o->uy[k]; }
+    if (o->g) init_g(o);
     return 0;
 }
 
@@ -333,6 +370,28 @@ orc_t *orc_create(int nx, int ny, const int bc[4], const double t_wall[4], doubl
     classify(o, mask);
     orc_set_state(o, NULL, NULL, NULL, t_init);
     return o;
+}
+
+/* Energy solver: ENERGY_FV (0, the finite-volume update) or ENERGY_LBM (1,
+ * the D2Q5 thermal lattice Boltzmann model).  Switching to LBM sets g to the
+ * equilibrium of the current T and u.  Returns -1 for another mode or when
+ * the populations cannot be allocated. */
+int orc_set_energy(orc_t *o, int mode) {
+    if (mode != ENERGY_FV && mode != ENERGY_LBM) return -1;
+    if (mode == ENERGY_LBM && !o->g) {
+        long n = (long)o->nx * o->ny;
+        o->g = (double *)calloc(Q5 * n, sizeof(double));
+        o->gs = (double *)calloc(Q5 * n, sizeof(double));
+        if (!o->g || !o->gs) {
+            free(o->g); free(o->gs);
+            o->g = o->gs = NULL;
+            return -1;
+        }
+    }
+    o->energy = mode;
+    o->tau_T = o->alpha / CS2 + 0.5; /* Eq. 20 with dt = 1 */
+    if (mode == ENERGY_LBM) init_g(o);
+    return 0;
 }
 
 /* Energy-update options: quick = 1 for QUICK face values, substeps >= 1.
@@ -385,6 +444,22 @@ static void step_once(orc_t *o) {
             }
         }
 
+    /* 2b. D2Q5 energy populations (Eq. 19): relaxation toward g_eq(T^n, u^n)
+     *     (Eq. 21) with tau_T (Eq. 20). */
+    if (o->energy == ENERGY_LBM) {
+        const double tau_T = o->tau_T;
+#pragma omp parallel for schedule(static) if (PARALLEL(o))
+        for (int j = 0; j < ny; j++)
+            for (int i = 0; i < nx; i++) {
+                long k = (long)j * nx + i;
+                if (o->kind[k] == K_SOLID) continue;
+                for (int q = 0; q < Q5; q++) {
+                    double gv = o->g[q * n + k];
+                    o->gs[q * n + k] = gv - (gv - geq(q, o->T[k], o->ux[k], o->uy[k])) / tau_T;
+                }
+            }
+    }
+
     /* 3. pull streaming into fluid nodes: f_q(x) = f*_q(x - e_q). */
 #pragma omp parallel for schedule(static) if (PARALLEL(o))
     for (int j = 0; j < ny; j++)
@@ -396,6 +471,20 @@ static void step_once(orc_t *o) {
                 o->f[q * n + k] = o->fs[q * n + s];
             }
         }
+
+    /* 3b. pull streaming of the energy populations into fluid nodes. */
+    if (o->energy == ENERGY_LBM) {
+#pragma omp parallel for schedule(static) if (PARALLEL(o))
+        for (int j = 0; j < ny; j++)
+            for (int i = 0; i < nx; i++) {
+                long k = (long)j * nx + i;
+                if (o->kind[k] != K_FLUID) continue;
+                for (int q = 0; q < Q5; q++) {
+                    int s = nbr(o, i, j, -EX[q], -EY[q]);
+                    o->g[q * n + k] = o->gs[q * n + s];
+                }
+            }
+    }
 
     /* 4. non-equilibrium extrapolation (Eq. 94 with rho_b = rho(x_f), Eq. 96):
      *    f_b = f_eq(rho_f, u_wall) + f(x_f) - f_eq(rho_f, u_f). */
@@ -411,6 +500,26 @@ static void step_once(orc_t *o) {
                 o->f[q * n + k] = feq(q, rf, o->uw[k], o->vw[k]) + o->f[q * n + p] - feq(q, rf, uf, vf);
         }
 
+    /* 4b. thermal non-equilibrium extrapolation (Eq. 95):
+     *     g_b = g_eq(T_b, u_b) + g(x_f) - g_eq(T_f, u_f), with T_b the wall
+     *     temperature on Dirichlet sides and T_f on adiabatic sides and
+     *     obstacle surfaces. */
+    if (o->energy == ENERGY_LBM) {
+#pragma omp parallel for schedule(static) if (PARALLEL(o))
+        for (int j = 0; j < ny; j++)
+            for (int i = 0; i < nx; i++) {
+                long k = (long)j * nx + i;
+                if (o->kind[k] != K_WALL) continue;
+                long p = o->partner[k];
+                double rf, uf, vf, Tf = 0.0;
+                moments(o, o->f, p, &rf, &uf, &vf);
+                for (int q = 0; q < Q5; q++) Tf += o->g[q * n + p];
+                double Tb = o->therm[k] == TH_DIRICHLET ? dirichlet_value(o, i, j) : Tf;
+                for (int q = 0; q < Q5; q++)
+                    o->g[q * n + k] = geq(q, Tb, o->uw[k], o->vw[k]) + o->g[q * n + p] - geq(q, Tf, uf, vf);
+            }
+    }
+
     /* 5. moments of f^{n+1}. */
     compute_moments(o);
 
@@ -422,6 +531,19 @@ static void step_once(orc_t *o) {
      *    A face is open when both sides take part in the FV balance; box walls
      *    and faces to obstacle/inert nodes carry no flux.  With m sub-steps
      *    the balance is applied m times with dt = 1/m. */
+    /* 6 (D2Q5). T^{n+1} = sum g (Eq. 23) at every node that holds
+     *     populations; inert nodes keep T. */
+    if (o->energy == ENERGY_LBM) {
+        for (long k = 0; k < n; k++) {
+            if (o->kind[k] == K_SOLID) continue;
+            double t = 0.0;
+            for (int q = 0; q < Q5; q++) t += o->g[q * n + k];
+            o->T[k] = t;
+        }
+        o->step++;
+        return;
+    }
+
     const int m_sub = o->fv_substeps;
     const double dt = 1.0 / m_sub;
     for (int sub = 0; sub < m_sub; sub++) {

@@ -421,6 +421,94 @@ def residual_cavity_fluid_nodes(make, K=150):
     return ok, f"residual {r:.9g} against {want:.9g} from two snapshots (rel. {rel:.3g}; walls would add {lid_share:.3g} of the denominator)"
 
 
+# ---- D2Q5 thermal lattice Boltzmann energy solver (Section 2.4) ----
+
+def lbm_conduction_linear(make, H=16):
+    """D2Q5 energy populations, pure conduction between T = 1 and T = 0 with
+    adiabatic top and bottom: the steady field is T = 1 - x/H to round-off
+    (a linear profile has a uniform non-equilibrium part, which the
+    extrapolation walls of Eq. 95 carry exactly) and Nu = 1."""
+    o = make(H + 1, H + 1, nu=0.1, alpha=0.2, gbeta=0.0, energy="lbm")
+    o.step(8000)
+    T = o.fields()[3]
+    x = np.arange(H + 1) / H
+    err = np.abs(T - (1 - x)[None, :]).max()
+    nh, _, nc, _ = o.nusselt()
+    ok = err <= 1e-12 and abs(nh - 1) <= 1e-12 and abs(nc - 1) <= 1e-12
+    return ok, f"max|T - (1 - x/H)| = {err:.3g}, Nu hot - 1 = {nh - 1:.3g}, Nu cold - 1 = {nc - 1:.3g}"
+
+
+def lbm_thermal_decay(make, L=64, alpha=0.1):
+    """A periodic temperature wave T = 1/2 + A sin(k y) at rest decays at the
+    rate alpha k^2 with alpha = c_s^2 (tau_T - 1/2) (Eq. 20)."""
+    o = make(3, L, bc=(PER, PER, PER, PER), nu=0.1, alpha=alpha, gbeta=0.0, energy="lbm")
+    y = np.arange(L)
+    k = 2 * np.pi / L
+    o.set_state(T=np.tile((0.5 + 1e-3 * np.sin(k * y))[:, None], (1, 3)))
+    amp = []
+    for t in (300, 3000):
+        o.step(t - o.step_count)
+        T = o.fields()[3][:, 1]
+        amp.append(2 / L * np.sum((T - 0.5) * np.sin(k * y)))
+    rate = math.log(amp[0] / amp[1]) / 2700
+    rel = abs(rate / (alpha * k * k) - 1)
+    return rel <= 0.01, f"decay rate / (alpha k^2) - 1 = {rel:.3g}"
+
+
+def lbm_thermal_advection(make, L=64, U=0.05, alpha=0.05, t=320):
+    """A temperature wave on a uniform stream (U, 0) travels downstream at U
+    (the e.u / c_s^2 term of Eq. 21)."""
+    k = 2 * np.pi / L
+    x = np.arange(L)
+    o = make(L, 3, bc=(PER, PER, PER, PER), nu=0.05, alpha=alpha, gbeta=0.0, energy="lbm")
+    o.set_state(u=np.full((3, L), U), T=np.tile((0.5 + 1e-3 * np.sin(k * x))[None, :], (3, 1)))
+    o.step(t)
+    T = o.fields()[3][1] - 0.5
+    phase = math.atan2(-np.sum(T * np.cos(k * x)), np.sum(T * np.sin(k * x)))  # T ~ sin(k (x - c t))
+    c = phase / (k * t)
+    rel = abs(c / U - 1)
+    return rel <= 0.02, f"phase speed / U - 1 = {rel:.3g}"
+
+
+def lbm_thermal_conservation(make, steps=3000):
+    """Periodic box with buoyant flow from a random temperature field: the
+    D2Q5 collision and streaming conserve sum T = sum g to round-off."""
+    rng = np.random.default_rng(11)
+    o = make(24, 19, bc=(PER, PER, PER, PER), nu=0.08, alpha=0.1, gbeta=2e-4, t_ref=0.5, energy="lbm")
+    o.set_state(T=rng.random((19, 24)))
+    e0 = o.fields()[3].sum()
+    o.step(100)
+    flow = np.abs(o.fields()[1]).max()  # the buoyant flow at its strongest
+    o.step(steps - 100)
+    T = o.fields()[3]
+    rel = abs(T.sum() - e0) / e0
+    return rel <= 1e-11 and flow > 1e-5, f"relative change of sum T over {steps} steps = {rel:.3g}"
+
+
+def lbm_thermal_walls(make):
+    """Extrapolation walls of the energy populations (Eq. 95): Dirichlet wall
+    nodes hold the wall temperature and adiabatic wall nodes and obstacle
+    surfaces their partner's temperature, to round-off (the non-equilibrium
+    part carries no energy)."""
+    ny, nx = 22, 28
+    mask = np.zeros((ny, nx), np.uint8)
+    mask[8:13, 10:16] = 1
+    o = make(nx, ny, mask=mask, nu=0.05, alpha=0.08, gbeta=5e-4, energy="lbm")
+    o.step(400)
+    _, _, _, T = o.fields()
+    kind, therm, partner = o.classes()
+    Tf, K, TH, P = T.ravel(), kind.ravel(), therm.ravel(), partner.ravel()
+    walls = np.nonzero(K == 1)[0]
+    dirichlet = walls[TH[walls] == 1]
+    other = walls[TH[walls] != 1]
+    want_d = np.where(dirichlet % nx == 0, 1.0, 0.0)
+    d_err = np.abs(Tf[dirichlet] - want_d).max()
+    o_err = np.abs(Tf[other] - Tf[P[other]]).max()
+    moving = np.ptp(T[kind == 0]) > 0.1
+    ok = d_err <= 1e-15 and o_err <= 1e-15 and len(other) > 2 * nx and moving
+    return ok, f"Dirichlet walls off by {d_err:.3g}, adiabatic/obstacle walls off their partner by {o_err:.3g}"
+
+
 QUICK = {
     "rest_state": rest_state,
     "mass_periodic": lambda m: mass_periodic(m, 2000),
@@ -443,4 +531,9 @@ QUICK = {
     "nee_wall_moments": nee_wall_moments,
     "residual_shear_wave": residual_shear_wave,
     "residual_cavity_fluid_nodes": residual_cavity_fluid_nodes,
+    "lbm_conduction_linear": lbm_conduction_linear,
+    "lbm_thermal_decay": lbm_thermal_decay,
+    "lbm_thermal_advection": lbm_thermal_advection,
+    "lbm_thermal_conservation": lambda m: lbm_thermal_conservation(m, 1000),
+    "lbm_thermal_walls": lbm_thermal_walls,
 }

@@ -35,6 +35,14 @@ MUTANTS = {
     "nusselt_trapezoid": ("(j == 0 || j == ny - 1) ? 0.5 : 1.0", "1.0"),
     "flux_nusselt_diffusion_area": ("Qs += A * un * Tf - o->alpha * A * (o->T[m] - o->T[k]);",
                                     "Qs += A * un * Tf - o->alpha * (o->T[m] - o->T[k]);"),
+    "d2q5_rest_weight": ("static const double W5[Q5] = {1.0 / 3.0,", "static const double W5[Q5] = {0.35,"),
+    "d2q5_tau_relation": ("o->tau_T = o->alpha / CS2 + 0.5;", "o->tau_T = o->alpha / 0.5 + 0.5;"),
+    "d2q5_equilibrium_velocity_factor": ("return T * W5[q] * (1.0 + (EX[q] * ux + EY[q] * uy) / CS2);",
+                                         "return T * W5[q] * (1.0 + (EX[q] * ux + EY[q] * uy));"),
+    "d2q5_walls_equilibrium_only": ("+ o->g[q * n + p] - geq(q, Tf, uf, vf);", ";"),
+    "d2q5_adiabatic_wall_cold": ("dirichlet_value(o, i, j) : Tf;", "dirichlet_value(o, i, j) : 0.0;"),
+    "d2q5_stream_direction": ("int s = nbr(o, i, j, -EX[q], -EY[q]);\n                    o->g[q * n + k]",
+                              "int s = nbr(o, i, j, EX[q], -EY[q]);\n                    o->g[q * n + k]"),
     "residual_without_square_roots": ("return sqrt(num) / sqrt(den);", "return num / den;"),
     "residual_normalised_by_snapshot": ("den += o->ux[k] * o->ux[k] + o->uy[k] * o->uy[k];",
                                         "den += o->su[k] * o->su[k] + o->sv[k] * o->sv[k];"),

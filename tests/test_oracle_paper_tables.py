@@ -70,3 +70,22 @@ def test_table1_table2_ra1e5_ra1e6_160_grid(idx):
     nmax, j = nu_max_interior(loc)
     assert nmax == pytest.approx(GOLDEN["table1_nu_max"]["hybrid"][idx], rel=0.03)
     assert abs(j / H - GOLDEN["table2_y_nu_max"]["hybrid"][idx]) <= 1.0 / H + 1e-9
+
+
+def test_table1_table2_lbm_column_ra1e4_80_grid():
+    """The D2Q5 thermal lattice-Boltzmann energy solver (Section 2.4, the
+    paper's pure-LBM column of Tables 1-2) on 81 x 81 nodes at Ra = 1e4:
+    maximum hot-wall Nusselt number within 2 % of the printed 3.5481 at the
+    printed height 0.1375 (to one node of 1/80), mean within 2 % of the
+    benchmark's 2.24 (Table 3)."""
+    n = 81
+    o = oracle.Oracle.from_groups(n, n, 1e4, 0.71, MA, energy="lbm")
+    for _ in range(200):
+        o.step(1000)
+        if o.residual() < 1e-7:
+            break
+    mean_hot, loc, _, _ = o.nusselt()
+    nmax, j = nu_max_interior(loc)
+    assert nmax == pytest.approx(GOLDEN["table1_nu_max"]["lbm"][0], rel=0.02)
+    assert abs(j / (n - 1) - GOLDEN["table2_y_nu_max"]["lbm"][0]) <= 1.0 / (n - 1) + 1e-9
+    assert mean_hot == pytest.approx(GOLDEN["table3_nu"]["reference_nu_ave"][0], rel=0.02)

@@ -33,6 +33,11 @@ PINS = [
     P.nee_wall_moments,
     P.residual_shear_wave,
     P.residual_cavity_fluid_nodes,
+    P.lbm_conduction_linear,
+    P.lbm_thermal_decay,
+    P.lbm_thermal_advection,
+    P.lbm_thermal_conservation,
+    P.lbm_thermal_walls,
 ]
 
 
@@ -86,3 +91,8 @@ def test_fv_options_are_checked():
         oracle.Oracle(8, 8, nu=0.1, alpha=0.1, fv_scheme="upwind")
     with pytest.raises(ValueError):
         oracle.Oracle(8, 8, nu=0.1, alpha=0.1, fv_substeps=0)
+
+
+def test_energy_option_is_checked():
+    with pytest.raises(ValueError):
+        oracle.Oracle(8, 8, nu=0.1, alpha=0.1, energy="mcm")
