@@ -17,7 +17,8 @@ MUTANTS = {
     "force_without_reference_temperature": ("o->gbeta * (o->T[k] - o->t_ref)", "o->gbeta * o->T[k]"),
     "weight_diagonal": ("1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0}", "1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 35.0}"),
     "tau_without_half": ("o->tau = nu / CS2 + 0.5;", "o->tau = nu / CS2 + 0.6;"),
-    "stream_push_direction": ("int s = nbr(o, i, j, -EX[q], -EY[q]);", "int s = nbr(o, i, j, -EX[q], EY[q]);"),
+    "stream_push_direction": ("int s = nbr(o, i, j, -EX[q], -EY[q]);\n                o->f[q * n + k]",
+                              "int s = nbr(o, i, j, -EX[q], EY[q]);\n                o->f[q * n + k]"),
     "nee_partner_velocity": ("feq(q, rf, o->uw[k], o->vw[k])", "feq(q, rf, uf, vf)"),
     "nee_wall_density_unit": ("feq(q, rf, o->uw[k], o->vw[k])", "feq(q, 1.0, o->uw[k], o->vw[k])"),
     "nee_equilibrium_only": ("+ o->f[q * n + p] - feq(q, rf, uf, vf);", ";"),
