@@ -100,6 +100,9 @@ def load_library(path: str):
     if hasattr(lib, "orc_set_energy"):
         lib.orc_set_energy.restype = i
         lib.orc_set_energy.argtypes = [vp, i]
+    if hasattr(lib, "orc_set_wall_bc"):
+        lib.orc_set_wall_bc.restype = i
+        lib.orc_set_wall_bc.argtypes = [vp, i]
     return lib
 
 
@@ -130,7 +133,7 @@ class Oracle:
     def __init__(self, nx, ny, *, bc=(BC_DIRICHLET, BC_DIRICHLET, BC_ADIABATIC, BC_ADIABATIC),
                  t_wall=(1.0, 0.0, 0.0, 0.0), u_lid=0.0, t_init=0.5, mask=None,
                  nu, alpha, gbeta=0.0, t_ref=None, fx=0.0, fy=0.0, fv_scheme="central", fv_substeps=1,
-                 energy="fv", lib=None):
+                 energy="fv", wall_bc="nee", lib=None):
         lib = lib if lib is not None else _load()
         self.nx, self.ny = int(nx), int(ny)
         self.t_wall = tuple(float(t) for t in t_wall)
@@ -158,6 +161,11 @@ class Oracle:
         if energy == "lbm" and lib.orc_set_energy(self._h, 1) != 0:
             raise ValueError("oracle: the D2Q5 energy populations could not be set up")
         self.energy = energy
+        if wall_bc not in ("nee", "fd"):
+            raise ValueError(f"oracle: wall_bc must be 'nee' or 'fd', not {wall_bc!r}")
+        if wall_bc == "fd":
+            lib.orc_set_wall_bc(self._h, 1)
+        self.wall_bc = wall_bc
         self.nu, self.alpha, self.gbeta = float(nu), float(alpha), float(gbeta)
         self.t_init = float(t_init)
 

@@ -63,6 +63,18 @@
  * with T^n and u^n beside f, streams both, extrapolates both at walls, then
  * takes rho, u and T of the new step.
  *
+ * Wall option (orc_set_wall_bc; extrapolation is the default): the
+ * finite-difference velocity-gradient boundary of Section 3 (hybrid method
+ * 2, Eqs. 61-72) on the box walls.  A box-wall node takes the first term of
+ * the Chapman-Enskog expansion, f_b = f_eq(rho_b, u_b) - (tau w_i / c_s^2)
+ * rho_b Q_i : S with Q_i = e_i e_i - c_s^2 I (Eqs. 67, 69-71), rho_b =
+ * rho(x_f) (Eq. 96), u_b the wall velocity, and the strain rate S from
+ * finite differences of the new velocity field: centred along the wall,
+ * second-order one-sided (-3 u_0 + 4 u_1 - u_2)/2 into the fluid, and the
+ * normal derivative of the normal velocity from continuity (Eq. 72; corners
+ * keep both one-sided derivatives).  Obstacle surfaces keep the
+ * extrapolation.
+ *
  * D2Q9 numbering used here (results do not depend on it): 0 rest, 1 E, 2 N,
  * 3 W, 4 S, 5 NE, 6 NW, 7 SW, 8 SE.  Weights from Eq. 9, c_s^2 = 1/3.  The
  * D2Q5 set is the first five of these directions.
@@ -86,6 +98,7 @@ enum { BC_DIRICHLET = 0, BC_ADIABATIC = 1, BC_PERIODIC = 2, BC_MOVING = 3 };
 enum { K_FLUID = 0, K_WALL = 1, K_SOLID = 2 };
 enum { TH_FV = 0, TH_DIRICHLET = 1, TH_OBSTACLE = 2, TH_INERT = 3 };
 enum { ENERGY_FV = 0, ENERGY_LBM = 1 };
+enum { WALL_NEE = 0, WALL_FD = 1 };
 #define Q5 5
 
 static const int EX[Q] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
@@ -122,6 +135,7 @@ typedef struct {
     int fv_quick;          /* QUICK face values instead of central ones */
     int fv_substeps;       /* explicit FV sub-steps per lattice step (>= 1) */
     int energy;            /* ENERGY_FV or ENERGY_LBM (D2Q5 populations) */
+    int wall_bc;           /* WALL_NEE or WALL_FD on the box walls */
     double tau_T;          /* relaxation time of g (Eq. 20) */
     double *g, *gs;        /* D2Q5 populations [5][ny][nx] and post-collision scratch */
 } orc_t;
@@ -394,6 +408,47 @@ int orc_set_energy(orc_t *o, int mode) {
     return 0;
 }
 
+/* Box-wall treatment: WALL_NEE (0, extrapolation) or WALL_FD (1, the
+ * finite-difference velocity-gradient scheme).  Returns -1 for another mode. */
+int orc_set_wall_bc(orc_t *o, int mode) {
+    if (mode != WALL_NEE && mode != WALL_FD) return -1;
+    o->wall_bc = mode;
+    return 0;
+}
+
+/* Velocity of node (i, j) in the state being built: wall nodes move with the
+ * wall, fluid nodes from their streamed populations, inert nodes rest. */
+static void vel_at(const orc_t *o, int i, int j, double *u, double *v) {
+    long k = (long)j * o->nx + i;
+    if (o->kind[k] == K_WALL) { *u = o->uw[k]; *v = o->vw[k]; return; }
+    if (o->kind[k] == K_SOLID) { *u = 0.0; *v = 0.0; return; }
+    double r;
+    moments(o, o->f, k, &r, u, v);
+}
+
+/* d(u, v)/d(axis) at (i, j): second-order one-sided into the domain at a
+ * non-periodic box side, centred elsewhere. */
+static void grad_at(const orc_t *o, int i, int j, int axis, double *du, double *dv) {
+    int lo = axis == 0 ? on_side(o, i, j, SIDE_W) : on_side(o, i, j, SIDE_S);
+    int hi = axis == 0 ? on_side(o, i, j, SIDE_E) : on_side(o, i, j, SIDE_N);
+    int dx = axis == 0, dy = axis == 1;
+    double u0, v0, u1, v1, u2, v2;
+    if (lo || hi) {
+        int s = lo ? 1 : -1;
+        vel_at(o, i, j, &u0, &v0);
+        vel_at(o, i + s * dx, j + s * dy, &u1, &v1);
+        vel_at(o, i + 2 * s * dx, j + 2 * s * dy, &u2, &v2);
+        *du = s * (-3.0 * u0 + 4.0 * u1 - u2) / 2.0;
+        *dv = s * (-3.0 * v0 + 4.0 * v1 - v2) / 2.0;
+    } else {
+        int p = nbr(o, i, j, dx, dy), m = nbr(o, i, j, -dx, -dy);
+        vel_at(o, p % o->nx, p / o->nx, &u1, &v1);
+        vel_at(o, m % o->nx, m / o->nx, &u2, &v2);
+        *du = (u1 - u2) / 2.0;
+        *dv = (v1 - v2) / 2.0;
+    }
+}
+
 /* Energy-update options: quick = 1 for QUICK face values, substeps >= 1.
  * Returns -1 (nothing changed) for substeps < 1. */
 int orc_set_fv(orc_t *o, int quick, int substeps) {
@@ -499,6 +554,34 @@ static void step_once(orc_t *o) {
             for (int q = 0; q < Q; q++)
                 o->f[q * n + k] = feq(q, rf, o->uw[k], o->vw[k]) + o->f[q * n + p] - feq(q, rf, uf, vf);
         }
+
+    /* 4a. finite-difference velocity-gradient walls (Eqs. 67, 69-72) on the
+     *     box walls in place of the extrapolation: f_b = f_eq(rho_f, u_w)
+     *     - (tau w_i / c_s^2) rho_f Q_i : S.  The strain rate uses the new
+     *     velocities of fluid nodes and the wall velocity of wall nodes. */
+    if (o->wall_bc == WALL_FD) {
+#pragma omp parallel for schedule(static) if (PARALLEL(o))
+        for (int j = 0; j < ny; j++)
+            for (int i = 0; i < nx; i++) {
+                long k = (long)j * nx + i;
+                if (o->kind[k] != K_WALL || o->therm[k] == TH_OBSTACLE) continue;
+                int vert = on_side(o, i, j, SIDE_W) || on_side(o, i, j, SIDE_E);
+                int hor = on_side(o, i, j, SIDE_S) || on_side(o, i, j, SIDE_N);
+                if (!vert && !hor) continue;
+                double dudx, dvdx, dudy, dvdy;
+                grad_at(o, i, j, 0, &dudx, &dvdx);
+                grad_at(o, i, j, 1, &dudy, &dvdy);
+                if (vert && !hor) dudx = -dvdy; /* Eq. 72 */
+                if (hor && !vert) dvdy = -dudx;
+                double sxx = dudx, syy = dvdy, sxy = 0.5 * (dudy + dvdx);
+                double rf, uf, vf;
+                moments(o, o->f, o->partner[k], &rf, &uf, &vf);
+                for (int q = 0; q < Q; q++) {
+                    double qs = (EX[q] * EX[q] - CS2) * sxx + 2.0 * EX[q] * EY[q] * sxy + (EY[q] * EY[q] - CS2) * syy;
+                    o->f[q * n + k] = feq(q, rf, o->uw[k], o->vw[k]) - tau * W[q] / CS2 * rf * qs;
+                }
+            }
+    }
 
     /* 4b. thermal non-equilibrium extrapolation (Eq. 95):
      *     g_b = g_eq(T_b, u_b) + g(x_f) - g_eq(T_f, u_f), with T_b the wall

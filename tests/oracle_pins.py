@@ -509,6 +509,60 @@ def lbm_thermal_walls(make):
     return ok, f"Dirichlet walls off by {d_err:.3g}, adiabatic/obstacle walls off their partner by {o_err:.3g}"
 
 
+# ---- finite-difference velocity-gradient walls (Section 3, Eqs. 61-72) ----
+
+def fd_poiseuille(make, Hs=(8, 16, 32)):
+    """Force-driven channel between finite-difference velocity-gradient
+    walls: the parabolic profile u = g_x y (H - y) / (2 nu) at second order
+    (the one-sided wall gradient is exact on a parabola, so the profile is
+    closer than with extrapolation walls)."""
+    errs = []
+    for H in Hs:
+        nu, umax = 0.1, 0.01
+        fx = 8 * nu * umax / (H * H)
+        o = make(4, H + 1, bc=(PER, PER, ADI, ADI), nu=nu, alpha=0.1, gbeta=0.0, fx=fx, wall_bc="fd")
+        o.step(int(30 * H * H / nu) + 2000)
+        u = o.fields()[1][:, 1]
+        y = np.arange(H + 1)
+        errs.append(np.sqrt(np.mean((u - fx * y * (H - y) / (2 * nu)) ** 2)) / umax)
+    orders = [math.log2(errs[i] / errs[i + 1]) for i in range(len(errs) - 1)]
+    ok = min(orders) >= 1.8 and errs[0] < 0.01
+    return ok, f"errors {['%.3g' % e for e in errs]}, orders {['%.3f' % p for p in orders]}"
+
+
+def fd_couette(make, H=16, U=0.02):
+    """Plane Couette flow between a resting wall and a sliding lid, both
+    finite-difference velocity-gradient walls: the linear profile is exact
+    (its strain is uniform, and the wall nodes carry the interior's
+    non-equilibrium part tau w_i / c_s^2 rho Q_i : S of Eq. 70)."""
+    o = make(4, H + 1, bc=(PER, PER, ADI, MOV), u_lid=U, nu=0.1, alpha=0.1, gbeta=0.0, wall_bc="fd")
+    o.step(20000)
+    u = o.fields()[1][:, 1]
+    err = np.abs(u - U * np.arange(H + 1) / H).max() / U
+    return err <= 1e-11, f"max|u - U y/H| / U = {err:.3g}"
+
+
+def fd_wall_moments(make, u_lid=0.04):
+    """Finite-difference walls rebuild box-wall nodes with the partner's
+    density (Eq. 96) and the wall velocity: Q_i : S carries no mass and no
+    momentum (sum w_i Q_i = 0, sum w_i e_i Q_i = 0)."""
+    ny, nx = 20, 26
+    mask = np.zeros((ny, nx), np.uint8)
+    mask[8:12, 10:15] = 1
+    o = make(nx, ny, bc=(DIR, DIR, ADI, MOV), u_lid=u_lid, mask=mask, nu=0.05, alpha=0.08, gbeta=5e-4, wall_bc="fd")
+    o.step(300)
+    rho, u, v, _ = o.fields()
+    kind, _, partner = o.classes()
+    walls = np.nonzero(kind.ravel() == 1)[0]
+    R, U, V = rho.ravel(), u.ravel(), v.ravel()
+    drho = np.abs(R[walls] - R[partner.ravel()[walls]]).max()
+    lid = walls[(walls // nx == ny - 1) & (walls % nx > 0) & (walls % nx < nx - 1)]
+    uw = np.where(np.isin(walls, lid), u_lid, 0.0)
+    du = max(np.abs(U[walls] - uw).max(), np.abs(V[walls]).max())
+    ok = drho <= 1e-14 and du <= 1e-15 and np.abs(u[kind == 0]).max() > 1e-3
+    return ok, f"max|rho_b - rho_f| = {drho:.3g}, max|u_b - u_w| = {du:.3g}"
+
+
 QUICK = {
     "rest_state": rest_state,
     "mass_periodic": lambda m: mass_periodic(m, 2000),
@@ -536,4 +590,7 @@ QUICK = {
     "lbm_thermal_advection": lbm_thermal_advection,
     "lbm_thermal_conservation": lambda m: lbm_thermal_conservation(m, 1000),
     "lbm_thermal_walls": lbm_thermal_walls,
+    "fd_poiseuille": lambda m: fd_poiseuille(m, (8, 16)),
+    "fd_couette": fd_couette,
+    "fd_wall_moments": fd_wall_moments,
 }

@@ -44,6 +44,12 @@ MUTANTS = {
     "d2q5_adiabatic_wall_cold": ("dirichlet_value(o, i, j) : Tf;", "dirichlet_value(o, i, j) : 0.0;"),
     "d2q5_stream_direction": ("int s = nbr(o, i, j, -EX[q], -EY[q]);\n                    o->g[q * n + k]",
                               "int s = nbr(o, i, j, EX[q], -EY[q]);\n                    o->g[q * n + k]"),
+    "fd_walls_skipped": ("if (o->wall_bc == WALL_FD) {", "if (0) {"),
+    "fd_without_tau": ("- tau * W[q] / CS2 * rf * qs;", "- W[q] / CS2 * rf * qs;"),
+    "fd_sign": ("- tau * W[q] / CS2 * rf * qs;", "+ tau * W[q] / CS2 * rf * qs;"),
+    "fd_first_order_wall_gradient": ("*du = s * (-3.0 * u0 + 4.0 * u1 - u2) / 2.0;", "*du = s * (u1 - u0);"),
+    "fd_wall_density_unit": ("o->f[q * n + k] = feq(q, rf, o->uw[k], o->vw[k]) - tau", "o->f[q * n + k] = feq(q, 1.0, o->uw[k], o->vw[k]) - tau"),
+    "fd_shear_half": ("double sxx = dudx, syy = dvdy, sxy = 0.5 * (dudy + dvdx);", "double sxx = dudx, syy = dvdy, sxy = 0.25 * (dudy + dvdx);"),
     "residual_without_square_roots": ("return sqrt(num) / sqrt(den);", "return num / den;"),
     "residual_normalised_by_snapshot": ("den += o->ux[k] * o->ux[k] + o->uy[k] * o->uy[k];",
                                         "den += o->su[k] * o->su[k] + o->sv[k] * o->sv[k];"),

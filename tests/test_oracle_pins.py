@@ -38,6 +38,9 @@ PINS = [
     P.lbm_thermal_advection,
     P.lbm_thermal_conservation,
     P.lbm_thermal_walls,
+    P.fd_poiseuille,
+    P.fd_couette,
+    P.fd_wall_moments,
 ]
 
 
@@ -93,6 +96,8 @@ def test_fv_options_are_checked():
         oracle.Oracle(8, 8, nu=0.1, alpha=0.1, fv_substeps=0)
 
 
-def test_energy_option_is_checked():
+def test_energy_and_wall_options_are_checked():
     with pytest.raises(ValueError):
         oracle.Oracle(8, 8, nu=0.1, alpha=0.1, energy="mcm")
+    with pytest.raises(ValueError):
+        oracle.Oracle(8, 8, nu=0.1, alpha=0.1, wall_bc="bounce")
