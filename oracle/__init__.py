@@ -103,6 +103,9 @@ def load_library(path: str):
     if hasattr(lib, "orc_set_wall_bc"):
         lib.orc_set_wall_bc.restype = i
         lib.orc_set_wall_bc.argtypes = [vp, i]
+    if hasattr(lib, "orc_set_grid2"):
+        lib.orc_set_grid2.restype = i
+        lib.orc_set_grid2.argtypes = [vp, i]
     return lib
 
 
@@ -133,7 +136,7 @@ class Oracle:
     def __init__(self, nx, ny, *, bc=(BC_DIRICHLET, BC_DIRICHLET, BC_ADIABATIC, BC_ADIABATIC),
                  t_wall=(1.0, 0.0, 0.0, 0.0), u_lid=0.0, t_init=0.5, mask=None,
                  nu, alpha, gbeta=0.0, t_ref=None, fx=0.0, fy=0.0, fv_scheme="central", fv_substeps=1,
-                 energy="fv", wall_bc="nee", lib=None):
+                 energy="fv", wall_bc="nee", fv_grid=1, fv_every=1, lib=None):
         lib = lib if lib is not None else _load()
         self.nx, self.ny = int(nx), int(ny)
         self.t_wall = tuple(float(t) for t in t_wall)
@@ -166,6 +169,12 @@ class Oracle:
         if wall_bc == "fd":
             lib.orc_set_wall_bc(self._h, 1)
         self.wall_bc = wall_bc
+        if fv_grid not in (1, 2):
+            raise ValueError(f"oracle: fv_grid must be 1 or 2, not {fv_grid!r}")
+        if fv_grid == 2 and lib.orc_set_grid2(self._h, int(fv_every)) != 0:
+            raise ValueError("oracle: grid setting 2 needs an even number of spacings (nodes along periodic axes), "
+                             "no obstacle, the finite-volume energy update and fv_every >= 1")
+        self.fv_grid = fv_grid
         self.nu, self.alpha, self.gbeta = float(nu), float(alpha), float(gbeta)
         self.t_init = float(t_init)
 

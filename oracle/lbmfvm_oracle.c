@@ -63,6 +63,20 @@
  * with T^n and u^n beside f, streams both, extrapolates both at walls, then
  * takes rho, u and T of the new step.
  *
+ * Grid setting 2 (orc_set_grid2; grid setting 1 is the default): the
+ * energy balance on the coarse grid of Section 5.1's second setting (Fig. 30):
+ * for a lattice of 2NX x 2NY spacings, NX x NY control volumes of 2 x 2
+ * spacings whose faces pass through lattice nodes, so the face velocities are
+ * the lattice velocities at those nodes, with no interpolation.  The volumes'
+ * centres are the odd-odd nodes.  The explicit update (central face values,
+ * conservative flux form) runs every k lattice steps with the time step k;
+ * a Dirichlet wall face lies half a volume from its centre, an adiabatic one
+ * carries no flux.  The lattice nodes' temperature is interpolated from the
+ * volumes (Section 5.1): the centre's value at a centre, the mean of the two
+ * or four nearest centres elsewhere, the nearest volume's value at an
+ * adiabatic or periodic-free side (zero gradient), the wall value on a
+ * Dirichlet wall.  Between updates the nodes keep their temperature.
+ *
  * Wall option (orc_set_wall_bc; extrapolation is the default): the
  * finite-difference velocity-gradient boundary of Section 3 (hybrid method
  * 2, Eqs. 61-72) on the box walls.  A box-wall node takes the first term of
@@ -131,6 +145,10 @@ typedef struct {
     double *Tn;            /* scratch */
     double *rho, *ux, *uy; /* moments of f^n */
     double *su, *sv;       /* residual snapshot */
+    int grid2;             /* energy balance on the coarse grid of setting 2 */
+    int fv_every;          /* lattice steps per coarse energy step (k) */
+    int ncx, ncy;          /* coarse volumes along x and y */
+    double *Tc, *Tcn;      /* volume temperatures and scratch [ncy][ncx] */
     long step;
     int fv_quick;          /* QUICK face values instead of central ones */
     int fv_substeps;       /* explicit FV sub-steps per lattice step (>= 1) */
@@ -193,6 +211,7 @@ void orc_destroy(orc_t *o) {
     free(o->f); free(o->fs); free(o->T); free(o->Tn);
     free(o->rho); free(o->ux); free(o->uy); free(o->su); free(o->sv);
     free(o->g); free(o->gs);
+    free(o->Tc); free(o->Tcn);
     free(o);
 }
 
@@ -311,6 +330,8 @@ static void compute_moments(orc_t *o) {
         }
 }
 
+static void grid2_to_nodes(orc_t *o);
+
 /* Energy populations at equilibrium with the current T and u (Eq. 21);
  * inert nodes hold none. */
 static void init_g(orc_t *o) {
@@ -339,6 +360,12 @@ int orc_set_state(orc_t *o, const double *u0, const double *v0, const double *T0
     compute_moments(o);
     for (long k = 0; k < n; k++) { o->su[k] = o->ux[k]; o->sv[k] = o->uy[k]; }
     if (o->g) init_g(o);
+    if (o->grid2) {
+        for (int J = 0; J < o->ncy; J++)
+            for (int I = 0; I < o->ncx; I++)
+                o->Tc[(long)J * o->ncx + I] = o->T[(long)(2 * J + 1) * o->nx + 2 * I + 1];
+        grid2_to_nodes(o);
+    }
     return 0;
 }
 
@@ -447,6 +474,98 @@ static void grad_at(const orc_t *o, int i, int j, int axis, double *du, double *
         *du = (u1 - u2) / 2.0;
         *dv = (v1 - v2) / 2.0;
     }
+}
+
+/* Node temperatures from the volumes of grid setting 2 (see the header). */
+static void grid2_to_nodes(orc_t *o) {
+    int nx = o->nx, ny = o->ny, cx = o->ncx, cy = o->ncy;
+    int perx = o->bc[SIDE_W] == BC_PERIODIC, pery = o->bc[SIDE_S] == BC_PERIODIC;
+    for (int j = 0; j < ny; j++)
+        for (int i = 0; i < nx; i++) {
+            long k = (long)j * nx + i;
+            if (o->therm[k] == TH_DIRICHLET) { o->T[k] = dirichlet_value(o, i, j); continue; }
+            /* volumes (and weights) along each axis: centres at odd nodes */
+            int ia[2], ja[2], ni, nj;
+            if (i % 2) { ia[0] = (i - 1) / 2; ni = 1; }
+            else if (perx) { ia[0] = (i / 2 + cx - 1) % cx; ia[1] = (i / 2) % cx; ni = 2; }
+            else if (i == 0) { ia[0] = 0; ni = 1; }
+            else if (i == nx - 1) { ia[0] = cx - 1; ni = 1; }
+            else { ia[0] = i / 2 - 1; ia[1] = i / 2; ni = 2; }
+            if (j % 2) { ja[0] = (j - 1) / 2; nj = 1; }
+            else if (pery) { ja[0] = (j / 2 + cy - 1) % cy; ja[1] = (j / 2) % cy; nj = 2; }
+            else if (j == 0) { ja[0] = 0; nj = 1; }
+            else if (j == ny - 1) { ja[0] = cy - 1; nj = 1; }
+            else { ja[0] = j / 2 - 1; ja[1] = j / 2; nj = 2; }
+            double t = 0.0;
+            for (int b = 0; b < nj; b++)
+                for (int a = 0; a < ni; a++) t += o->Tc[(long)ja[b] * cx + ia[a]];
+            o->T[k] = t / (ni * nj);
+        }
+}
+
+/* Grid setting 2 with a coarse energy step every k >= 1 lattice steps.  The
+ * lattice must span an even number of spacings along each walled axis (an
+ * even number of nodes along a periodic one) and hold no obstacle.  The
+ * volumes start from the node temperatures at their centres.  Returns -1
+ * (nothing changed) otherwise. */
+int orc_set_grid2(orc_t *o, int k) {
+    if (k < 1 || o->energy != ENERGY_FV) return -1;
+    int perx = o->bc[SIDE_W] == BC_PERIODIC, pery = o->bc[SIDE_S] == BC_PERIODIC;
+    if ((perx ? o->nx : o->nx - 1) % 2 || (pery ? o->ny : o->ny - 1) % 2) return -1;
+    for (long n = 0; n < (long)o->nx * o->ny; n++)
+        if (o->therm[n] == TH_OBSTACLE || o->therm[n] == TH_INERT) return -1;
+    o->ncx = perx ? o->nx / 2 : (o->nx - 1) / 2;
+    o->ncy = pery ? o->ny / 2 : (o->ny - 1) / 2;
+    long m = (long)o->ncx * o->ncy;
+    free(o->Tc); free(o->Tcn);
+    o->Tc = (double *)calloc(m, sizeof(double));
+    o->Tcn = (double *)calloc(m, sizeof(double));
+    if (!o->Tc || !o->Tcn) return -1;
+    for (int J = 0; J < o->ncy; J++)
+        for (int I = 0; I < o->ncx; I++) o->Tc[(long)J * o->ncx + I] = o->T[(long)(2 * J + 1) * o->nx + 2 * I + 1];
+    o->grid2 = 1;
+    o->fv_every = k;
+    grid2_to_nodes(o);
+    return 0;
+}
+
+/* One explicit energy step of grid setting 2 (time step k) with the current
+ * lattice velocities: V (T' - T) = k sum over faces of [-F_f T_f + alpha A_f
+ * (T_nb - T_P) / d], V = 4, A = 2, d = 2 between volumes and 1 to a
+ * Dirichlet wall face; F_f = A u_face.n with u_face the lattice velocity at
+ * the face's middle node; T_f the mean of the two volumes. */
+static void grid2_step(orc_t *o) {
+    int cx = o->ncx, cy = o->ncy, nx = o->nx;
+    int per[2] = {o->bc[SIDE_W] == BC_PERIODIC, o->bc[SIDE_S] == BC_PERIODIC};
+    const double dt = o->fv_every, V = 4.0, A = 2.0, alpha = o->alpha;
+    static const int FD[4][2] = {{1, 0}, {0, 1}, {-1, 0}, {0, -1}};
+    static const int SIDE[4] = {SIDE_E, SIDE_N, SIDE_W, SIDE_S};
+    for (int J = 0; J < cy; J++)
+        for (int I = 0; I < cx; I++) {
+            double TP = o->Tc[(long)J * cx + I], acc = 0.0;
+            int ci = 2 * I + 1, cj = 2 * J + 1;
+            for (int f = 0; f < 4; f++) {
+                int dx = FD[f][0], dy = FD[f][1];
+                /* the face's middle node, one node from the centre */
+                int fi = ci + dx, fj = cj + dy;
+                if (per[0]) fi = wrap(fi, nx);
+                if (per[1]) fj = wrap(fj, o->ny);
+                long kf = (long)fj * nx + fi;
+                double un = o->ux[kf] * dx + o->uy[kf] * dy;
+                int In = I + dx, Jn = J + dy;
+                int inside = 1;
+                if (In < 0 || In >= cx) { if (per[0]) In = wrap(In, cx); else inside = 0; }
+                if (Jn < 0 || Jn >= cy) { if (per[1]) Jn = wrap(Jn, cy); else inside = 0; }
+                if (inside) {
+                    double Tn = o->Tc[(long)Jn * cx + In];
+                    acc += -A * un * 0.5 * (TP + Tn) + alpha * A * (Tn - TP) / 2.0;
+                } else if (o->bc[SIDE[f]] == BC_DIRICHLET) {
+                    acc += alpha * A * (o->t_wall[SIDE[f]] - TP) / 1.0;
+                }
+            }
+            o->Tcn[(long)J * cx + I] = TP + dt * acc / V;
+        }
+    double *t = o->Tc; o->Tc = o->Tcn; o->Tcn = t;
 }
 
 /* Energy-update options: quick = 1 for QUICK face values, substeps >= 1.
@@ -614,6 +733,17 @@ static void step_once(orc_t *o) {
      *    A face is open when both sides take part in the FV balance; box walls
      *    and faces to obstacle/inert nodes carry no flux.  With m sub-steps
      *    the balance is applied m times with dt = 1/m. */
+    /* 6 (grid setting 2).  Every k-th step the coarse energy step with the
+     *     new velocity, then the node temperatures from the volumes. */
+    if (o->grid2) {
+        if ((o->step + 1) % o->fv_every == 0) {
+            grid2_step(o);
+            grid2_to_nodes(o);
+        }
+        o->step++;
+        return;
+    }
+
     /* 6 (D2Q5). T^{n+1} = sum g (Eq. 23) at every node that holds
      *     populations; inert nodes keep T. */
     if (o->energy == ENERGY_LBM) {

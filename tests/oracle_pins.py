@@ -563,6 +563,71 @@ def fd_wall_moments(make, u_lid=0.04):
     return ok, f"max|rho_b - rho_f| = {drho:.3g}, max|u_b - u_w| = {du:.3g}"
 
 
+# ---- grid setting 2 (Section 5.1, Fig. 30): coarse energy grid ----
+
+def grid2_conduction_linear(make, H=16):
+    """Grid setting 2, pure conduction: the coarse volumes and the nodes
+    interpolated from them hold T = 1 - x/H to round-off (the half-volume
+    wall distance and the two-point means are exact on a linear profile), and
+    Nu = 1."""
+    o = make(H + 1, H + 1, nu=0.1, alpha=0.2, gbeta=0.0, fv_grid=2, fv_every=2)
+    o.step(20000)
+    T = o.fields()[3]
+    x = np.arange(H + 1) / H
+    err = np.abs(T - (1 - x)[None, :]).max()
+    nh = o.nusselt()[0]
+    return err <= 1e-12 and abs(nh - 1) <= 1e-12, f"max|T - (1 - x/H)| = {err:.3g}, Nu - 1 = {nh - 1:.3g}"
+
+
+def grid2_periodic_decay(make, L=32, alpha=0.1, k=4, n=40):
+    """Grid setting 2 in a periodic box, a temperature wave along x at rest:
+    each coarse step (volumes 2 apart, time step k) multiplies it by exactly
+    g = 1 - alpha k (1 - cos(4 pi / L)) / 2, the discrete eigenvalue."""
+    o = make(L, 4, bc=(PER, PER, PER, PER), nu=0.1, alpha=alpha, gbeta=0.0, fv_grid=2, fv_every=k)
+    o.set_state(T=np.tile((0.5 + 1e-3 * np.sin(2 * np.pi * np.arange(L) / L))[None, :], (4, 1)))
+    a0 = o.fields()[3][1, 1::2] - 0.5  # the volume centres
+    o.step(n * k)
+    a1 = o.fields()[3][1, 1::2] - 0.5
+    g = 1 - alpha * k * (1 - math.cos(4 * math.pi / L)) / 2
+    err = np.abs(a1 - a0 * g ** n).max() / np.abs(a0).max()
+    return err <= 1e-11, f"max relative deviation from g^n = {err:.3g}"
+
+
+def grid2_conservation(make, n=400):
+    """Grid setting 2 in a box with adiabatic walls and buoyant flow: the
+    conservative flux form keeps the coarse volumes' total energy (4 T per
+    volume at the odd-odd centre nodes) to round-off."""
+    ny, nx = 25, 33
+    o = make(nx, ny, bc=(ADI, ADI, ADI, ADI), nu=0.06, alpha=0.1, gbeta=4e-4, t_ref=0.5, fv_grid=2, fv_every=2)
+    o.set_state(T=np.random.default_rng(9).random((ny, nx)))
+    e0 = o.fields()[3][1::2, 1::2].sum()
+    o.step(60)
+    flow = np.abs(o.fields()[1]).max()
+    o.step(n - 60)
+    rel = abs(o.fields()[3][1::2, 1::2].sum() - e0) / e0
+    return rel <= 1e-12 and flow > 1e-4, f"relative change of the volumes' energy = {rel:.3g} (max|u| {flow:.3g})"
+
+
+def grid2_same_steady_state(make, n=41):
+    """Section 5.1: both grid settings reach the same results.  At Ra = 1e4
+    the steady mean Nusselt number of setting 2 lies within 1 % of setting
+    1's, and a coarse step every 4 lattice steps reaches the steady state of
+    a step every lattice step (the steady balance has no time step in it)."""
+    out = []
+    for grid, k in ((1, 1), (2, 1), (2, 4)):
+        U0 = 0.1
+        H = n - 1
+        o = make(n, n, nu=U0 * H * math.sqrt(0.71 / 1e4), alpha=U0 * H / math.sqrt(1e4 * 0.71), gbeta=U0 * U0 / H,
+                 fv_grid=grid, fv_every=k)
+        for _ in range(200):
+            o.step(1000)
+            if o.residual() < 1e-10:
+                break
+        out.append(o.nusselt()[0])
+    d12, dk = abs(out[1] / out[0] - 1), abs(out[2] / out[1] - 1)
+    return d12 <= 0.01 and dk <= 1e-7, f"Nu {out}: settings differ by {d12:.3g}, coarse steps by {dk:.3g}"
+
+
 QUICK = {
     "rest_state": rest_state,
     "mass_periodic": lambda m: mass_periodic(m, 2000),
@@ -593,4 +658,7 @@ QUICK = {
     "fd_poiseuille": lambda m: fd_poiseuille(m, (8, 16)),
     "fd_couette": fd_couette,
     "fd_wall_moments": fd_wall_moments,
+    "grid2_conduction_linear": grid2_conduction_linear,
+    "grid2_periodic_decay": grid2_periodic_decay,
+    "grid2_conservation": grid2_conservation,
 }

@@ -50,6 +50,12 @@ MUTANTS = {
     "fd_first_order_wall_gradient": ("*du = s * (-3.0 * u0 + 4.0 * u1 - u2) / 2.0;", "*du = s * (u1 - u0);"),
     "fd_wall_density_unit": ("o->f[q * n + k] = feq(q, rf, o->uw[k], o->vw[k]) - tau", "o->f[q * n + k] = feq(q, 1.0, o->uw[k], o->vw[k]) - tau"),
     "fd_shear_half": ("double sxx = dudx, syy = dvdy, sxy = 0.5 * (dudy + dvdx);", "double sxx = dudx, syy = dvdy, sxy = 0.25 * (dudy + dvdx);"),
+    "grid2_wall_full_distance": ("acc += alpha * A * (o->t_wall[SIDE[f]] - TP) / 1.0;",
+                                 "acc += alpha * A * (o->t_wall[SIDE[f]] - TP) / 2.0;"),
+    "grid2_time_step_one": ("const double dt = o->fv_every, V = 4.0, A = 2.0, alpha = o->alpha;",
+                            "const double dt = 1.0, V = 4.0, A = 2.0, alpha = o->alpha;"),
+    "grid2_interpolation_one_sided": ("else { ia[0] = i / 2 - 1; ia[1] = i / 2; ni = 2; }", "else { ia[0] = i / 2 - 1; ni = 1; }"),
+    "grid2_face_node": ("int fi = ci + dx, fj = cj + dy;", "int fi = ci + 2 * dx, fj = cj + dy;"),
     "residual_without_square_roots": ("return sqrt(num) / sqrt(den);", "return num / den;"),
     "residual_normalised_by_snapshot": ("den += o->ux[k] * o->ux[k] + o->uy[k] * o->uy[k];",
                                         "den += o->su[k] * o->su[k] + o->sv[k] * o->sv[k];"),

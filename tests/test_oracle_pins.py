@@ -1,6 +1,7 @@
 """The FP64 oracle against closed forms, invariants and exact discrete
 solutions (CPU only).  See tests/oracle_pins.py for what each pin fixes."""
 
+import numpy as np
 import pytest
 
 import oracle
@@ -41,6 +42,10 @@ PINS = [
     P.fd_poiseuille,
     P.fd_couette,
     P.fd_wall_moments,
+    P.grid2_conduction_linear,
+    P.grid2_periodic_decay,
+    P.grid2_conservation,
+    P.grid2_same_steady_state,
 ]
 
 
@@ -101,3 +106,9 @@ def test_energy_and_wall_options_are_checked():
         oracle.Oracle(8, 8, nu=0.1, alpha=0.1, energy="mcm")
     with pytest.raises(ValueError):
         oracle.Oracle(8, 8, nu=0.1, alpha=0.1, wall_bc="bounce")
+    with pytest.raises(ValueError):  # an odd number of spacings
+        oracle.Oracle(8, 9, nu=0.1, alpha=0.1, fv_grid=2)
+    mask = np.zeros((9, 9), np.uint8)
+    mask[4, 4] = 1
+    with pytest.raises(ValueError):  # an obstacle
+        oracle.Oracle(9, 9, nu=0.1, alpha=0.1, fv_grid=2, mask=mask)
