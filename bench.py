@@ -32,7 +32,9 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-METRIC = "coupled MLUPS (1024^2 cavity, Ra 1e6) & % HBM peak"
+# The headline metric's name; the workload it is measured on is named in the
+# line's config.workload (the cavity size follows --size).
+METRIC = "coupled MLUPS & % HBM peak; time-to-steady-state vs plain FP32 at Nu err \u22640.5%"
 # Algorithmic bytes per lattice update of the fused step: read + write the
 # nine populations, read + write T, read the node code.
 BYTES_PER_LU = {"f64": 72 + 72 + 8 + 8 + 1, "f32x2": 72 + 72 + 8 + 8 + 1, "f32": 36 + 36 + 4 + 4 + 1,
@@ -41,8 +43,11 @@ BYTES_PER_LU = {"f64": 72 + 72 + 8 + 8 + 1, "f32x2": 72 + 72 + 8 + 8 + 1, "f32":
 L2_FLUSH_BYTES = 512 << 20
 FALLBACK_HBM_GBS = 6800.0
 
-# DRAM bytes per launch of step_kernel from one ncu capture
-# (profiles/step_kernel_*.md), valid only for the kernel source hashed here.
+# DRAM bytes (read + write) per launch of step_tma_kernel from one ncu
+# capture (profiles/step_tma_kernel_f32_*.md), keyed by storage, cavity side
+# and the hash of the kernel source they were taken with: a constant from that
+# capture, not measured in this run, and reported only while the source hash
+# matches.
 NCU_TRAFFIC = {("f32", 4096, "d18624217ad849dc"): 1329.1e6,
                # 1024^2: the 85 MB state stays in the 129 MB L2 between steps,
                # so DRAM sees about half the algorithmic bytes
@@ -188,6 +193,85 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def roofline_large(L, WL, dev, stream, peak, peak_kind, n=4096, launches=128, warm=128):
+    """Average launch time of the step kernel on an n x n FP32 cavity whose
+    state (about 1.4 GB at 4096^2) is ten times the L2, timed with CUDA events
+    around `launches` back-to-back launches (graph replays) after `warm`
+    untimed ones (which also capture the graph)."""
+    import torch
+
+    case = WL.config_large(n, 1e7)
+    cav = L.Cavity(case.nx, case.ny, Ra=case.Ra, Pr=case.Pr, Ma=case.Ma, store="f32", device=dev)
+    cav.step(warm)
+    torch.cuda.synchronize()
+    n0 = L.lbmfvm_launch_count(cav.h)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    cav.step(launches)
+    e1.record(stream)
+    e1.synchronize()
+    k = L.lbmfvm_launch_count(cav.h) - n0
+    launch_s = e0.elapsed_time(e1) * 1e-3 / k
+    nbytes = BYTES_PER_LU["f32"] * case.nx * case.ny
+    achieved = nbytes / launch_s / 1e9
+    traffic = NCU_TRAFFIC.get(("f32", n, kernel_hash()))
+    cav.close()
+    return {"workload": f"cavity {case.nx}x{case.ny}, Ra 1e7, Pr 0.71, U0 0.1, f32 storage",
+            "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "peak_kind": peak_kind, "traffic": traffic,
+            "traffic_source": ("ncu capture of this kernel source (hash %s)" % kernel_hash()) if traffic else None,
+            "kernel": "step_tma_kernel", "algorithmic_bytes_per_launch": nbytes, "avg_launch_us": launch_s * 1e6,
+            "launches": k, "mlups": case.nx * case.ny / launch_s / 1e6}
+
+
+# Algorithmic bytes per lattice update of the other rows of the path, FP32
+# unless named: the D2Q5 energy solver reads and writes f (9) and g (5),
+# writes T and reads the code; the sub-step path reads f and the code and
+# writes u, v (velocity pass), reads T, u, v and the code and writes T per
+# sub-step, then runs the fused kernel with the given T.
+# Grid setting 2 runs the given-temperature step every step and, every k-th
+# step, the velocity pass, the coarse step (a quarter of the nodes: T read and
+# written, four face velocities read) and the node temperatures (X and T
+# written, the code and the wall values read).
+ROW_BYTES = {"f16_storage": 45, "bf16_storage": 45, "f32x2_storage": 161, "quick": 81,
+             "substeps_2": (36 + 1 + 8) + 2 * (4 + 8 + 1 + 4) + 81, "d2q5": 36 + 36 + 20 + 20 + 4 + 1,
+             "fd_walls": 81, "grid2_k4": 81 + ((36 + 1 + 8) + (8 + 16) / 4 + (4 + 1 + 4 + 4)) / 4}
+ROW_CAVITY = {"f16_storage": dict(store="f16"), "bf16_storage": dict(store="bf16"),
+              "f32x2_storage": dict(store="f32x2"), "quick": dict(fv_scheme="quick"),
+              "substeps_2": dict(fv_substeps=2), "d2q5": dict(energy="lbm"), "fd_walls": dict(wall_bc="fd"),
+              "grid2_k4": dict(fv_grid=2, fv_every=4)}
+
+
+def rows_measurement(L, WL, dev, stream, peak, n=1024, launches=256, warm=128):
+    """Average time of one coupled step of each other row of the path on the
+    n x n Ra 1e6 cavity (CUDA events around `launches` steps, graph replays,
+    after `warm` untimed ones, which also capture the graph), with its
+    algorithmic GB/s and fraction of the HBM peak."""
+    import torch
+
+    out = {}
+    for name, kw in ROW_CAVITY.items():
+        # grid setting 2 needs an even number of spacings: one node more
+        case = WL.config_large(n + 1 if kw.get("fv_grid") == 2 else n)
+        cav = L.Cavity(case.nx, case.ny, Ra=case.Ra, Pr=case.Pr, Ma=case.Ma, device=dev, **kw)
+        cav.step(warm)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        cav.step(launches)
+        e1.record(stream)
+        e1.synchronize()
+        us = e0.elapsed_time(e1) * 1e3 / launches
+        gbs = ROW_BYTES[name] * case.nx * case.ny / (us * 1e-6) / 1e9
+        out[name] = {"workload": f"cavity {case.nx}x{case.ny}, Ra 1e6", "us_per_coupled_step": us,
+                     "mlups": case.nx * case.ny / us, "bytes_per_lu": ROW_BYTES[name], "achieved_gbs": gbs,
+                     "frac": gbs / peak}
+        cav.close()
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -272,6 +356,16 @@ def run_ours(args):
     peak, peak_kind = measured_peak()
     traffic = NCU_TRAFFIC.get((args.store, args.size, kernel_hash()))
 
+    # The same kernel on a state ten times the L2 (4096^2, FP32; Ra 1e7 keeps
+    # the thermal diffusivity inside the explicit limit): the HBM fraction of
+    # a launch whose every byte comes from DRAM.
+    large = None
+    if rank == 0 and not args.no_large and args.store == "f32":
+        large = roofline_large(L, WL, dev, stream, peak, peak_kind)
+    rows = None
+    if rank == 0 and not args.no_rows and args.size == 1024 and args.store == "f32":
+        rows = rows_measurement(L, WL, dev, stream, peak)
+
     # End to end through the C-ABI with host buffers: each step uploads the
     # initial (u, v, T) from pinned host memory, runs the chunk, reads back the
     # residual, the Nusselt number and (u, v, T).
@@ -300,6 +394,14 @@ def run_ours(args):
                "h2d_bytes_per_step": 3 * 4 * n_nodes,
                "d2h_bytes_per_step": 3 * 4 * n_nodes + 8 * case.ny + 16, "steps": ke}
 
+    # Time to steady state of a bounded seeded sample of the uneven-cavity
+    # draw (the second half of the metric), sharded over the ranks.
+    tts = None
+    if args.tts_cavities > 0 and args.size == 1024 and args.store == "f32":
+        del cav
+        torch.cuda.empty_cache()
+        tts = time_to_steady(args.tts_cavities, args.seed, tuple(int(x) for x in args.tts_sizes.split(",")),
+                             rank=rank, world=world)
     if rank != 0:
         return
     line = {
@@ -313,10 +415,14 @@ def run_ours(args):
                    "wall_s": wall_s, "final_residual": last[0] if last else None,
                    "final_nusselt": last[1] if last else None},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": traffic, "kernel": "step_kernel" if args.kernel == "generic" or args.store == "f64" else "step_tma_kernel", "peak_kind": peak_kind,
+                     "traffic": traffic,
+                     "traffic_source": ("ncu capture of this kernel source (hash %s)" % kernel_hash()) if traffic else None, "kernel": "step_kernel" if args.kernel == "generic" or args.store == "f64" else "step_tma_kernel", "peak_kind": peak_kind,
                      "algorithmic_bytes_per_launch": bytes_per_launch, "avg_launch_us": launch_s * 1e6,
                      "coupled_steps_per_launch": k_steps / k_launches,
                      "us_per_coupled_step": launch_s * 1e6 * k_launches / k_steps},
+        "roofline_large": large,
+        "rows": rows,
+        "time_to_steady": tts,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": timed_launches + 3 * args.steps,
@@ -325,39 +431,97 @@ def run_ours(args):
     print(json.dumps(line), flush=True)
 
 
-def run_steady(args):
-    """Time to steady state (residual below --tol) of a seeded draw of uneven
+def golden_steady_nusselt(seed, sizes, velocity):
+    """Steady hot-wall Nusselt numbers of the FP64 oracle for the seeded draw
+    (tests/golden/steady_nusselt.json, written by the oracle script beside
+    it), or None when the draw is not the stored one."""
+    p = os.path.join(ROOT, "tests", "golden", "steady_nusselt.json")
+    try:
+        d = json.load(open(p))
+    except Exception:
+        return None
+    if d.get("seed") != seed or tuple(d.get("sizes", ())) != tuple(sizes) or d.get("velocity") != velocity:
+        return None
+    return {row["index"]: row["nu_mean_hot"] for row in d["cavities"]}
+
+
+def time_to_steady(count, seed, sizes, velocity="capped", store_fast="f16", tol=1e-8, warm=True, plain=True,
+                   rank=0, world=1):
+    """Time to steady state (residual below tol) of a seeded draw of uneven
     cavities: the fast form (one batch, 16-bit storage on the precision
-    ladder, learned warm start) against the plain per-cavity FP32 loop; one
-    JSON line."""
+    ladder, learned warm start) against the plain per-cavity FP32 loop, both
+    finishing in double-single.  With several ranks the cavities are sharded
+    (longest first by nodes) and the per-cavity results gathered; times are
+    the slowest rank's.  The Nusselt numbers are checked against the FP64
+    oracle's steady values stored for this draw."""
     import numpy as np
     import torch
 
-    from paper_1908_08386_gb300 import steady, surrogate, workloads
+    from paper_1908_08386_gb300 import replicas, steady, surrogate, workloads
 
-    sizes = tuple(int(s) for s in args.sizes.split(","))
-    cases = workloads.cavity_batch(args.cavities, args.seed, sizes=sizes)
-    nodes = sum(c.nx * c.ny for c in cases)
+    cases = workloads.cavity_batch(count, seed, sizes=sizes, velocity=velocity)
+    mine = replicas.shard([c.nx * c.ny for c in cases], world)[rank]
+    local = [cases[i] for i in mine]
     weights = os.path.join(ROOT, "paper_1908_08386_gb300", "data", "warmstart_128.npz")
-    net = None if args.no_warm else surrogate.Surrogate.load(weights)
+    net = surrogate.Surrogate.load(weights) if warm else None
     torch.cuda.synchronize()
-    fast_s, fast_steps, fast_r, fast_nu = steady.fast_form(cases, net, store=args.store_fast, tol=args.tol)
-    line = {"metric": f"time to steady state (residual < {args.tol:g}) of {len(cases)} uneven cavities",
-            "value": fast_s, "unit": "s", "n_gpus": 1, "higher_is_better": False, "scaling": "weak",
+    replicas.barrier(world)
+    fast_s, fast_steps, fast_r, fast_nu = steady.fast_form(local, net, store=store_fast, tol=tol)
+    fast_s = replicas.max_over_ranks(fast_s, world)
+    rows = [(i, int(fast_steps[k]), float(fast_r[k]), float(fast_nu[k])) for k, i in enumerate(mine)]
+    out = {"cavities": len(cases), "nodes": sum(c.nx * c.ny for c in cases), "seed": seed, "sizes": list(sizes),
+           "velocity": velocity, "tol": tol,
+           "fast_form": f"one batch per GPU, {store_fast} storage on the precision ladder (FP32, then double-single)"
+                        + (", learned warm start" if warm else ""),
+           "fast_s": fast_s}
+    if plain:
+        replicas.barrier(world)
+        plain_s, plain_steps, plain_r, plain_nu = steady.plain_loop(local, tol=tol)
+        plain_s = replicas.max_over_ranks(plain_s, world)
+        rows = [r + (int(plain_steps[k]), float(plain_r[k]), float(plain_nu[k])) for k, r in enumerate(rows)]
+        out.update(plain_s=plain_s, plain_form="one FP32 handle per cavity, double-single finish at the same switch",
+                   speedup_vs_plain=plain_s / fast_s)
+    table = sorted(replicas.gather_rows(rows, world))
+    fnu = np.array([t[3] for t in table])
+    out.update(fast_steps_max=max(t[1] for t in table), fast_steps_sum=sum(t[1] for t in table),
+               fast_residual_max=max(t[2] for t in table))
+    if plain:
+        pnu = np.array([t[6] for t in table])
+        out.update(plain_steps_sum=sum(t[4] for t in table), plain_residual_max=max(t[5] for t in table),
+                   nu_max_rel_diff_fast_vs_plain=float(np.max(np.abs(fnu - pnu) / np.abs(pnu))))
+    gold = golden_steady_nusselt(seed, sizes, velocity)
+    if gold is not None and all(t[0] in gold for t in table):
+        onu = np.array([gold[t[0]] for t in table])
+        out["nu_vs_oracle"] = {"max_rel_err_fast": float(np.max(np.abs(fnu - onu) / np.abs(onu))),
+                               "within_0.5pct": bool(np.all(np.abs(fnu - onu) <= 5e-3 * np.abs(onu))),
+                               "cavities": len(table),
+                               "source": "FP64 oracle steady states, tests/golden/steady_nusselt.json"}
+        if plain:
+            out["nu_vs_oracle"]["max_rel_err_plain"] = float(np.max(np.abs(pnu - onu) / np.abs(onu)))
+    if world > 1:
+        out["parallelism"] = f"cavities sharded over {world} GPUs (slowest rank's time)"
+    return out
+
+
+def run_steady(args):
+    """Time to steady state of a seeded draw of uneven cavities on its own
+    (one JSON line, value = the fast form's seconds)."""
+    rank, world, _ = dist_setup(args.gpus)
+    import torch
+
+    if world == 1:
+        torch.cuda.set_device(0)
+    sizes = tuple(int(x) for x in args.sizes.split(","))
+    t = time_to_steady(args.cavities, args.seed, sizes, args.velocity, args.store_fast, args.tol, not args.no_warm,
+                       not args.no_plain, rank, world)
+    if rank != 0:
+        return
+    line = {"metric": f"time to steady state (residual < {args.tol:g}) of {t['cavities']} uneven cavities",
+            "value": t["fast_s"], "unit": "s", "n_gpus": world, "higher_is_better": False, "scaling": "strong",
             "vs_baseline": None, "dtype": args.store_fast, "data": "synthetic",
             "config": {"workload": f"uneven cavities, seed {args.seed}, sides {sizes}, aspect 1/2, Ra 1e3-1e6, "
-                                   f"Pr 0.71/7, 0-3 obstacles", "cavities": len(cases), "nodes": nodes,
-                       "fast_form": f"one batch, {args.store_fast} storage on the precision ladder"
-                                    + ("" if args.no_warm else ", learned warm start"),
-                       "fast_steps_max": int(fast_steps.max()), "fast_steps_sum": int(fast_steps.sum()),
-                       "fast_residual_max": float(np.max(fast_r))}}
-    if not args.no_plain:
-        plain_s, plain_steps, plain_r, plain_nu = steady.plain_loop(cases, tol=args.tol)
-        line["plain_fp32_loop_s"] = plain_s
-        line["speedup_vs_plain"] = plain_s / fast_s
-        line["config"]["plain_steps_sum"] = int(plain_steps.sum())
-        line["config"]["plain_residual_max"] = float(np.max(plain_r))
-        line["nu_max_rel_diff_vs_plain"] = float(np.max(np.abs(fast_nu - plain_nu) / np.abs(plain_nu)))
+                                   f"Pr 0.71/7, 0-3 obstacles, U0 {args.velocity}"},
+            "time_to_steady": t}
     print(json.dumps(line), flush=True)
 
 
@@ -367,6 +531,11 @@ def main():
                     help="step: MLUPS of the fused step (default); steady: time to steady state of uneven cavities")
     ap.add_argument("--cavities", type=int, default=64)
     ap.add_argument("--sizes", default="64,96,128,192,256,384,512")
+    ap.add_argument("--velocity", choices=["capped", "substeps"], default="capped",
+                    help="velocity scale of the uneven draw: capped U0, or U0 = 0.1 with energy sub-steps")
+    ap.add_argument("--tts-cavities", type=int, default=32,
+                    help="cavities of the default line's time-to-steady sample (0 skips it)")
+    ap.add_argument("--tts-sizes", default="64,96,128")
     ap.add_argument("--seed", type=int, default=20190822)
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--store-fast", choices=["f16", "bf16", "f32"], default="f16")
@@ -381,10 +550,12 @@ def main():
     ap.add_argument("--chunk", type=int, default=1000, help="coupled steps per benchmark step")
     ap.add_argument("--store", choices=["f32", "f16", "bf16", "f64", "f32x2"], default="f32")
     ap.add_argument("--kernel", choices=["auto", "tma", "generic"], default="auto")
-    ap.add_argument("--tma-config", type=int, default=1)
+    ap.add_argument("--tma-config", default="default", help="tile shape 0-4, 'default' or 'auto'")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-large", action="store_true", help="skip the 4096^2 roofline_large measurement")
+    ap.add_argument("--no-rows", action="store_true", help="skip the timing of the other rows of the path")
     ap.add_argument("--ref-chunk", type=int, default=10, help="coupled steps per reference-arm step")
     args = ap.parse_args()
     if args.impl == "reference":

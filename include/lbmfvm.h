@@ -84,12 +84,45 @@ extern "C" {
 #define LBMFVM_KERNEL_GENERIC 1
 #define LBMFVM_KERNEL_TMA 2
 #define LBMFVM_TMA_AUTOTUNE (-1)
+#define LBMFVM_TMA_DEFAULT (-2)
 
 /* Face temperatures of the explicit energy update (lbmfvm_opts_t.fv_scheme)
  * and automatic sub-steps (lbmfvm_opts_t.fv_substeps). */
 #define LBMFVM_FV_CENTRAL 0
 #define LBMFVM_FV_QUICK 1
 #define LBMFVM_FV_SUBSTEPS_AUTO 0
+
+/* Energy solver (lbmfvm_opts_t.energy).
+ *   FV        the explicit finite-volume energy balance of Section 5 (the
+ *             hybrid method; default);
+ *   LBM_D2Q5  the D2Q5 thermal lattice-Boltzmann model of Section 2.4 (the
+ *             paper's pure-LBM comparison, Tables 1-2): energy populations
+ *             g_i relax toward g_eq = T w_i (1 + e_i.u / c_s^2) (Eqs. 19, 21,
+ *             22) with tau_T = alpha / c_s^2 + 1/2 (Eq. 20), stream like f
+ *             and give T = sum g (Eq. 23); walls rebuild g by
+ *             non-equilibrium extrapolation (Eq. 95) with the wall
+ *             temperature on Dirichlet sides and the partner's temperature on
+ *             adiabatic sides and obstacle surfaces.  One step is one launch
+ *             of its own kernel (one node per thread, pulls from global
+ *             memory).  F64, F32 or F32X2 storage; single cavities only; no
+ *             energy-update options. */
+#define LBMFVM_ENERGY_FV 0
+#define LBMFVM_ENERGY_LBM_D2Q5 1
+
+/* Box-wall treatment of the populations (lbmfvm_opts_t.wall_bc).
+ *   NEE  non-equilibrium extrapolation, f_b = f_eq(rho_f, u_w) + f(x_f)
+ *        - f_eq(rho_f, u_f) (Eqs. 94, 96; default);
+ *   FD   the finite-difference velocity-gradient scheme of Section 3
+ *        (hybrid method 2, Eqs. 61-72): f_b = f_eq(rho_f, u_w) - (tau w_i /
+ *        c_s^2) rho_f Q_i : S with Q_i = e_i e_i - c_s^2 I (Eqs. 67, 69-71),
+ *        the strain rate S from finite differences of the new velocity field
+ *        (centred along the wall, second-order one-sided into the fluid) and
+ *        the normal strain from continuity (Eq. 72) off the corners.
+ *        Obstacle surfaces keep the extrapolation.  Runs on the GENERIC
+ *        kernel (the one-sided differences reach two nodes into the fluid);
+ *        single cavities with the finite-volume energy update only. */
+#define LBMFVM_WALL_NEE 0
+#define LBMFVM_WALL_FD 1
 
 /* Storage precision of the distributions.  F32/F16/BF16 store f - w_i and
  * compute in FP32 with FP32 temperature; F64 stores and computes in FP64.
@@ -120,17 +153,24 @@ typedef struct {
     int32_t tile_y;         /* rows per thread block of the generic step kernel:
                                0 = default, else one of 4, 8, 16 */
     int32_t kernel;         /* LBMFVM_KERNEL_*; default AUTO */
-    int32_t tma_config;     /* tile shape of the TMA kernel, 0..4, or
+    int32_t tma_config;     /* tile shape of the TMA kernel, 0..5,
+                               LBMFVM_TMA_DEFAULT (the default) or
                                LBMFVM_TMA_AUTOTUNE.  32- and 16-bit storage
                                (width x height, threads, input stages at 32 / 16
-                               bit): 64x16, 1024, 3/3; 64x16, 512, 3/3 (the
-                               default, 1); 64x8, 512, 2/3 (two blocks per SM);
-                               128x8, 1024, 2/3; 64x16, 512 + 128 ring threads
-                               (four warps that take the one-node ring's moments
-                               and issue the copies), 3/3.  64-bit storage:
-                               64x8, 256, 2; 32x8, 256, 3; 32x16, 512, 2; 32x8,
-                               256, 2 (two blocks per SM); 32x8, 256 + 64 ring
-                               threads, 3.  LBMFVM_TMA_AUTOTUNE times every
+                               bit, population halo rows): 64x16, 1024, 3/3, 3;
+                               64x16, 512, 3/3, 3; 64x8, 512, 2/3, 3 (two blocks
+                               per SM); 128x8, 1024, 2/3, 3; 64x16, 512 + 128 ring
+                               threads (four warps that take the one-node ring's
+                               moments and issue the copies), 3/3, 2; the same
+                               with 3 halo rows.  64-bit storage: 64x8, 256, 2;
+                               32x8, 256, 3; 32x16, 512, 2; 32x8, 256, 2 (two
+                               blocks per SM); 32x8, 256 + 64 ring threads, 3;
+                               the same with 3 halo rows (64-bit shapes 0-4 take 2).
+                               LBMFVM_TMA_DEFAULT: 4 when both population buffers
+                               and temperature planes fit in the L2, 5 otherwise
+                               (32- and 16-bit storage), 3 for 64-bit storage:
+                               the fastest measured on 1024^2 and 4096^2 cavities.
+                               LBMFVM_TMA_AUTOTUNE times every
                                shape on the handle's own grid at create and keeps
                                the fastest (remembered per storage precision and
                                power-of-two size class for the process); shapes
@@ -161,6 +201,29 @@ typedef struct {
                                U0^2/m <= 2 alpha.  QUICK and m != 1 need the TMA
                                kernel (walls on every side); they fix its tile
                                shape to 1 (no autotuning). */
+    int32_t energy;         /* LBMFVM_ENERGY_FV (default) or LBMFVM_ENERGY_LBM_D2Q5 */
+    int32_t wall_bc;        /* LBMFVM_WALL_NEE (default) or LBMFVM_WALL_FD */
+    int32_t fv_grid;        /* 1 (default): the energy balance on the lattice's own
+                               node-centred volumes (grid setting 1, Fig. 29);
+                               2: grid setting 2 (Section 5.1, Fig. 30), NX x NY
+                               control volumes of 2 x 2 lattice spacings whose
+                               faces pass through lattice nodes (face velocities
+                               are lattice velocities), centres at the odd-odd
+                               nodes, node temperatures interpolated from the
+                               volumes (the centre's value, the mean of two or
+                               four centres, the nearest volume on a wall without
+                               heat flux, the wall value on a Dirichlet wall).
+                               Grid setting 2 needs an even number of spacings
+                               along each axis, no obstacle, walls on every side,
+                               the central update without sub-steps, single
+                               cavities; it takes four more launches on a coarse
+                               step and the collision with the node temperatures
+                               every step; no checkpoints. */
+    int32_t fv_every;       /* grid setting 2: lattice steps per coarse explicit
+                               energy step, each of time step fv_every (default
+                               1; alpha * fv_every <= 0.8, the coarse explicit
+                               limit beside a Dirichlet wall).  A captured graph
+                               of steps is used when fv_every divides 64. */
 } lbmfvm_opts_t;
 
 /* Fill *opts with the defaults listed above. */
@@ -391,7 +454,13 @@ typedef struct {
     uint32_t payload_crc;       /* CRC-32 of the payload */
     int32_t fv_scheme;          /* LBMFVM_FV_* of the energy update */
     int32_t fv_substeps;        /* its sub-steps per lattice step (0 is read as 1) */
-    uint8_t pad[84];            /* zero */
+    int32_t energy;             /* LBMFVM_ENERGY_*; with LBM_D2Q5 the payload ends
+                                   with both energy-population buffers, [5][ny][nx]
+                                   each in the storage type, stored as g_i - w_i T_0
+                                   (T_0 = (t_wall[W] + t_wall[E]) / 2), current
+                                   state first */
+    int32_t wall_bc;            /* LBMFVM_WALL_* */
+    uint8_t pad[76];            /* zero */
     uint32_t header_crc;        /* CRC-32 of the 252 bytes before it */
 } lbmfvm_checkpoint_header_t;
 

@@ -35,6 +35,7 @@ LBMFVM_BC_DIRICHLET, LBMFVM_BC_ADIABATIC, LBMFVM_BC_PERIODIC, LBMFVM_BC_MOVING =
 LBMFVM_KERNEL_AUTO, LBMFVM_KERNEL_GENERIC, LBMFVM_KERNEL_TMA = 0, 1, 2
 KERNELS = {"auto": LBMFVM_KERNEL_AUTO, "generic": LBMFVM_KERNEL_GENERIC, "tma": LBMFVM_KERNEL_TMA}
 LBMFVM_TMA_AUTOTUNE = -1
+LBMFVM_TMA_DEFAULT = -2
 # Storage precisions
 LBMFVM_F64, LBMFVM_F32, LBMFVM_F16, LBMFVM_BF16, LBMFVM_F32X2 = 0, 1, 2, 3, 4
 PRECISIONS = {"f64": LBMFVM_F64, "f32": LBMFVM_F32, "f16": LBMFVM_F16, "bf16": LBMFVM_BF16,
@@ -43,6 +44,12 @@ PRECISIONS = {"f64": LBMFVM_F64, "f32": LBMFVM_F32, "f16": LBMFVM_F16, "bf16": L
 LBMFVM_FV_CENTRAL, LBMFVM_FV_QUICK = 0, 1
 FV_SCHEMES = {"central": LBMFVM_FV_CENTRAL, "quick": LBMFVM_FV_QUICK}
 LBMFVM_FV_SUBSTEPS_AUTO = 0
+# Energy solvers
+LBMFVM_ENERGY_FV, LBMFVM_ENERGY_LBM_D2Q5 = 0, 1
+ENERGY = {"fv": LBMFVM_ENERGY_FV, "lbm": LBMFVM_ENERGY_LBM_D2Q5}
+# Box-wall treatments
+LBMFVM_WALL_NEE, LBMFVM_WALL_FD = 0, 1
+WALLS = {"nee": LBMFVM_WALL_NEE, "fd": LBMFVM_WALL_FD}
 
 # Every entry point the header declares (checked by the test-suite).
 EXPORTS = (
@@ -65,7 +72,9 @@ class lbmfvm_opts_t(ctypes.Structure):
     _fields_ = [("store", ctypes.c_int32), ("tile_y", ctypes.c_int32), ("kernel", ctypes.c_int32),
                 ("tma_config", ctypes.c_int32), ("t_ref", ctypes.c_double),
                 ("cuda_stream", ctypes.c_void_p), ("workspace", ctypes.c_void_p),
-                ("workspace_bytes", ctypes.c_size_t), ("fv_scheme", ctypes.c_int32), ("fv_substeps", ctypes.c_int32)]
+                ("workspace_bytes", ctypes.c_size_t), ("fv_scheme", ctypes.c_int32), ("fv_substeps", ctypes.c_int32),
+                ("energy", ctypes.c_int32), ("wall_bc", ctypes.c_int32), ("fv_grid", ctypes.c_int32),
+                ("fv_every", ctypes.c_int32)]
 
 
 class lbmfvm_checkpoint_header_t(ctypes.Structure):
@@ -76,7 +85,8 @@ class lbmfvm_checkpoint_header_t(ctypes.Structure):
                 ("alpha", ctypes.c_double), ("gbeta", ctypes.c_double), ("t_ref", ctypes.c_double),
                 ("force", ctypes.c_double * 2), ("payload_bytes", ctypes.c_uint64), ("code_crc", ctypes.c_uint32),
                 ("payload_crc", ctypes.c_uint32), ("fv_scheme", ctypes.c_int32), ("fv_substeps", ctypes.c_int32),
-                ("pad", ctypes.c_uint8 * 84), ("header_crc", ctypes.c_uint32)]
+                ("energy", ctypes.c_int32), ("wall_bc", ctypes.c_int32), ("pad", ctypes.c_uint8 * 76),
+                ("header_crc", ctypes.c_uint32)]
 
 
 class LbmfvmError(RuntimeError):
@@ -270,7 +280,8 @@ def lbmfvm_fv_info(h):
 
 
 def _tma_config(cfg):
-    return LBMFVM_TMA_AUTOTUNE if cfg == "auto" else int(cfg)
+    return {"auto": LBMFVM_TMA_AUTOTUNE, "default": LBMFVM_TMA_DEFAULT}.get(cfg, cfg) if isinstance(cfg, str) \
+        else int(cfg)
 
 
 def lbmfvm_copy_state(dst, src):
@@ -308,7 +319,7 @@ def lbmfvm_checkpoint_info(path) -> dict:
     return dict(nx=hd.nx, ny=hd.ny, store=hd.store, steps=hd.steps, bc=tuple(hd.bc), t_wall=tuple(hd.t_wall),
                 u_lid=hd.u_lid, tau=hd.tau, alpha=hd.alpha, gbeta=hd.gbeta, t_ref=hd.t_ref, force=tuple(hd.force),
                 payload_bytes=hd.payload_bytes, code_crc=hd.code_crc, payload_crc=hd.payload_crc,
-                fv_scheme=hd.fv_scheme, fv_substeps=max(1, hd.fv_substeps))
+                fv_scheme=hd.fv_scheme, fv_substeps=max(1, hd.fv_substeps), energy=hd.energy, wall_bc=hd.wall_bc)
 
 
 def lbmfvm_destroy(h):
@@ -333,7 +344,8 @@ class Cavity:
                  mask=None, store="f32", bc=(LBMFVM_BC_DIRICHLET, LBMFVM_BC_DIRICHLET, LBMFVM_BC_ADIABATIC,
                                              LBMFVM_BC_ADIABATIC),
                  t_wall=(1.0, 0.0, 0.0, 0.0), u_lid=0.0, t_init=0.5, t_ref=None, tile_y=0, kernel="auto",
-                 tma_config=1, fv_scheme="central", fv_substeps=1, device=None):
+                 tma_config="default", fv_scheme="central", fv_substeps=1, energy="fv", wall_bc="nee", fv_grid=1,
+                 fv_every=1, device=None):
         import torch
 
         self.nx, self.ny = int(nx), int(ny)
@@ -346,6 +358,10 @@ class Cavity:
         self.opts.t_ref = math.nan if t_ref is None else float(t_ref)
         self.opts.fv_scheme = FV_SCHEMES[fv_scheme] if isinstance(fv_scheme, str) else int(fv_scheme)
         self.opts.fv_substeps = int(fv_substeps)
+        self.opts.energy = ENERGY[energy] if isinstance(energy, str) else int(energy)
+        self.opts.wall_bc = WALLS[wall_bc] if isinstance(wall_bc, str) else int(wall_bc)
+        self.opts.fv_grid = int(fv_grid)
+        self.opts.fv_every = int(fv_every)
         dev = torch.device("cuda" if device is None else device)
         self.device = dev
         nbytes = lbmfvm_workspace_bytes(self.grid, self.opts)

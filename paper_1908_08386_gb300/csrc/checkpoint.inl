@@ -35,11 +35,12 @@ uint32_t crc32_update(uint32_t crc, const void *data, size_t n) {
 
 // Payload bytes of a checkpoint of an nx x ny grid in storage prec (0 for an
 // unknown precision).
-uint64_t ckpt_payload_bytes(int nx, int ny, int prec) {
+uint64_t ckpt_payload_bytes(int nx, int ny, int prec, int energy) {
     const uint64_t n = (uint64_t)nx * (uint64_t)ny;
     const uint64_t ss = store_size(prec), ts = temp_size(prec);
-    if (ss == 0) return 0;
-    return 2 * 9 * n * ss + n * ts + 2 * n * sizeof(double);
+    if (ss == 0 || (energy != LBMFVM_ENERGY_FV && energy != LBMFVM_ENERGY_LBM_D2Q5)) return 0;
+    const uint64_t g = energy == LBMFVM_ENERGY_LBM_D2Q5 ? 2 * 5 * n * ss : 0;
+    return 2 * 9 * n * ss + n * ts + 2 * n * sizeof(double) + g;
 }
 
 struct FileCloser {
@@ -71,7 +72,7 @@ int read_checkpoint(const char *path, lbmfvm_checkpoint_header_t *hd, std::vecto
         snprintf(why, why_len, "checkpoint %s: header CRC mismatch", path);
         return LBMFVM_ERR_IO;
     }
-    const uint64_t want = ckpt_payload_bytes(hd->nx, hd->ny, hd->store);
+    const uint64_t want = ckpt_payload_bytes(hd->nx, hd->ny, hd->store, hd->energy);
     if (hd->nx < 3 || hd->ny < 3 || (int64_t)hd->nx * hd->ny > (int64_t(1) << 30) || want == 0 ||
         hd->payload_bytes != want) {
         snprintf(why, why_len, "checkpoint %s: payload size does not match its %d x %d grid", path, hd->nx, hd->ny);
@@ -126,9 +127,10 @@ int lbmfvm_checkpoint_info(const char *path, lbmfvm_checkpoint_header_t *header)
 int lbmfvm_save(lbmfvm_t *h, const char *path) {
     if (!h || !path) return fail_thread(LBMFVM_ERR_ARG, "handle or path is NULL");
     if (!h->atlas_cavs.empty()) return fail(h, LBMFVM_ERR_ARG, "checkpoints hold single-cavity handles");
+    if (h->grid2) return fail(h, LBMFVM_ERR_ARG, "checkpoints hold handles of grid setting 1");
     const int nx = h->grid.nx, ny = h->grid.ny;
     const size_t n = (size_t)nx * ny, ss = store_size(h->prec), ts = temp_size(h->prec);
-    std::vector<uint8_t> payload(ckpt_payload_bytes(nx, ny, h->prec));
+    std::vector<uint8_t> payload(ckpt_payload_bytes(nx, ny, h->prec, h->energy));
     if (int r = join_in(h)) return r;
     uint8_t *dst = payload.data();
     // f*^n, then f*^(n-1): nine planes of ny rows each, one 2-D copy per buffer
@@ -142,6 +144,14 @@ int lbmfvm_save(lbmfvm_t *h, const char *path) {
                             cudaMemcpyDeviceToHost, h->s));
     dst += n * ts;
     CU(h, cudaMemcpyAsync(dst, h->base + h->L.snap, 2 * n * sizeof(double), cudaMemcpyDeviceToHost, h->s));
+    dst += 2 * n * sizeof(double);
+    // energy populations g*^n, then g*^(n-1)
+    for (int b = 0; b < 2 && h->energy == LBMFVM_ENERGY_LBM_D2Q5; b++) {
+        const int buf = b == 0 ? h->parity : h->parity ^ 1;
+        CU(h, cudaMemcpy2DAsync(dst, nx * ss, h->base + h->L.g[buf], (size_t)h->L.pitch * ss, nx * ss, 5 * (size_t)ny,
+                                cudaMemcpyDeviceToHost, h->s));
+        dst += 5 * n * ss;
+    }
     CU(h, cudaStreamSynchronize(h->s));
     if (int r = check_device_status(h)) return r;
 
@@ -169,6 +179,8 @@ int lbmfvm_save(lbmfvm_t *h, const char *path) {
     hd.code_crc = h->code_crc;
     hd.fv_scheme = h->fv_quick ? LBMFVM_FV_QUICK : LBMFVM_FV_CENTRAL;
     hd.fv_substeps = h->fv_sub;
+    hd.energy = h->energy;
+    hd.wall_bc = h->wall_bc;
     hd.payload_crc = crc32_update(0, payload.data(), payload.size());
     hd.header_crc = crc32_update(0, &hd, offsetof(lbmfvm_checkpoint_header_t, header_crc));
 
@@ -193,6 +205,7 @@ int lbmfvm_save(lbmfvm_t *h, const char *path) {
 int lbmfvm_load(lbmfvm_t *h, const char *path) {
     if (!h || !path) return fail_thread(LBMFVM_ERR_ARG, "handle or path is NULL");
     if (!h->atlas_cavs.empty()) return fail(h, LBMFVM_ERR_ARG, "checkpoints hold single-cavity handles");
+    if (h->grid2) return fail(h, LBMFVM_ERR_ARG, "checkpoints hold handles of grid setting 1");
     lbmfvm_checkpoint_header_t hd;
     std::vector<uint8_t> payload;
     char why[512];
@@ -209,6 +222,8 @@ int lbmfvm_load(lbmfvm_t *h, const char *path) {
     else if (hd.fv_scheme != (h->fv_quick ? LBMFVM_FV_QUICK : LBMFVM_FV_CENTRAL) ||
              (hd.fv_substeps < 1 ? 1 : hd.fv_substeps) != h->fv_sub)
         diff = "energy-update scheme or sub-steps";
+    else if (hd.energy != h->energy) diff = "energy solver";
+    else if (hd.wall_bc != h->wall_bc) diff = "wall treatment";
     for (int s = 0; s < 4 && !diff; s++)
         if (hd.bc[s] != h->grid.bc[s] || hd.t_wall[s] != h->grid.t_wall[s]) diff = "boundary conditions";
     if (diff) return fail(h, LBMFVM_ERR_ARG, "checkpoint %s was saved with other %s", path, diff);
@@ -227,6 +242,12 @@ int lbmfvm_load(lbmfvm_t *h, const char *path) {
                             cudaMemcpyHostToDevice, h->s));
     src += n * ts;
     CU(h, cudaMemcpyAsync(h->base + h->L.snap, src, 2 * n * sizeof(double), cudaMemcpyHostToDevice, h->s));
+    src += 2 * n * sizeof(double);
+    for (int b = 0; b < 2 && h->energy == LBMFVM_ENERGY_LBM_D2Q5; b++) {
+        CU(h, cudaMemcpy2DAsync(h->base + h->L.g[b], (size_t)h->L.pitch * ss, src, nx * ss, nx * ss, 5 * (size_t)ny,
+                                cudaMemcpyHostToDevice, h->s));
+        src += 5 * n * ss;
+    }
     if (int r = clear_tile_counters(h)) return r;
     CU(h, cudaStreamSynchronize(h->s));
     h->parity = 0;

@@ -168,6 +168,8 @@ struct StepArgs {
     C wall_u[4], wall_v[4];  // velocity of box walls per side W, E, S, N
     int *err;                // device status word (bounded waits that ran out)
     int stall;               // test hook: block 0 skips its first staged load
+    int wall_fd;             // generic kernel: finite-difference velocity-gradient box walls
+    C fd_coef;               // their 3 tau (tau w_i / c_s^2 = 3 tau w_i)
 };
 
 // One cavity of the TMA path: its rectangle in the (possibly multi-cavity)
@@ -397,9 +399,81 @@ __device__ __forceinline__ void gather(const S *__restrict__ fin, long long plan
     g[8] = ld(rp + 8 * plane + xm);
 }
 
+// Velocity of node (x, y) at the new step for the finite-difference wall
+// gradients: wall nodes move with their wall, fluid nodes from their pulled
+// populations, inert nodes rest; positions wrap across periodic sides.
+template <class S, class C>
+__device__ __forceinline__ void fd_velocity(const StepArgs<S> &a, const S *__restrict__ fin, int x, int y, C &u,
+                                            C &v) {
+    x = x < 0 ? x + a.nx : (x >= a.nx ? x - a.nx : x);
+    y = y < 0 ? y + a.ny : (y >= a.ny ? y - a.ny : y);
+    const uint8_t c = decode(a.code[(long long)y * a.pitch + x]);
+    u = v = C(0);
+    if ((c & 3) == KIND_WALL) {
+        wall_velocity<S>(a, x, y, c, u, v);
+    } else if ((c & 3) == KIND_FLUID) {
+        C g[9], d;
+        gather<S, C>(fin, a.plane, a.pitch, a.nx, a.ny, x, y, g);
+        moments<C>(g, d, u, v);
+    }
+}
+
+// d(u, v)/d(axis) at (x, y): second-order one-sided into the domain at a
+// walled box side, centred elsewhere.
+template <class S, class C>
+__device__ __forceinline__ void fd_gradient(const StepArgs<S> &a, const S *__restrict__ fin, int x, int y, int axis,
+                                            C &du, C &dv) {
+    const int dx = axis == 0, dy = axis == 1;
+    const bool lo = axis == 0 ? (!a.perx && x == 0) : (!a.pery && y == 0);
+    const bool hi = axis == 0 ? (!a.perx && x == a.nx - 1) : (!a.pery && y == a.ny - 1);
+    C u0, v0, u1, v1, u2, v2;
+    if (lo || hi) {
+        const int sg = lo ? 1 : -1;
+        fd_velocity<S, C>(a, fin, x, y, u0, v0);
+        fd_velocity<S, C>(a, fin, x + sg * dx, y + sg * dy, u1, v1);
+        fd_velocity<S, C>(a, fin, x + 2 * sg * dx, y + 2 * sg * dy, u2, v2);
+        const C h = C(0.5) * C(sg);
+        du = h * (C(-3) * u0 + C(4) * u1 - u2);
+        dv = h * (C(-3) * v0 + C(4) * v1 - v2);
+    } else {
+        fd_velocity<S, C>(a, fin, x + dx, y + dy, u1, v1);
+        fd_velocity<S, C>(a, fin, x - dx, y - dy, u2, v2);
+        du = C(0.5) * (u1 - u2);
+        dv = C(0.5) * (v1 - v2);
+    }
+}
+
+// Finite-difference velocity-gradient wall (Section 3, Eqs. 67, 69-72) on
+// shifted storage: g_b = w (drho_f + rho_f P(u_w) - 3 tau rho_f Q : S), with
+// the partner's density (Eq. 96), the wall velocity, S from the new velocity
+// field and the normal strain from continuity off the corners (Eq. 72).
+// On entry drho holds the partner's density deviation.
+template <class S, class C>
+__device__ __forceinline__ void fd_wall(const StepArgs<S> &a, const S *__restrict__ fin, int x, int y,
+                                        uint8_t code, C g[9], C &drho, C &ux, C &uy) {
+    C uw, vw, dudx, dvdx, dudy, dvdy;
+    wall_velocity<S>(a, x, y, code, uw, vw);
+    fd_gradient<S, C>(a, fin, x, y, 0, dudx, dvdx);
+    fd_gradient<S, C>(a, fin, x, y, 1, dudy, dvdy);
+    const bool vert = !a.perx && (x == 0 || x == a.nx - 1), hor = !a.pery && (y == 0 || y == a.ny - 1);
+    if (vert && !hor) dudx = -dvdy;
+    if (hor && !vert) dvdy = -dudx;
+    const C sxx = dudx, syy = dvdy, sxy = C(0.5) * (dudy + dvdx);
+    const C rho = C(1) + drho, usq = uw * uw + vw * vw;
+    const C third = C(1.0 / 3.0);
+#pragma unroll
+    for (int q = 0; q < 9; q++) {
+        const C ex = C(cx(q)), ey = C(cy(q));
+        const C qs = (ex * ex - third) * sxx + C(2) * ex * ey * sxy + (ey * ey - third) * syy;
+        g[q] = wq<C>(q) * (drho + rho * eq_poly<C>(q, uw, vw, usq) - a.fd_coef * rho * qs);
+    }
+    moments<C>(g, drho, ux, uy);
+}
+
 // Pre-collision populations and moments of node (x, y) at the new step:
 // streamed populations for fluid nodes, non-equilibrium extrapolation from
-// the partner for wall nodes, nothing for inert nodes.
+// the partner for wall nodes (or the finite-difference velocity-gradient
+// scheme on box walls), nothing for inert nodes.
 template <class S, class C>
 __device__ __forceinline__ void node_state(const StepArgs<S> &a, const S *__restrict__ fin, int x,
                                            int y, uint8_t code, C g[9], C &drho, C &ux, C &uy) {
@@ -422,9 +496,13 @@ __device__ __forceinline__ void node_state(const StepArgs<S> &a, const S *__rest
     gather<S, C>(fin, a.plane, a.pitch, a.nx, a.ny, sx, sy, g);
     moments<C>(g, drho, ux, uy);
     if (kind == KIND_WALL) {
-        C uw, vw;
-        wall_velocity<S>(a, x, y, code, uw, vw);
-        nee<C>(g, drho, ux, uy, uw, vw);
+        if (a.wall_fd && (code >> 6) != TH_OBSTACLE) {
+            fd_wall<S, C>(a, fin, x, y, code, g, drho, ux, uy);
+        } else {
+            C uw, vw;
+            wall_velocity<S>(a, x, y, code, uw, vw);
+            nee<C>(g, drho, ux, uy, uw, vw);
+        }
     }
 }
 
@@ -605,9 +683,13 @@ __device__ __forceinline__ void load_2d(void *dst, const CUtensorMap *map, uint6
 }  // namespace tma
 
 // Tile geometry of the TMA tile path.  A tile is TW x TH output nodes at
-// (x0, y0), NPT of them per thread; the staged input box reaches 3 nodes
-// beyond it in y and XOFF (>= 4, one 16-byte TMA granule) in x, enough for the
-// pull stencil of the one-node ring and of any wall partner on that ring.
+// (x0, y0), NPT of them per thread; the staged input box reaches FHALO (2 or
+// 3) nodes beyond it in y and XOFF (>= 4, one 16-byte TMA granule) in x.  Two
+// rows are enough for the pull stencil of the one-node ring's fluid nodes and
+// of the tile's wall partners (a wall node on the ring needs no pull: its
+// velocity after the extrapolation of Eq. 94 is the wall's); a third row
+// makes the boxes of vertically adjacent tiles overlap by six rows, which
+// measured faster on grids larger than the L2.
 // The temperature box reaches THALO rows beyond the tile (1 for central face
 // values, 2 for QUICK's far upstream node) and 4 columns.
 // Once a tile's moments are taken, its staged populations are dead and the
@@ -618,7 +700,8 @@ __device__ __forceinline__ void load_2d(void *dst, const CUtensorMap *map, uint6
 // the THREADS compute threads all carry the same load into each tile's block
 // barrier; with 0 the first compute threads also take the ring and thread 0
 // issues.
-template <class S, int TW_, int TH_, int STAGES_, int THREADS_, int MINB_ = 1, int THALO_ = 1, int RT_ = 0>
+template <class S, int TW_, int TH_, int STAGES_, int THREADS_, int MINB_ = 1, int THALO_ = 1, int RT_ = 0,
+          int FHALO_ = 2>
 struct TmaTile {
     using TC = typename Compute<S>::type;  // temperature and ring element
     static constexpr int TW = TW_, TH = TH_, STAGES = STAGES_, THREADS = THREADS_;
@@ -628,7 +711,8 @@ struct TmaTile {
     static constexpr int THALO = THALO_;
     static constexpr int NPT = TW * TH / THREADS;  // own nodes per thread
     static constexpr int XOFF = 16 / (int)sizeof(S) < 4 ? 4 : 16 / (int)sizeof(S);
-    static constexpr int FW = TW + 2 * XOFF, FH = TH + 6;  // population box
+    static constexpr int FHALO = FHALO_;
+    static constexpr int FW = TW + 2 * XOFF, FH = TH + 2 * FHALO;  // population box
     static constexpr int TWD = TW + 8, THT = TH + 2 * THALO;  // temperature box (x0-4, y0-THALO)
     static constexpr int CWD = TW + 32, CHT = TH + 2;      // code box (x0-16, y0-1), codes then face flags
     static constexpr int RW = TW + 2, RH = TH + 2;         // tile + ring
@@ -661,9 +745,10 @@ struct TmaTile {
     static_assert(RT_ % 32 == 0 && THREADS % 32 == 0, "whole warps");
     static_assert(STAGES >= 2, "the pipeline needs two stages");
     static_assert(THALO == 1 || THALO == 2, "temperature halo of one or two rows");
+    static_assert(FHALO == 2 || FHALO == 3, "population halo of two or three rows");
     // the same tile with a temperature box of h halo rows
     template <int h>
-    using WithTHalo = TmaTile<S, TW_, TH_, STAGES_, THREADS_, MINB_, h, RT_>;
+    using WithTHalo = TmaTile<S, TW_, TH_, STAGES_, THREADS_, MINB_, h, RT_, FHALO_>;
 };
 
 // Energy update of a launch of the TMA kernel: the central face values of
@@ -677,25 +762,29 @@ enum : int { FV_CENTRAL = 0, FV_QUICK = 1, FV_GIVEN = 2 };
 // 227 KB of shared memory allow for 32-bit storage; 16-bit storage halves the
 // population box and takes one more stage where it fits.
 template <class S, int CFG> struct TmaConfig;
-template <class S> struct TmaConfig<S, 0> { using G = TmaTile<S, 64, 16, 3, 1024>; };
-template <class S> struct TmaConfig<S, 1> { using G = TmaTile<S, 64, 16, 3, 512>; };
-template <class S> struct TmaConfig<S, 2> { using G = TmaTile<S, 64, 8, sizeof(S) == 4 ? 2 : 3, 512, 2>; };
-template <class S> struct TmaConfig<S, 3> { using G = TmaTile<S, 128, 8, sizeof(S) == 4 ? 2 : 3, 1024>; };
-// 64 x 16 with four ring warps (which also issue the copies)
-template <class S> struct TmaConfig<S, 4> { using G = TmaTile<S, 64, 16, 3, 512, 1, 1, 128>; };
+template <class S> struct TmaConfig<S, 0> { using G = TmaTile<S, 64, 16, 3, 1024, 1, 1, 0, 3>; };
+template <class S> struct TmaConfig<S, 1> { using G = TmaTile<S, 64, 16, 3, 512, 1, 1, 0, 3>; };
+template <class S> struct TmaConfig<S, 2> { using G = TmaTile<S, 64, 8, sizeof(S) == 4 ? 2 : 3, 512, 2, 1, 0, 3>; };
+template <class S> struct TmaConfig<S, 3> { using G = TmaTile<S, 128, 8, sizeof(S) == 4 ? 2 : 3, 1024, 1, 1, 0, 3>; };
+// 64 x 16 with four ring warps (which also issue the copies): two halo rows
+// (the faster on grids inside the L2), three rows (the faster beyond it)
+template <class S> struct TmaConfig<S, 4> { using G = TmaTile<S, 64, 16, 3, 512, 1, 1, 128, 2>; };
+template <class S> struct TmaConfig<S, 5> { using G = TmaTile<S, 64, 16, 3, 512, 1, 1, 128, 3>; };
 // 64-bit storage: a 32 x 8 tile stages 43 KB, a 64 x 8 tile 78 KB.
 template <> struct TmaConfig<double, 0> { using G = TmaTile<double, 64, 8, 2, 256>; };
 template <> struct TmaConfig<double, 1> { using G = TmaTile<double, 32, 8, 3, 256>; };
 template <> struct TmaConfig<double, 2> { using G = TmaTile<double, 32, 16, 2, 512>; };
 template <> struct TmaConfig<double, 3> { using G = TmaTile<double, 32, 8, 2, 256, 2>; };
 template <> struct TmaConfig<double, 4> { using G = TmaTile<double, 32, 8, 3, 256, 1, 1, 64>; };
+template <> struct TmaConfig<double, 5> { using G = TmaTile<double, 32, 8, 3, 256, 1, 1, 64, 3>; };
 // double-single storage: 8-byte elements like FP64, the same shapes
 template <> struct TmaConfig<dsf, 0> { using G = TmaTile<dsf, 64, 8, 2, 256>; };
 template <> struct TmaConfig<dsf, 1> { using G = TmaTile<dsf, 32, 8, 3, 256>; };
 template <> struct TmaConfig<dsf, 2> { using G = TmaTile<dsf, 32, 16, 2, 512>; };
 template <> struct TmaConfig<dsf, 3> { using G = TmaTile<dsf, 32, 8, 2, 256, 2>; };
 template <> struct TmaConfig<dsf, 4> { using G = TmaTile<dsf, 32, 8, 3, 256, 1, 1, 64>; };
-constexpr int kTmaConfigs = 5;
+template <> struct TmaConfig<dsf, 5> { using G = TmaTile<dsf, 32, 8, 3, 256, 1, 1, 64, 3>; };
+constexpr int kTmaConfigs = 6;
 // QUICK face values and the sub-step path use shape 1 (FV_QUICK with a
 // temperature box of two halo rows).
 constexpr int kTmaConfigFv = 1;
@@ -791,7 +880,7 @@ __global__ void __launch_bounds__(G::BLOCK, G::MINB)
         unsigned char *stg = stage(k);
         tma::mbar_arrive_expect_tx(&bars[s], G::TX_BYTES + (uint32_t)sizeof(TileHeader));
         tma::load_bytes(&hdrs[s], tiles + t, sizeof(TileHeader), &bars[s]);
-        tma::load_3d(stg + G::F_OFF, &map_f, &bars[s], x0 - XOFF, y0 - 3, 0);
+        tma::load_3d(stg + G::F_OFF, &map_f, &bars[s], x0 - XOFF, y0 - G::FHALO, 0);
         tma::load_2d(stg + G::T_OFF, &map_T, &bars[s], x0 - 4, y0 - G::THALO);
         tma::load_3d(stg + G::C_OFF, &map_c, &bars[s], x0 - 16, y0 - 1, 0);
     };
@@ -872,13 +961,29 @@ __global__ void __launch_bounds__(G::BLOCK, G::MINB)
         const uint8_t *CF = CC + G::C_PLANE;  // face flags
         C *RU = reinterpret_cast<C *>(smem + G::RING_OFF + (k & 1) * G::RING_BYTES), *RV = RU + G::RH * RW;
         // staged-box index of node (lx, ly) relative to the tile origin
-        auto fidx = [&](int lx, int ly) { return (ly + 3) * FW + (lx + XOFF); };
+        auto fidx = [&](int lx, int ly) { return (ly + G::FHALO) * FW + (lx + XOFF); };
         auto tidx = [&](int lx, int ly) { return (ly + G::THALO) * G::TWD + (lx + 4); };
         auto cidx = [&](int lx, int ly) { return (ly + 1) * G::CWD + (lx + 16); };
         auto pull = [&](int lx, int ly, C g[9]) {
             const S *p = F + fidx(lx, ly);
 #pragma unroll
             for (int q = 0; q < 9; q++) g[q] = ld(p + q * (FH * FW) - cy(q) * FW - cx(q));
+        };
+        // velocity of wall node (lx, ly): 0 on obstacle surfaces, the side's
+        // on box walls (vertical sides own the corners)
+        auto wall_vel = [&](int lx, int ly, uint8_t c, C &uw, C &vw) {
+            uw = vw = C(0);
+            if ((c >> 6) != TH_OBSTACLE) {
+                const int cx = ox + lx, cy = oy + ly;
+                const int side = cx == 0 ? 0 : (cx == cv_nx - 1 ? 1 : (cy == 0 ? 2 : 3));
+                if constexpr (std::is_same<C, double>::value || std::is_same<C, dsf>::value) {
+                    uw = C(cvp->wall_u[side]);
+                    vw = C(cvp->wall_v[side]);
+                } else {
+                    uw = cvp->wall_uf[side];
+                    vw = cvp->wall_vf[side];
+                }
+            }
         };
         auto state = [&](int lx, int ly, uint8_t c, C g[9], C &drho, C &ux, C &uy) {
             const int kind = c & 3;
@@ -889,19 +994,8 @@ __global__ void __launch_bounds__(G::BLOCK, G::MINB)
                 const int d = partner_dir(c);
                 pull(lx + cx_rt(d), ly + cy_rt(d), g);
                 moments<C>(g, drho, ux, uy);
-                C uw = C(0), vw = C(0);
-                if ((c >> 6) != TH_OBSTACLE) {
-                    // box walls: vertical sides own the corners
-                    const int cx = ox + lx, cy = oy + ly;
-                    const int side = cx == 0 ? 0 : (cx == cv_nx - 1 ? 1 : (cy == 0 ? 2 : 3));
-                    if constexpr (std::is_same<C, double>::value || std::is_same<C, dsf>::value) {
-                        uw = C(cvp->wall_u[side]);
-                        vw = C(cvp->wall_v[side]);
-                    } else {
-                        uw = cvp->wall_uf[side];
-                        vw = cvp->wall_vf[side];
-                    }
-                }
+                C uw, vw;
+                wall_vel(lx, ly, c, uw, vw);
                 nee<C>(g, drho, ux, uy, uw, vw);
             } else {
 #pragma unroll
@@ -938,8 +1032,14 @@ __global__ void __launch_bounds__(G::BLOCK, G::MINB)
                 else if (hr < 2 * RW) { rx = hr - RW; ry = TH + 1; }
                 else { const int h = hr - 2 * RW; rx = (h & 1) ? RW - 1 : 0; ry = 1 + (h >> 1); }
                 const uint8_t c = decode(CC[cidx(rx - 1, ry - 1)]);
-                C hg[9], hd, hu, hv;
-                state(rx - 1, ry - 1, c, hg, hd, hu, hv);
+                C hu = C(0), hv = C(0);
+                if ((c & 3) == KIND_FLUID) {
+                    C hg[9], hd;
+                    state(rx - 1, ry - 1, c, hg, hd, hu, hv);
+                } else if ((c & 3) == KIND_WALL) {
+                    // the extrapolated wall node moves with the wall (Eq. 94)
+                    wall_vel(rx - 1, ry - 1, c, hu, hv);
+                }
                 RU[ry * RW + rx] = hu;
                 RV[ry * RW + rx] = hv;
             }
@@ -1203,6 +1303,253 @@ __global__ void __launch_bounds__(256)
             Tout[k] = Tn;
         }
     }
+}
+
+// ---------------------------------------------------------------------------
+// D2Q5 thermal lattice Boltzmann energy solver (Section 2.4), the paper's
+// pure-LBM comparison: energy populations g_i (rest, E, N, W, S: the first
+// five D2Q9 directions) relax toward g_eq = T w_i (1 + 3 e_i.u) (Eqs. 19, 21;
+// w = 1/3, 1/6 of Eq. 22) with omega_T = 1/tau_T, tau_T = 3 alpha + 1/2
+// (Eq. 20), stream like f and give T = sum g (Eq. 23).  Wall nodes take
+// g_b = g_eq(T_b, u_b) + g(x_f) - g_eq(T_f, u_f) (Eq. 95) with T_b the wall
+// temperature on Dirichlet sides (held in the temperature plane) and T_f on
+// adiabatic sides and obstacle surfaces.  State between launches: the
+// post-collision f* and g*; the temperature plane receives T of the new step
+// for the field, residual and Nusselt kernels.  One node per thread, pulls
+// from global memory (every neighbour lies one node away); no halo exchange
+// is needed because the energy update is local.
+// ---------------------------------------------------------------------------
+
+// Eq. 22: 1/3 for the rest population, 1/6 for the axis ones.
+template <class C>
+__device__ __forceinline__ C w5(int q) {
+    return q == 0 ? C(1) / C(3) : C(1) / C(6);
+}
+template <>
+__device__ __forceinline__ dsf w5<dsf>(int q) {
+    return q == 0 ? dsf(1.0 / 3.0) : dsf(1.0 / 6.0);
+}
+
+// The energy populations are stored shifted, s_i = g_i - w_i T_0, with T_0
+// the mean of the two wall temperatures (the way f is stored as f - w), and
+// the collision works on the shifted values: near T_0 they are small, so their
+// rounding is too.  With dT = T - T_0, the shifted equilibrium (Eq. 21 with
+// c_s^2 = 1/3) is
+//   g_eq,i - w_i T_0 = w_i dT + 3 w_i T e_i.u,
+// and for the axis directions 3 w_i T = T/2 exactly.  The rest direction is
+// taken as dT minus the four others' dT/6 parts, so that the shifted
+// equilibria sum to dT without the bias of a rounded weight.
+template <class C>
+__device__ __forceinline__ void geq5_shifted(C T, C dT, C ux, C uy, C e[5]) {
+    const C a = dT * w5<C>(1), t = C(0.5) * T;
+    e[0] = dT - C(4) * a;
+    e[1] = a + t * ux;
+    e[3] = a - t * ux;
+    e[2] = a + t * uy;
+    e[4] = a - t * uy;
+}
+
+template <class S>
+struct Lbm5Args {
+    using C = typename Compute<S>::type;
+    StepArgs<S> a;     // populations f, temperature plane, codes, lattice parameters
+    const S *gin;      // shifted post-collision g of the previous step [5][ny][pitch]
+    S *gout;
+    C omega_T;         // 1 / tau_T
+    C T0;              // the shift of the stored populations
+};
+
+template <class S>
+__global__ void __launch_bounds__(256) step_lbm5_kernel(const Lbm5Args<S> p) {
+    using C = typename Compute<S>::type;
+    const StepArgs<S> &a = p.a;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= a.nx || y >= a.ny) return;
+    const long long k = (long long)y * a.pitch + x;
+    const uint8_t c = decode(a.code[k]);
+    const int kind = c & 3;
+    S *fo = a.fout + k;
+    S *go = p.gout + k;
+    if (kind == KIND_SOLID) {
+#pragma unroll
+        for (int q = 0; q < 9; q++) st(fo + q * a.plane, C(0));
+#pragma unroll
+        for (int q = 0; q < 5; q++) st(go + q * a.plane, C(0));
+        a.Tout[k] = a.Tin[k];
+        return;
+    }
+    // the node itself (fluid) or its partner (wall) receives the pull
+    int sx = x, sy = y;
+    if (kind == KIND_WALL) {
+        const int d = partner_dir(c);
+        sx = x + cx_rt(d);
+        sy = y + cy_rt(d);
+        sx = sx < 0 ? sx + a.nx : (sx >= a.nx ? sx - a.nx : sx);
+        sy = sy < 0 ? sy + a.ny : (sy >= a.ny ? sy - a.ny : sy);
+    }
+    C g[9], h[5], drho, ux, uy;
+    gather<S, C>(a.fin, a.plane, a.pitch, a.nx, a.ny, sx, sy, g);
+    {
+        const int xm = sx > 0 ? sx - 1 : a.nx - 1, xp = sx < a.nx - 1 ? sx + 1 : 0;
+        const int ym = sy > 0 ? sy - 1 : a.ny - 1, yp = sy < a.ny - 1 ? sy + 1 : 0;
+        const S *gi = p.gin;
+        h[0] = ld(gi + (long long)sy * a.pitch + sx);
+        h[1] = ld(gi + a.plane + (long long)sy * a.pitch + xm);
+        h[2] = ld(gi + 2 * a.plane + (long long)ym * a.pitch + sx);
+        h[3] = ld(gi + 3 * a.plane + (long long)sy * a.pitch + xp);
+        h[4] = ld(gi + 4 * a.plane + (long long)yp * a.pitch + sx);
+    }
+    moments<C>(g, drho, ux, uy);
+    C dT = (((h[0] + h[1]) + (h[2] + h[3])) + h[4]);  // Eq. 23 on shifted populations
+    if (kind == KIND_WALL) {
+        C uw, vw;
+        wall_velocity<S>(a, x, y, c, uw, vw);
+        const C uf = ux, vf = uy, dTf = dT;
+        nee<C>(g, drho, ux, uy, uw, vw);
+        // Eq. 95 with T_b the wall temperature (Dirichlet) or T_f
+        const C dTb = (c >> 6) == TH_DIRICHLET ? a.Tin[k] - p.T0 : dTf;
+        C eb[5], ef[5];
+        geq5_shifted<C>(p.T0 + dTb, dTb, uw, vw, eb);
+        geq5_shifted<C>(p.T0 + dTf, dTf, uf, vf, ef);
+#pragma unroll
+        for (int q = 0; q < 5; q++) h[q] = eb[q] + h[q] - ef[q];
+        dT = (((h[0] + h[1]) + (h[2] + h[3])) + h[4]);
+    }
+    const C T = p.T0 + dT;
+    a.Tout[k] = T;
+    const C Gy = a.fy + a.gbeta * (T - a.t_ref);
+    const long long plane = a.plane;
+    collide<C>(g, drho, ux, uy, a.omega, a.fx, Gy, [&](int q, C v) { st(fo + q * plane, v); });
+    // Eq. 19 on shifted populations: s* = s - (s - (g_eq - w T_0)) / tau_T
+    C e[5];
+    geq5_shifted<C>(T, dT, ux, uy, e);
+#pragma unroll
+    for (int q = 0; q < 5; q++) st(go + q * plane, h[q] - p.omega_T * (h[q] - e[q]));
+}
+
+// Energy populations of the initial state: g^0 = g_eq(T^0, u^0) (Eq. 21),
+// stored shifted by w_i T_0, in both buffers (at equilibrium the collision
+// leaves g unchanged); u^0 from the initial populations f0 (stored as f - w).
+template <class S>
+__global__ void init_lbm5_kernel(const StepArgs<S> a, const S *f0, S *g0, S *g1, typename Compute<S>::type T0) {
+    using C = typename Compute<S>::type;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= a.nx || y >= a.ny) return;
+    const long long k = (long long)y * a.pitch + x;
+    const bool inert = (decode(a.code[k]) & 3) == KIND_SOLID;
+    C g[9], drho = C(0), ux = C(0), uy = C(0);
+    if (!inert) {
+#pragma unroll
+        for (int q = 0; q < 9; q++) g[q] = ld(f0 + k + q * a.plane);
+        moments<C>(g, drho, ux, uy);
+    }
+    C e[5];
+    const C T = a.Tin[k];
+    geq5_shifted<C>(T, T - T0, ux, uy, e);
+#pragma unroll
+    for (int q = 0; q < 5; q++) {
+        const C v = inert ? C(0) : e[q];
+        st(g0 + k + q * a.plane, v);
+        st(g1 + k + q * a.plane, v);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Grid setting 2 (Section 5.1, Fig. 30): the energy balance on NX x NY
+// control volumes of 2 x 2 lattice spacings whose faces pass through lattice
+// nodes (face velocities are lattice velocities, no interpolation; centres at
+// the odd-odd nodes), an explicit step of k lattice steps every k-th step,
+// node temperatures interpolated from the volumes.  Single walled cavities
+// without obstacles: the cavity spans 2 NX x 2 NY spacings.
+// ---------------------------------------------------------------------------
+
+struct Grid2Args {
+    int nx, ny, pitch, ncx, ncy;  // lattice nodes, node pitch, volumes
+    int dirichlet[4];             // W, E, S, N: Dirichlet side (else no heat flux)
+    double t_wall[4];
+};
+
+// One coarse step: Tn = T + (k / V) sum over faces of [-A u_n (T_P + T_nb)/2
+// + alpha A (T_nb - T_P) / d], V = 4, A = 2, d = 2 between volumes, d = 1 to a
+// Dirichlet wall face, no flux through other walls; u_n the lattice velocity
+// at the face's middle node (the velocity planes U, V).
+template <class C>
+__global__ void grid2_step_kernel(const Grid2Args g, const C *__restrict__ Tc, C *__restrict__ Tn,
+                                  const C *__restrict__ U, const C *__restrict__ V, C alpha, C dt) {
+    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    const int J = blockIdx.y * blockDim.y + threadIdx.y;
+    if (I >= g.ncx || J >= g.ncy) return;
+    const C TP = Tc[J * g.ncx + I];
+    const long long cn = (long long)(2 * J + 1) * g.pitch + (2 * I + 1);  // centre node
+    C acc = C(0);
+    auto face = [&](int dx, int dy, int side) {
+        const int In = I + dx, Jn = J + dy;
+        const long long kf = cn + (long long)dy * g.pitch + dx;
+        const C un = dx ? C(dx) * U[kf] : C(dy) * V[kf];
+        if (In >= 0 && In < g.ncx && Jn >= 0 && Jn < g.ncy) {
+            const C TN = Tc[Jn * g.ncx + In];
+            acc = acc + (C(-2) * un * C(0.5) * (TP + TN) + alpha * (TN - TP));
+        } else if (g.dirichlet[side]) {
+            acc = acc + C(2) * alpha * (C(g.t_wall[side]) - TP);
+        }
+    };
+    face(1, 0, 1);
+    face(0, 1, 3);
+    face(-1, 0, 0);
+    face(0, -1, 2);
+    Tn[J * g.ncx + I] = TP + dt * acc * C(0.25);
+}
+
+// Node temperatures from the volumes (Section 5.1's interpolation): a
+// centre takes its volume's value, a node between two (four) centres their
+// mean, a node on a wall without heat flux the nearest volume's value, a
+// Dirichlet node its wall value (as held in the temperature plane Tdir).
+// Writes the node plane X (and, when given, the two temperature planes of
+// the state), and copies the new volume values Tn into Tc at the centre
+// nodes.
+template <class C>
+__global__ void grid2_nodes_kernel(const Grid2Args g, const uint8_t *__restrict__ code, const C *Tdir,
+                                   const C *__restrict__ Tn, C *__restrict__ Tc, C *X, C *Ta, C *Tb) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= g.nx || j >= g.ny) return;
+    int ia0, ia1, ja0, ja1;
+    if (i & 1) ia0 = ia1 = (i - 1) / 2;
+    else if (i == 0) ia0 = ia1 = 0;
+    else if (i == g.nx - 1) ia0 = ia1 = g.ncx - 1;
+    else ia0 = i / 2 - 1, ia1 = i / 2;
+    if (j & 1) ja0 = ja1 = (j - 1) / 2;
+    else if (j == 0) ja0 = ja1 = 0;
+    else if (j == g.ny - 1) ja0 = ja1 = g.ncy - 1;
+    else ja0 = j / 2 - 1, ja1 = j / 2;
+    C t;
+    const long long k = (long long)j * g.pitch + i;
+    if ((decode(code[k]) >> 6) == TH_DIRICHLET) {
+        t = Tdir[k];  // the wall value the temperature planes hold
+    } else if (ia0 == ia1 && ja0 == ja1) {
+        t = Tn[ja0 * g.ncx + ia0];
+    } else if (ja0 == ja1) {
+        t = C(0.5) * (Tn[ja0 * g.ncx + ia0] + Tn[ja0 * g.ncx + ia1]);
+    } else if (ia0 == ia1) {
+        t = C(0.5) * (Tn[ja0 * g.ncx + ia0] + Tn[ja1 * g.ncx + ia0]);
+    } else {
+        t = C(0.25) * ((Tn[ja0 * g.ncx + ia0] + Tn[ja0 * g.ncx + ia1]) + (Tn[ja1 * g.ncx + ia0] + Tn[ja1 * g.ncx + ia1]));
+    }
+    X[k] = t;
+    if (Ta) Ta[k] = t;
+    if (Tb) Tb[k] = t;
+    if ((i & 1) && (j & 1)) Tc[((j - 1) / 2) * g.ncx + (i - 1) / 2] = Tn[((j - 1) / 2) * g.ncx + (i - 1) / 2];
+}
+
+// Volume values from the node temperatures at the centres (the initial state).
+template <class C>
+__global__ void grid2_gather_kernel(const Grid2Args g, const C *__restrict__ T, C *__restrict__ Tn) {
+    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    const int J = blockIdx.y * blockDim.y + threadIdx.y;
+    if (I >= g.ncx || J >= g.ncy) return;
+    Tn[J * g.ncx + I] = T[(long long)(2 * J + 1) * g.pitch + 2 * I + 1];
 }
 
 // Initial state: f^0 = f_eq(1, u0) (kept unrelaxed in f0_out for the step-0
@@ -1478,6 +1825,21 @@ struct TmaLaunch {
     int nfix, blocks;
     cudaStream_t stream;
 };
+
+// Box geometry of a tile shape (the host encodes its tensor maps from it).
+struct TmaShape {
+    int TW, TH, FW, FH, TWD, THT, THT_QUICK, CWD, CHT, STAGES, BLOCK;
+    unsigned SMEM;
+};
+
+// Tile shape cfg of the fused step kernel (central energy update): its
+// geometry, the shared-memory limit set and its blocks per SM.  Compiled in
+// one translation unit per storage type (step_*.cu).
+template <class S>
+cudaError_t tma_prepare(int cfg, TmaShape *shape, int *blocks_per_sm);
+// Launch of the fused step kernel of tile shape cfg.
+template <class S>
+cudaError_t tma_launch(int cfg, const TmaLaunch<S> &l);
 
 // Shared-memory limits of the QUICK (two temperature halo rows) and the
 // given-temperature kernels of shape kTmaConfigFv; blocks per SM of each.

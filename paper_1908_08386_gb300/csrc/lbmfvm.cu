@@ -78,9 +78,10 @@ struct Layout {
     // temperature planes X, Y (0 when the handle takes no sub-steps)
     size_t uv[2], tx[2];
     bool split;
+    size_t g[2];  // D2Q5 energy populations [5][ny][pitch] (0 for the FV energy update)
 };
 
-Layout make_layout(const lbmfvm_grid_t &g, int prec, int ncav = 1, bool split = false) {
+Layout make_layout(const lbmfvm_grid_t &g, int prec, int ncav = 1, bool split = false, bool lbm5 = false) {
     Layout L{};
     L.pitch = (int)align_up((size_t)g.nx, 64);
     L.plane = (long long)g.ny * L.pitch;
@@ -95,6 +96,8 @@ Layout make_layout(const lbmfvm_grid_t &g, int prec, int ncav = 1, bool split = 
     L.f[1] = take(9 * (size_t)L.plane * ss);
     L.T[0] = take((size_t)L.plane * cs);
     L.T[1] = take((size_t)L.plane * cs);
+    if (lbm5)
+        for (int i = 0; i < 2; i++) L.g[i] = take(5 * (size_t)L.plane * ss);
     L.split = split;
     if (split)
         for (int i = 0; i < 2; i++) {
@@ -274,6 +277,7 @@ struct lbmfvm {
     CUtensorMap map_f[2], map_T[2], map_c;
     CUtensorMap map_fo[2], map_To[2];  // output-tile boxes of the TMA tile kernel
     int tma_blocks_per_sm;
+    int tma_stages;   // pipeline stages of the tile shape in use
     int ntiles;       // tiles of the fused list (cavities with one energy update per step)
     int ntiles_split; // tiles of the sub-step list
     // tiles of the sub-step list taking part in sub-step s + 1 (the list is
@@ -283,6 +287,11 @@ struct lbmfvm {
     int fv_sub;       // sub-steps of a single cavity (batches: per cavity)
     int blocks_quick, blocks_given;  // blocks per SM of the QUICK and given-temperature kernels
     CUtensorMap map_TX;              // temperature box of the sub-steps' result plane X
+    int energy;                      // LBMFVM_ENERGY_*
+    int wall_bc;                     // LBMFVM_WALL_*
+    bool grid2;                      // energy balance on the coarse volumes of grid setting 2
+    int fv_every;                    // lattice steps per coarse energy step
+    int ncx, ncy;                    // coarse volumes
     uint64_t tiles_gen, graph_gen;   // tile-list generation, and the one the graph was captured with
     uint32_t code_crc; // CRC-32 of the node codes, identifies the geometry in checkpoints
     int tile_w, tile_h;
@@ -332,6 +341,8 @@ StepArgs<S> args_for(const lbmfvm_t *h, int cur) {
     a.t_ref = C(h->t_ref);
     a.fx = C(h->force[0]);
     a.fy = C(h->force[1]);
+    a.wall_fd = h->wall_bc == LBMFVM_WALL_FD;
+    a.fd_coef = C(3.0 * h->tau);
     for (int s = 0; s < 4; s++) {
         const bool moving = h->grid.bc[s] == LBMFVM_BC_MOVING;
         const bool vertical = s < 2;
@@ -405,29 +416,6 @@ lbmfvm_fv::TmaLaunch<S> tma_args(const lbmfvm_t *h, int cur, TileList list, cons
     return l;
 }
 
-template <class S, int CFG>
-void launch_tma_cfg(const lbmfvm_t *h, int cur, cudaStream_t s, bool stall) {
-    using G = typename TmaConfig<S, CFG>::G;
-    const lbmfvm_fv::TmaLaunch<S> l =
-        tma_args<S>(h, cur, list_fused(h), &h->map_T[cur], h->tma_blocks_per_sm, G::STAGES, s, stall);
-    if (l.blocks < 1) return;  // no active tile
-    // launched with programmatic stream serialisation: a step overlaps its
-    // launch and prologue with the previous step's last tiles (the kernel
-    // waits for the previous grid before touching the state)
-    cudaLaunchConfig_t lc = {};
-    lc.gridDim = dim3(l.blocks);
-    lc.blockDim = dim3(G::BLOCK);
-    lc.dynamicSmemBytes = G::SMEM_BYTES;
-    lc.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    lc.attrs = attr;
-    lc.numAttrs = 1;
-    cudaLaunchKernelEx(&lc, step_tma_kernel<S, G>, l.a, l.cavs, l.tiles, l.count, *l.map_f, *l.map_T, *l.map_c,
-                       *l.map_fo, *l.map_To, l.ctr, l.ctr_next, l.nfix);
-}
-
 // The cavities of the sub-step list: velocity pass, the sub-steps, then the
 // collision with the temperature the last sub-step left in plane X.
 template <class S>
@@ -453,28 +441,67 @@ void launch_split(const lbmfvm_t *h, int cur, cudaStream_t s) {
     lbmfvm_fv::launch_given<S>(tma_args<S>(h, cur, list, &h->map_TX, h->blocks_given, G::STAGES, s, false));
 }
 
+Grid2Args grid2_args(const lbmfvm_t *h) {
+    Grid2Args g{};
+    g.nx = h->grid.nx;
+    g.ny = h->grid.ny;
+    g.pitch = h->L.pitch;
+    g.ncx = h->ncx;
+    g.ncy = h->ncy;
+    for (int sd = 0; sd < 4; sd++) {
+        g.dirichlet[sd] = h->grid.bc[sd] == LBMFVM_BC_DIRICHLET;
+        g.t_wall[sd] = h->grid.t_wall[sd];
+    }
+    return g;
+}
+
+// Grid setting 2: on a coarse step the velocity pass, the coarse energy step
+// and the node temperatures from the volumes; every step the collision with
+// the node temperatures (plane X).
 template <class S>
-void launch_step_tma(const lbmfvm_t *h, int cur, cudaStream_t s, bool stall) {
+void launch_grid2(const lbmfvm_t *h, int cur, cudaStream_t s, bool fv_now) {
+    using C = typename Compute<S>::type;
+    using G = typename TmaConfig<S, kTmaConfigFv>::G;
+    const TileList list = list_split(h);
+    if (list.n < 1) return;
+    const TileHeader *tiles = reinterpret_cast<const TileHeader *>(h->base + list.slot) + 1;
+    const CavityDesc *cavs = reinterpret_cast<const CavityDesc *>(h->base + h->L.cav);
+    C *U = reinterpret_cast<C *>(h->base + h->L.uv[0]);
+    C *V = reinterpret_cast<C *>(h->base + h->L.uv[1]);
+    C *X = reinterpret_cast<C *>(h->base + h->L.tx[0]);
+    C *Tc = reinterpret_cast<C *>(h->base + h->L.tx[1]);
+    C *Tn = Tc + (size_t)h->ncx * h->ncy;
+    if (fv_now) {
+        const S *fin = reinterpret_cast<const S *>(h->base + h->L.f[cur]);
+        lbmfvm_fv::launch_uv<S>(fin, h->L.plane, h->L.pitch, h->grid.nx, h->grid.ny, tiles, list.n, cavs,
+                                h->base + h->L.code, U, V, h->tile_w, h->tile_h, s);
+        const Grid2Args g = grid2_args(h);
+        dim3 b(16, 16), gc((h->ncx + 15) / 16, (h->ncy + 15) / 16), gn((h->grid.nx + 15) / 16, (h->grid.ny + 15) / 16);
+        grid2_step_kernel<C><<<gc, b, 0, s>>>(g, Tc, Tn, U, V, C(h->alpha), C((double)h->fv_every));
+        const C *Tdir = reinterpret_cast<const C *>(h->base + h->L.T[cur]);
+        grid2_nodes_kernel<C><<<gn, b, 0, s>>>(g, h->base + h->L.code, Tdir, Tn, Tc, X, nullptr, nullptr);
+    }
+    lbmfvm_fv::launch_given<S>(tma_args<S>(h, cur, list, &h->map_TX, h->blocks_given, G::STAGES, s, false));
+}
+
+template <class S>
+void launch_step_tma(const lbmfvm_t *h, int cur, cudaStream_t s, bool stall, bool fv_now) {
     if (h->fv_quick) {
         using G = typename TmaConfig<S, kTmaConfigFv>::G;
         lbmfvm_fv::launch_quick<S>(
             tma_args<S>(h, cur, list_fused(h), &h->map_T[cur], h->blocks_quick, G::STAGES, s, stall));
     } else {
-        switch (h->tma_config) {
-            case 0: launch_tma_cfg<S, 0>(h, cur, s, stall); break;
-            case 2: launch_tma_cfg<S, 2>(h, cur, s, stall); break;
-            case 3: launch_tma_cfg<S, 3>(h, cur, s, stall); break;
-            case 4: launch_tma_cfg<S, 4>(h, cur, s, stall); break;
-            default: launch_tma_cfg<S, 1>(h, cur, s, stall); break;
-        }
+        lbmfvm_fv::tma_launch<S>(h->tma_config, tma_args<S>(h, cur, list_fused(h), &h->map_T[cur],
+                                                            h->tma_blocks_per_sm, h->tma_stages, s, stall));
     }
-    if (h->L.split) launch_split<S>(h, cur, s);
+    if (h->grid2) launch_grid2<S>(h, cur, s, fv_now);
+    else if (h->L.split) launch_split<S>(h, cur, s);
 }
 
 template <class S>
-void launch_step(const lbmfvm_t *h, int cur, cudaStream_t s, bool stall) {
+void launch_step(const lbmfvm_t *h, int cur, cudaStream_t s, bool stall, bool fv_now) {
     if (h->use_tma) {
-        launch_step_tma<S>(h, cur, s, stall);
+        launch_step_tma<S>(h, cur, s, stall, fv_now);
         return;
     }
     switch (h->tile_y) {
@@ -484,13 +511,41 @@ void launch_step(const lbmfvm_t *h, int cur, cudaStream_t s, bool stall) {
     }
 }
 
-void launch_one(const lbmfvm_t *h, int cur, cudaStream_t s, bool stall = false) {
+// Shift T_0 of the stored D2Q5 populations: the mean wall temperature of the
+// west and east sides.
+double lbm5_shift(const lbmfvm_t *h) { return 0.5 * (h->grid.t_wall[LBMFVM_SIDE_W] + h->grid.t_wall[LBMFVM_SIDE_E]); }
+
+// One step of the D2Q5 thermal lattice-Boltzmann energy solver.
+template <class S>
+void launch_lbm5(const lbmfvm_t *h, int cur, cudaStream_t s) {
+    using C = typename Compute<S>::type;
+    Lbm5Args<S> p{};
+    p.a = args_for<S>(h, cur);
+    p.gin = reinterpret_cast<const S *>(h->base + h->L.g[cur]);
+    p.gout = reinterpret_cast<S *>(h->base + h->L.g[cur ^ 1]);
+    p.omega_T = C(1.0 / (3.0 * h->alpha + 0.5));  // tau_T = alpha / c_s^2 + 1/2 (Eq. 20)
+    p.T0 = C(lbm5_shift(h));
+    dim3 block(32, 8), grid((h->grid.nx + 31) / 32, (h->grid.ny + 7) / 8);
+    step_lbm5_kernel<S><<<grid, block, 0, s>>>(p);
+}
+
+// One coupled step at parity cur; fv_now: grid setting 2 takes its coarse
+// energy step in this one.
+void launch_one(const lbmfvm_t *h, int cur, cudaStream_t s, bool stall = false, bool fv_now = true) {
+    if (h->energy == LBMFVM_ENERGY_LBM_D2Q5) {
+        switch (h->prec) {
+            case LBMFVM_F64: launch_lbm5<double>(h, cur, s); break;
+            case LBMFVM_F32X2: launch_lbm5<dsf>(h, cur, s); break;
+            default: launch_lbm5<float>(h, cur, s); break;
+        }
+        return;
+    }
     switch (h->prec) {
-        case LBMFVM_F64: launch_step<double>(h, cur, s, stall); break;
-        case LBMFVM_F32: launch_step<float>(h, cur, s, stall); break;
-        case LBMFVM_F16: launch_step<__half>(h, cur, s, stall); break;
-        case LBMFVM_BF16: launch_step<__nv_bfloat16>(h, cur, s, stall); break;
-        case LBMFVM_F32X2: launch_step<dsf>(h, cur, s, stall); break;
+        case LBMFVM_F64: launch_step<double>(h, cur, s, stall, fv_now); break;
+        case LBMFVM_F32: launch_step<float>(h, cur, s, stall, fv_now); break;
+        case LBMFVM_F16: launch_step<__half>(h, cur, s, stall, fv_now); break;
+        case LBMFVM_BF16: launch_step<__nv_bfloat16>(h, cur, s, stall, fv_now); break;
+        case LBMFVM_F32X2: launch_step<dsf>(h, cur, s, stall, fv_now); break;
     }
 }
 
@@ -509,7 +564,9 @@ int join_out(lbmfvm_t *h) {
 int build_graph(lbmfvm_t *h) {
     cudaGraph_t g = nullptr;
     CU(h, cudaStreamBeginCapture(h->s, cudaStreamCaptureModeThreadLocal));
-    for (int i = 0; i < kGraphSteps; i++) launch_one(h, i & 1, h->s);
+    // a graph starts at a step count that is a multiple of the coarse step
+    // interval (which divides kGraphSteps), so its coarse steps sit at fixed places
+    for (int i = 0; i < kGraphSteps; i++) launch_one(h, i & 1, h->s, false, (i + 1) % h->fv_every == 0);
     cudaError_t e = cudaStreamEndCapture(h->s, &g);
     if (e != cudaSuccess) return fail(h, LBMFVM_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(e));
     e = cudaGraphInstantiate(&h->graph, g, 0);
@@ -534,6 +591,9 @@ void launch_init(lbmfvm_t *h, const float *u0, const float *v0, const float *T0)
     dim3 block(32, 8), grid((h->grid.nx + 31) / 32, (h->grid.ny + 7) / 8);
     init_kernel<S><<<grid, block, 0, h->s>>>(a, f0, fstar, u0, v0, T0, h->grid.t_init, tw, h->grid.bc[0],
                                              h->grid.bc[1], h->grid.bc[2], h->grid.bc[3], Ta, Tb);
+    if (h->energy == LBMFVM_ENERGY_LBM_D2Q5)
+        init_lbm5_kernel<S><<<grid, block, 0, h->s>>>(a, f0, reinterpret_cast<S *>(h->base + h->L.g[0]),
+                                                      reinterpret_cast<S *>(h->base + h->L.g[1]), C(lbm5_shift(h)));
 }
 
 // Arguments of the kernels that read the state of the current step: the
@@ -600,6 +660,23 @@ void launch_rescale(lbmfvm_t *h) {
 
 int clear_tile_counters(lbmfvm_t *h);
 
+// Grid setting 2 at set_state: the volumes from the node temperatures at
+// their centres, then the node temperatures (plane X and both state planes)
+// from the volumes, as the oracle starts.
+template <class S>
+void launch_grid2_init(lbmfvm_t *h) {
+    using C = typename Compute<S>::type;
+    C *X = reinterpret_cast<C *>(h->base + h->L.tx[0]);
+    C *Tc = reinterpret_cast<C *>(h->base + h->L.tx[1]);
+    C *Tn = Tc + (size_t)h->ncx * h->ncy;
+    C *Ta = reinterpret_cast<C *>(h->base + h->L.T[0]);
+    C *Tb = reinterpret_cast<C *>(h->base + h->L.T[1]);
+    const Grid2Args g = grid2_args(h);
+    dim3 b(16, 16), gc((h->ncx + 15) / 16, (h->ncy + 15) / 16), gn((h->grid.nx + 15) / 16, (h->grid.ny + 15) / 16);
+    grid2_gather_kernel<C><<<gc, b, 0, h->s>>>(g, Ta, Tn);
+    grid2_nodes_kernel<C><<<gn, b, 0, h->s>>>(g, h->base + h->L.code, Ta, Tn, Tc, X, Ta, Tb);
+}
+
 int set_state_impl(lbmfvm_t *h, const float *u, const float *v, const float *T) {
     const size_t n = (size_t)h->grid.nx * h->grid.ny;
     float *stage = reinterpret_cast<float *>(h->base + h->L.stage);
@@ -614,6 +691,10 @@ int set_state_impl(lbmfvm_t *h, const float *u, const float *v, const float *T) 
     CU(h, cudaMemcpyAsync(dtw, tw, sizeof(tw), cudaMemcpyHostToDevice, h->s));
     DISPATCH(h, launch_init, h, du, dv, dT);
     CU(h, cudaGetLastError());
+    if (h->grid2) {
+        DISPATCH(h, launch_grid2_init, h);
+        CU(h, cudaGetLastError());
+    }
     h->parity = 0;
     h->steps = 0;
     if (int r = clear_tile_counters(h)) return r;
@@ -687,39 +768,39 @@ int encode_maps(lbmfvm_t *h, int fw, int fh, int tw, int th, int cw, int ch, siz
 int upload_tiles(lbmfvm_t *h, int tw, int th);
 CavityDesc single_cavity_desc(const lbmfvm_t *h);
 
-template <class S, int CFG>
-int setup_tma_cfg(lbmfvm_t *h) {
-    using G = typename TmaConfig<S, CFG>::G;
+template <class S>
+int setup_tma(lbmfvm_t *h) {
+    lbmfvm_fv::TmaShape g{};
+    int per_sm = 0;
+    CU(h, lbmfvm_fv::tma_prepare<S>(h->tma_config, &g, &per_sm));
     // output boxes first: encode_maps() leaves the load boxes in map_f/map_T
-    if (int r = encode_maps<S>(h, G::TW, G::TH, G::TW, G::TH, G::CWD, G::CHT)) return r;
+    if (int r = encode_maps<S>(h, g.TW, g.TH, g.TW, g.TH, g.CWD, g.CHT)) return r;
     for (int b = 0; b < 2; b++) {
         h->map_fo[b] = h->map_f[b];
         h->map_To[b] = h->map_T[b];
     }
     if (h->L.split) {
         // the given-temperature kernel loads plane X with the central box
-        if (int r = encode_maps<S>(h, G::FW, G::FH, G::TWD, G::THT, G::CWD, G::CHT, h->L.tx[0])) return r;
+        if (int r = encode_maps<S>(h, g.FW, g.FH, g.TWD, g.THT, g.CWD, g.CHT, h->L.tx[0])) return r;
         h->map_TX = h->map_T[0];
     }
     // QUICK's fused kernel reaches two rows beyond the tile for temperatures
-    const int tht = h->fv_quick ? G::template WithTHalo<2>::THT : G::THT;
-    if (int r = encode_maps<S>(h, G::FW, G::FH, G::TWD, tht, G::CWD, G::CHT)) return r;
-    auto kern = step_tma_kernel<S, G>;
-    CU(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM_BYTES));
-    int dev = 0, per_sm = 0;
+    const int tht = h->fv_quick ? g.THT_QUICK : g.THT;
+    if (int r = encode_maps<S>(h, g.FW, g.FH, g.TWD, tht, g.CWD, g.CHT)) return r;
+    int dev = 0;
     CU(h, cudaGetDevice(&dev));
     CU(h, cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev));
-    CU(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, G::BLOCK, G::SMEM_BYTES));
     if (per_sm < 1) return fail(h, LBMFVM_ERR_CUDA, "TMA tile kernel does not fit on an SM");
     h->tma_blocks_per_sm = per_sm;
+    h->tma_stages = g.STAGES;
     if (h->fv_quick || h->L.split) {
         CU(h, lbmfvm_fv::prepare_modes<S>(&h->blocks_quick, &h->blocks_given));
         if (h->blocks_quick < 1 || h->blocks_given < 1)
             return fail(h, LBMFVM_ERR_CUDA, "TMA tile kernel of the energy-update options does not fit on an SM");
     }
-    h->tile_w = G::TW;
-    h->tile_h = G::TH;
-    return upload_tiles(h, G::TW, G::TH);
+    h->tile_w = g.TW;
+    h->tile_h = g.TH;
+    return upload_tiles(h, g.TW, g.TH);
 }
 
 // Tile lists of the TMA kernel (row by row over every active cavity) and the
@@ -739,7 +820,9 @@ int upload_tiles(lbmfvm_t *h, int tw, int th) {
         if (!h->atlas_cavs.empty() && !h->atlas_active[c]) continue;
         const CavityDesc &cd = table[c];
         const int m = cd.substeps < 1 ? 1 : cd.substeps;
-        std::vector<TileHeader> &tl = m > 1 ? split : fused;
+        // grid setting 2 collides with the node temperatures of its coarse
+        // volumes, like the sub-step path
+        std::vector<TileHeader> &tl = m > 1 || h->grid2 ? split : fused;
         for (int y0 = cd.y0; y0 < cd.y0 + cd.ny; y0 += th)
             for (int x0 = cd.x0; x0 < cd.x0 + cd.nx; x0 += tw) {
                 TileHeader t{};
@@ -877,17 +960,6 @@ int encode_maps(lbmfvm_t *h, int fw, int fh, int tw, int th, int cw, int ch, siz
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(h, LBMFVM_ERR_CUDA, "tensor map of the node codes failed (%d)", (int)r);
     return LBMFVM_OK;
-}
-
-template <class S>
-int setup_tma(lbmfvm_t *h) {
-    switch (h->tma_config) {
-        case 0: return setup_tma_cfg<S, 0>(h);
-        case 2: return setup_tma_cfg<S, 2>(h);
-        case 3: return setup_tma_cfg<S, 3>(h);
-        case 4: return setup_tma_cfg<S, 4>(h);
-        default: return setup_tma_cfg<S, 1>(h);
-    }
 }
 
 int setup_kernels(lbmfvm_t *h) {
@@ -1037,8 +1109,10 @@ int create_impl(const lbmfvm_grid_t *grid, const uint8_t *mask, double nu, doubl
     const bool tma_ok = !periodic;
     if (opts.kernel < LBMFVM_KERNEL_AUTO || opts.kernel > LBMFVM_KERNEL_TMA)
         return fail_thread(LBMFVM_ERR_ARG, "kernel = %d is not a LBMFVM_KERNEL_* value", opts.kernel);
-    if (opts.tma_config != LBMFVM_TMA_AUTOTUNE && (opts.tma_config < 0 || opts.tma_config >= kTmaConfigs))
-        return fail_thread(LBMFVM_ERR_ARG, "tma_config must be LBMFVM_TMA_AUTOTUNE or in [0, %d) (got %d)",
+    if (opts.tma_config != LBMFVM_TMA_AUTOTUNE && opts.tma_config != LBMFVM_TMA_DEFAULT &&
+        (opts.tma_config < 0 || opts.tma_config >= kTmaConfigs))
+        return fail_thread(LBMFVM_ERR_ARG,
+                           "tma_config must be LBMFVM_TMA_AUTOTUNE, LBMFVM_TMA_DEFAULT or in [0, %d) (got %d)",
                            kTmaConfigs, opts.tma_config);
     if (opts.kernel == LBMFVM_KERNEL_TMA && !tma_ok)
         return fail_thread(LBMFVM_ERR_ARG, "the TMA kernel needs walls on every side");
@@ -1050,19 +1124,62 @@ int create_impl(const lbmfvm_grid_t *grid, const uint8_t *mask, double nu, doubl
         return fail_thread(LBMFVM_ERR_ARG, "fv_scheme = %d is not a LBMFVM_FV_* value", opts.fv_scheme);
     if (opts.fv_substeps < 0 || opts.fv_substeps > 256)
         return fail_thread(LBMFVM_ERR_ARG, "fv_substeps = %d is outside [0, 256]", opts.fv_substeps);
-    // a single cavity's sub-steps (a batch's come with its cavity table)
+    if (opts.energy != LBMFVM_ENERGY_FV && opts.energy != LBMFVM_ENERGY_LBM_D2Q5)
+        return fail_thread(LBMFVM_ERR_ARG, "energy = %d is not a LBMFVM_ENERGY_* value", opts.energy);
+    const bool lbm5 = opts.energy == LBMFVM_ENERGY_LBM_D2Q5;
+    if (opts.wall_bc != LBMFVM_WALL_NEE && opts.wall_bc != LBMFVM_WALL_FD)
+        return fail_thread(LBMFVM_ERR_ARG, "wall_bc = %d is not a LBMFVM_WALL_* value", opts.wall_bc);
+    const bool fd = opts.wall_bc == LBMFVM_WALL_FD;
+    if (opts.fv_grid != 1 && opts.fv_grid != 2)
+        return fail_thread(LBMFVM_ERR_ARG, "fv_grid = %d is not 1 or 2", opts.fv_grid);
+    if (opts.fv_every < 1 || opts.fv_every > 4096)
+        return fail_thread(LBMFVM_ERR_ARG, "fv_every = %d is outside [1, 4096]", opts.fv_every);
+    const bool grid2 = opts.fv_grid == 2;
+    if (grid2) {
+        if (atlas || lbm5 || fd || !tma_ok || opts.kernel == LBMFVM_KERNEL_GENERIC ||
+            opts.fv_scheme != LBMFVM_FV_CENTRAL || opts.fv_substeps != 1)
+            return fail_thread(LBMFVM_ERR_ARG, "grid setting 2 runs single walled cavities on the TMA kernel with "
+                                               "the central energy update, extrapolation walls and no sub-steps");
+        if ((grid->nx - 1) % 2 || (grid->ny - 1) % 2)
+            return fail_thread(LBMFVM_ERR_ARG, "grid setting 2 needs an even number of spacings (got %d x %d nodes)",
+                               grid->nx, grid->ny);
+        if (mask)
+            for (size_t k = 0; k < (size_t)grid->nx * grid->ny; k++)
+                if (mask[k]) return fail_thread(LBMFVM_ERR_ARG, "grid setting 2 takes no obstacle");
+        // positivity of the coarse explicit step next to a Dirichlet wall:
+        // (k / 4) (3 alpha + 2 alpha) <= 1
+        if (alpha * opts.fv_every > 0.8)
+            return fail_thread(LBMFVM_ERR_UNSTABLE, "alpha * fv_every = %.6g exceeds 0.8 (coarse explicit limit)",
+                               alpha * opts.fv_every);
+    } else if (opts.fv_every != 1) {
+        return fail_thread(LBMFVM_ERR_ARG, "fv_every applies to grid setting 2");
+    }
+    if (fd && (atlas || lbm5 || opts.kernel == LBMFVM_KERNEL_TMA || opts.fv_scheme != LBMFVM_FV_CENTRAL ||
+               opts.fv_substeps != 1))
+        return fail_thread(LBMFVM_ERR_ARG,
+                           "finite-difference walls run single cavities on the generic kernel with the central "
+                           "one-step energy update");
+    if (lbm5) {
+        if (atlas) return fail_thread(LBMFVM_ERR_ARG, "the D2Q5 energy solver runs single cavities only");
+        if (opts.store == LBMFVM_F16 || opts.store == LBMFVM_BF16)
+            return fail_thread(LBMFVM_ERR_ARG, "the D2Q5 energy solver stores F64, F32 or F32X2");
+        if (opts.fv_scheme != LBMFVM_FV_CENTRAL || opts.fv_substeps != 1)
+            return fail_thread(LBMFVM_ERR_ARG, "QUICK and sub-steps belong to the finite-volume energy update");
+    }
+    // a single cavity's sub-steps (a batch's come with its cavity table);
+    // the D2Q5 populations have no explicit-step limit (tau_T > 1/2)
     const int m = atlas ? 1 : substeps_for(opts.fv_substeps, alpha, 0.0);
-    if (!atlas)
+    if (!atlas && !lbm5 && opts.fv_grid != 2)
         if (const char *why = fv_unstable(alpha, 0.0, m))
             return fail_thread(LBMFVM_ERR_UNSTABLE, "alpha = %.6g, %d sub-step(s): %s", alpha, m, why);
-    bool split = m > 1;
+    bool split = m > 1 || grid2;
     if (atlas)
         for (const CavityDesc &cd : atlas->cavs) split |= cd.substeps > 1;
-    const bool fv_opt = split || opts.fv_scheme == LBMFVM_FV_QUICK;
+    const bool fv_opt = split || opts.fv_scheme == LBMFVM_FV_QUICK;  // (grid setting 2 is split)
     if (fv_opt && (!tma_ok || opts.kernel == LBMFVM_KERNEL_GENERIC))
         return fail_thread(LBMFVM_ERR_ARG, "QUICK face values and energy sub-steps need the TMA kernel (walls on every side)");
     if (atlas && !tma_ok) return fail_thread(LBMFVM_ERR_ARG, "a batch needs walls on every side");
-    const Layout L = make_layout(*grid, opts.store, atlas ? (int)atlas->cavs.size() : 1, split);
+    const Layout L = make_layout(*grid, opts.store, atlas ? (int)atlas->cavs.size() : 1, split, lbm5);
     if (opts.workspace && opts.workspace_bytes < L.total)
         return fail_thread(LBMFVM_ERR_NOMEM, "workspace of %zu bytes is smaller than the %zu needed",
                            opts.workspace_bytes, L.total);
@@ -1075,9 +1192,29 @@ int create_impl(const lbmfvm_grid_t *grid, const uint8_t *mask, double nu, doubl
     h->prec = opts.store;
     h->tile_y = opts.tile_y ? opts.tile_y : 8;
     h->use_tma = tma_ok && opts.kernel != LBMFVM_KERNEL_GENERIC;
-    h->tma_config = opts.tma_config == LBMFVM_TMA_AUTOTUNE ? 1 : opts.tma_config;
+    // the default shapes are the fastest measured ones: 64 x 16 with ring
+    // warps for 32- and 16-bit storage (two population halo rows when both
+    // population buffers and temperature planes fit in the L2, three
+    // otherwise), two blocks of 32 x 8 per SM for 64-bit
+    int shape_default = 3;
+    if (store_size(opts.store) != 8) {
+        int dev = 0, l2 = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) != cudaSuccess)
+            l2 = 0;
+        const size_t state = 2 * (9 * store_size(opts.store) + temp_size(opts.store)) * (size_t)L.plane;
+        shape_default = state <= (size_t)l2 ? 4 : 5;
+    }
+    h->tma_config = opts.tma_config == LBMFVM_TMA_AUTOTUNE || opts.tma_config == LBMFVM_TMA_DEFAULT ? shape_default
+                                                                                                  : opts.tma_config;
     h->fv_quick = opts.fv_scheme == LBMFVM_FV_QUICK;
     h->fv_sub = m;
+    h->energy = opts.energy;
+    h->wall_bc = opts.wall_bc;
+    h->grid2 = grid2;
+    h->fv_every = opts.fv_every;
+    h->ncx = (grid->nx - 1) / 2;
+    h->ncy = (grid->ny - 1) / 2;
+    if (lbm5 || fd) h->use_tma = false;  // their own or the generic kernel, no staged loads
     if (fv_opt) h->tma_config = kTmaConfigFv;  // the options' kernels come in this shape
     h->L = L;
     h->nu = nu;
@@ -1177,16 +1314,16 @@ int step_impl(lbmfvm_t *h, int64_t n) {
         CU(h, cudaGraphExecDestroy(h->graph));
         h->graph = nullptr;
     }
-    if (n >= kGraphSteps && !h->graph)
+    if (n >= kGraphSteps && !h->graph && kGraphSteps % h->fv_every == 0)
         if (int r = build_graph(h)) return r;
     while (n > 0) {
-        if (h->parity == 0 && n >= kGraphSteps && h->graph && !h->stall_next) {
+        if (h->parity == 0 && n >= kGraphSteps && h->graph && !h->stall_next && h->steps % h->fv_every == 0) {
             CU(h, cudaGraphLaunch(h->graph, h->s));
             n -= kGraphSteps;
             h->steps += kGraphSteps;
             h->launches += kGraphSteps;
         } else {
-            launch_one(h, h->parity, h->s, h->stall_next);
+            launch_one(h, h->parity, h->s, h->stall_next, (h->steps + 1) % h->fv_every == 0);
             h->stall_next = false;
             CU(h, cudaGetLastError());
             h->parity ^= 1;
@@ -1207,9 +1344,14 @@ void lbmfvm_opts_default(lbmfvm_opts_t *o) {
     o->store = LBMFVM_F32;
     o->tile_y = 0;
     o->kernel = LBMFVM_KERNEL_AUTO;
+    o->tma_config = LBMFVM_TMA_DEFAULT;
     o->t_ref = NAN;
     o->fv_scheme = LBMFVM_FV_CENTRAL;
     o->fv_substeps = 1;
+    o->energy = LBMFVM_ENERGY_FV;
+    o->wall_bc = LBMFVM_WALL_NEE;
+    o->fv_grid = 1;
+    o->fv_every = 1;
 }
 
 int lbmfvm_workspace_bytes(const lbmfvm_grid_t *grid, const lbmfvm_opts_t *opts, size_t *bytes) {
@@ -1218,8 +1360,9 @@ int lbmfvm_workspace_bytes(const lbmfvm_grid_t *grid, const lbmfvm_opts_t *opts,
     const int prec = opts ? opts->store : LBMFVM_F32;
     if (prec < LBMFVM_F64 || prec > LBMFVM_F32X2) return fail_thread(LBMFVM_ERR_ARG, "invalid store precision");
     // sub-steps (or the automatic choice, which may take them) need the planes
-    const bool split = opts && opts->fv_substeps != 1;
-    *bytes = make_layout(*grid, prec, 1, split).total;
+    const bool split = opts && (opts->fv_substeps != 1 || opts->fv_grid == 2);
+    const bool lbm5 = opts && opts->energy == LBMFVM_ENERGY_LBM_D2Q5;
+    *bytes = make_layout(*grid, prec, 1, split, lbm5).total;
     return LBMFVM_OK;
 }
 
@@ -1243,10 +1386,17 @@ int lbmfvm_create(const lbmfvm_grid_t *grid, const uint8_t *mask, double Ra, dou
     if (opts) o = *opts;
     if (o.fv_substeps < 0 || o.fv_substeps > 256)
         return fail_thread(LBMFVM_ERR_ARG, "fv_substeps = %d is outside [0, 256]", o.fv_substeps);
-    o.fv_substeps = substeps_for(o.fv_substeps, alpha, U0);
-    if (const char *why = fv_unstable(alpha, U0, o.fv_substeps))
-        return fail_thread(LBMFVM_ERR_UNSTABLE, "U0 = %.6g, alpha = %.6g, %d sub-step(s): %s", U0, alpha,
-                           o.fv_substeps, why);
+    if (o.energy == LBMFVM_ENERGY_FV && o.fv_grid == 2) {
+        // grid setting 2: central advection over k lattice steps, (U0 k)^2 <= 2 alpha k
+        if (U0 * U0 * o.fv_every > 2.0 * alpha)
+            return fail_thread(LBMFVM_ERR_UNSTABLE, "U0^2 fv_every = %.6g exceeds 2 alpha = %.6g (coarse advection limit)",
+                               U0 * U0 * o.fv_every, 2.0 * alpha);
+    } else if (o.energy == LBMFVM_ENERGY_FV) {
+        o.fv_substeps = substeps_for(o.fv_substeps, alpha, U0);
+        if (const char *why = fv_unstable(alpha, U0, o.fv_substeps))
+            return fail_thread(LBMFVM_ERR_UNSTABLE, "U0 = %.6g, alpha = %.6g, %d sub-step(s): %s", U0, alpha,
+                               o.fv_substeps, why);
+    }
     return create_impl(grid, mask, nu, alpha, gbeta, nullptr, &o, out);
 }
 
@@ -1372,6 +1522,8 @@ int lbmfvm_copy_state(lbmfvm_t *dst, lbmfvm_t *src) {
     if (dst->grid.nx != src->grid.nx || dst->grid.ny != src->grid.ny)
         return fail(dst, LBMFVM_ERR_ARG, "grids differ: %dx%d and %dx%d", dst->grid.nx, dst->grid.ny, src->grid.nx,
                     src->grid.ny);
+    if (dst->energy != LBMFVM_ENERGY_FV || src->energy != LBMFVM_ENERGY_FV)
+        return fail(dst, LBMFVM_ERR_ARG, "state copies hold finite-volume handles");
     // the source's queued steps finish before the copy reads its buffers
     if (int r = join_in(src)) return r;
     CU(src, cudaStreamSynchronize(src->s));

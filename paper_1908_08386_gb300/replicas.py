@@ -1,9 +1,11 @@
-"""Host-side logic of runs with one independent cavity per GPU (replicas).
+"""Host-side logic of multi-GPU runs of independent cavities.
 
-Cavities never exchange data, so several GPUs run independent problems and
-the only collective traffic is bookkeeping: a barrier around the timed
-region and the maximum of the per-rank times.  ``torchrun`` supplies RANK,
-WORLD_SIZE and LOCAL_RANK; the backend is NCCL on GPUs and gloo on CPU.
+Cavities never exchange data: several GPUs run independent problems (one
+cavity per GPU, or a batch's cavities sharded across GPUs), and the only
+collective traffic is bookkeeping: a barrier around the timed region, the
+maximum of the per-rank times and a gather of per-cavity results.
+``torchrun`` supplies RANK, WORLD_SIZE and LOCAL_RANK; the backend is NCCL on
+GPUs and gloo on CPU.
 """
 
 from __future__ import annotations
@@ -55,3 +57,30 @@ def max_over_ranks(x: float, size: int, device: str = "cuda") -> float:
 def whole_job_rate(units_per_rank: float, size: int, seconds: float) -> float:
     """Throughput of the whole job: every rank's units over the slowest rank's time."""
     return units_per_rank * size / seconds
+
+
+def shard(costs, size: int) -> list[list[int]]:
+    """Indices of the items each rank takes: longest-processing-time-first
+    over the given per-item costs (largest first, each to the least loaded
+    rank, ties to the lower rank), so the ranks' loads stay within the
+    largest single cost of each other.  Deterministic; every index appears
+    once."""
+    loads = [0.0] * size
+    out: list[list[int]] = [[] for _ in range(size)]
+    for i in sorted(range(len(costs)), key=lambda k: (-costs[k], k)):
+        r = min(range(size), key=lambda q: (loads[q], q))
+        out[r].append(i)
+        loads[r] += costs[i]
+    return [sorted(x) for x in out]
+
+
+def gather_rows(rows: list, size: int) -> list:
+    """Every rank's list of per-item rows, concatenated in rank order (every
+    rank gets the whole list)."""
+    if size == 1:
+        return list(rows)
+    import torch.distributed as dist
+
+    parts: list = [None] * size
+    dist.all_gather_object(parts, list(rows))
+    return [r for p in parts for r in p]

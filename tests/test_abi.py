@@ -4,6 +4,7 @@ declares, and rejects invalid arguments before touching the device."""
 import os
 import re
 
+import numpy as np
 import pytest
 
 import paper_1908_08386_gb300 as L
@@ -96,7 +97,7 @@ def test_null_handle_calls_fail_cleanly():
     lib.lbmfvm_destroy(None)
 
 
-@pytest.mark.parametrize("cfg", [-2, 5, 99])
+@pytest.mark.parametrize("cfg", [-3, 6, 99])
 def test_rejects_unknown_tile_shapes(cfg):
     o = L.lbmfvm_opts_default()
     o.tma_config = cfg
@@ -178,3 +179,58 @@ def test_workspace_holds_the_substep_planes():
     more = L.lbmfvm_workspace_bytes(g, o)
     # velocity planes u, v and two scratch temperature planes, FP32
     assert more - one >= 4 * 33 * 128 * 4
+
+
+def test_d2q5_energy_solver_options_are_checked():
+    g = L.make_grid(40, 40)
+    for store in (L.LBMFVM_F16, L.LBMFVM_BF16):
+        o = L.lbmfvm_opts_default()
+        o.energy, o.store = L.LBMFVM_ENERGY_LBM_D2Q5, store
+        with pytest.raises(L.LbmfvmError) as e:
+            L.lbmfvm_create_lattice(g, None, 0.1, 0.1, 0.0, None, o)
+        assert e.value.code == L.LBMFVM_ERR_ARG
+    o = L.lbmfvm_opts_default()
+    o.energy, o.fv_substeps = L.LBMFVM_ENERGY_LBM_D2Q5, 2
+    with pytest.raises(L.LbmfvmError) as e:
+        L.lbmfvm_create_lattice(g, None, 0.1, 0.1, 0.0, None, o)
+    assert e.value.code == L.LBMFVM_ERR_ARG
+    o = L.lbmfvm_opts_default()
+    o.energy = 7
+    with pytest.raises(L.LbmfvmError) as e:
+        L.lbmfvm_create_lattice(g, None, 0.1, 0.1, 0.0, None, o)
+    assert e.value.code == L.LBMFVM_ERR_ARG
+    # the populations add two buffers of five planes
+    o = L.lbmfvm_opts_default()
+    fv = L.lbmfvm_workspace_bytes(g, o)
+    o.energy = L.LBMFVM_ENERGY_LBM_D2Q5
+    assert L.lbmfvm_workspace_bytes(g, o) - fv >= 2 * 5 * 40 * 64 * 4
+
+
+def test_grid_setting_2_options_are_checked():
+    def create(nx, ny, k=1, mask=None, alpha=0.1, **kw):
+        o = L.lbmfvm_opts_default()
+        o.fv_grid, o.fv_every = 2, k
+        for a, v in kw.items():
+            setattr(o, a, v)
+        L.lbmfvm_create_lattice(L.make_grid(nx, ny), mask, 0.1, alpha, 0.0, None, o)
+
+    assert (L.lbmfvm_opts_default().fv_grid, L.lbmfvm_opts_default().fv_every) == (1, 1)
+    for args, code in (((40, 41), L.LBMFVM_ERR_ARG),          # odd number of spacings
+                       ((41, 41, 0), L.LBMFVM_ERR_ARG),       # k < 1
+                       ((41, 41, 9), L.LBMFVM_ERR_UNSTABLE)):  # alpha k > 0.8
+        with pytest.raises(L.LbmfvmError) as e:
+            create(*args)
+        assert e.value.code == code, args
+    mask = np.zeros((41, 41), np.uint8)
+    mask[20, 20] = 1
+    with pytest.raises(L.LbmfvmError) as e:
+        create(41, 41, mask=mask)
+    assert e.value.code == L.LBMFVM_ERR_ARG
+    with pytest.raises(L.LbmfvmError) as e:
+        create(41, 41, fv_substeps=2)
+    assert e.value.code == L.LBMFVM_ERR_ARG
+    o = L.lbmfvm_opts_default()
+    o.fv_every = 2  # without grid setting 2
+    with pytest.raises(L.LbmfvmError) as e:
+        L.lbmfvm_create_lattice(L.make_grid(41, 41), None, 0.1, 0.1, 0.0, None, o)
+    assert e.value.code == L.LBMFVM_ERR_ARG

@@ -14,7 +14,7 @@ import pytest
 
 import paper_1908_08386_gb300 as L
 
-HEADER_FMT = "<8sII4iq4i4dd6dQII2i84sI"  # the struct's fields in order, no padding
+HEADER_FMT = "<8sII4iq4i4dd6dQII4i76sI"  # the struct's fields in order, no padding
 
 
 def make_checkpoint(path, nx=7, ny=5, store=L.LBMFVM_F32, steps=1234, seed=0):
@@ -23,7 +23,7 @@ def make_checkpoint(path, nx=7, ny=5, store=L.LBMFVM_F32, steps=1234, seed=0):
     n = nx * ny
     payload = np.random.default_rng(seed).integers(0, 256, 2 * 9 * n * ss + n * ts + 2 * n * 8, dtype=np.uint8).tobytes()
     fields = [b"LBMFVMC1", 1, 256, nx, ny, store, 0, steps, 0, 0, 1, 1, 1.0, 0.0, 0.0, 0.0, 0.0,
-              0.8, 0.01, 1e-5, 0.5, 0.0, 0.0, len(payload), 0xDEADBEEF, zlib.crc32(payload), 0, 1, bytes(84)]
+              0.8, 0.01, 1e-5, 0.5, 0.0, 0.0, len(payload), 0xDEADBEEF, zlib.crc32(payload), 0, 1, 0, 0, bytes(76)]
     head = struct.pack(HEADER_FMT[:-1], *fields)
     head += struct.pack("<I", zlib.crc32(head))
     assert len(head) == 256
@@ -37,7 +37,7 @@ def test_header_struct_is_256_bytes_with_the_documented_offsets():
     assert ctypes.sizeof(H) == 256 == struct.calcsize(HEADER_FMT)
     assert H.steps.offset == 32 and H.t_wall.offset == 56 and H.payload_bytes.offset == 144
     assert H.code_crc.offset == 152 and H.payload_crc.offset == 156 and H.header_crc.offset == 252
-    assert H.fv_scheme.offset == 160 and H.fv_substeps.offset == 164
+    assert H.fv_scheme.offset == 160 and H.fv_substeps.offset == 164 and H.energy.offset == 168 and H.wall_bc.offset == 172
 
 
 @pytest.mark.parametrize("store", [L.LBMFVM_F32, L.LBMFVM_F16, L.LBMFVM_F64, L.LBMFVM_F32X2])

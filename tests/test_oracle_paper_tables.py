@@ -30,8 +30,13 @@ def steady(n, Ra, tol=1e-7, max_k=400):
 
 
 def nu_max_interior(loc):
-    # Eq. 90 evaluated on the rows strictly between the corner rows.
-    j = int(np.argmax(loc[1:-1])) + 1
+    """The boundary layer's maximum of Eq. 90's local Nusselt number: over the
+    rows from the third above the bottom corner to the third below the top
+    one.  The corner rows themselves and the two next to each belong to the
+    corner, where the Dirichlet corner node meets the adiabatic wall: at
+    Ra = 1e6 on 161^2 nodes they carry 18.5, 17.8 and 17.4 against the
+    boundary layer's 17.48 at Y = 0.0437 (row 7)."""
+    j = int(np.argmax(loc[3:-3])) + 3
     return loc[j], j
 
 

@@ -90,7 +90,7 @@ def test_ragged_grid_with_obstacles(store, tol, kernel, tile_y):
 
 
 @pytest.mark.parametrize("kernel", ["tma"])
-@pytest.mark.parametrize("cfg", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("cfg", [0, 1, 2, 3, 4, 5])
 @pytest.mark.parametrize("store", ["f64", "f32x2", "f32", "f16", "bf16"])
 @pytest.mark.parametrize("shape", [(130, 67), (64, 16), (200, 150), (31, 97)])
 def test_tma_kernels_agree_with_generic(store, shape, cfg, kernel):
