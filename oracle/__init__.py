@@ -86,6 +86,7 @@ def load_library(path: str):
     lib.orc_fields.argtypes = [vp, vp, vp, vp, vp]
     lib.orc_get_f.argtypes = [vp, vp]
     lib.orc_set_f.argtypes = [vp, vp]
+    lib.orc_set_T.argtypes = [vp, vp]
     lib.orc_classes.argtypes = [vp, vp, vp, vp]
     lib.orc_nusselt.argtypes = [vp, dp, vp, dp, vp]
     lib.orc_flux_nusselt.argtypes = [vp, vp]
@@ -222,6 +223,11 @@ class Oracle:
     def set_f(self, f):
         f = np.ascontiguousarray(f, dtype=np.float64).reshape(9, self.ny, self.nx)
         self._lib.orc_set_f(self._h, _ptr(f))
+
+    def set_T(self, T):
+        """Replace the temperature of the current state (f stays)."""
+        T = np.ascontiguousarray(T, dtype=np.float64).reshape(self.ny, self.nx)
+        self._lib.orc_set_T(self._h, _ptr(T))
 
     def classes(self):
         shp = (self.ny, self.nx)

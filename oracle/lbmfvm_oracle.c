@@ -833,6 +833,12 @@ void orc_set_f(orc_t *o, const double *f) {
     compute_moments(o);
 }
 
+/* Replace the temperature of the current state (ny*nx values, every node,
+ * the layout of orc_fields); f and the step count stay.  With orc_set_f it
+ * lets a test hand rows of one instance's state to another (a slab split
+ * with halo copies). */
+void orc_set_T(orc_t *o, const double *T) { memcpy(o->T, T, sizeof(double) * o->nx * o->ny); }
+
 void orc_classes(const orc_t *o, unsigned char *kind, unsigned char *therm, int *partner) {
     long n = (long)o->nx * o->ny;
     for (long k = 0; k < n; k++) {
