@@ -44,19 +44,27 @@ L2_FLUSH_BYTES = 512 << 20
 FALLBACK_HBM_GBS = 6800.0
 
 # DRAM bytes (read + write) per launch of step_tma_kernel from one ncu
-# capture (profiles/step_tma_kernel_f32_*.md), keyed by storage, cavity side
-# and the hash of the kernel source they were taken with: a constant from that
-# capture, not measured in this run, and reported only while the source hash
-# matches.
-NCU_TRAFFIC = {("f32", 4096, "d18624217ad849dc"): 1329.1e6,
+# capture (profiles/step_tma_kernel_f32_*.md), keyed by storage, cavity side,
+# tile shape and the hash of the kernel sources they were taken with: a
+# constant from that capture, not measured in this run, and reported only
+# while the key matches.
+NCU_TRAFFIC = {("f32", 4096, 5, "b9a392c2bdf1f262"): 1331.3e6,
                # 1024^2: the 85 MB state stays in the 129 MB L2 between steps,
                # so DRAM sees about half the algorithmic bytes
-               ("f32", 1024, "d18624217ad849dc"): 45.5e6}
+               ("f32", 1024, 4, "b9a392c2bdf1f262"): 46.8e6}
 
 
 def kernel_hash() -> str:
-    p = os.path.join(ROOT, "paper_1908_08386_gb300", "csrc", "kernels.cuh")
-    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+    h = hashlib.sha256()
+    for name in ("kernels.cuh", "step_shapes.inl"):
+        h.update(open(os.path.join(ROOT, "paper_1908_08386_gb300", "csrc", name), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(store, n, cfg):
+    """(bytes per launch, source label) of the ncu capture for this key, or (None, None)."""
+    t = NCU_TRAFFIC.get((store, n, cfg, kernel_hash()))
+    return (t, f"ncu capture of this kernel source (hash {kernel_hash()}, tile shape {cfg})") if t else (None, None)
 
 
 def measured_peak():
@@ -215,13 +223,13 @@ def roofline_large(L, WL, dev, stream, peak, peak_kind, n=4096, launches=128, wa
     launch_s = e0.elapsed_time(e1) * 1e-3 / k
     nbytes = BYTES_PER_LU["f32"] * case.nx * case.ny
     achieved = nbytes / launch_s / 1e9
-    traffic = NCU_TRAFFIC.get(("f32", n, kernel_hash()))
+    cfg = L.lbmfvm_kernel_info(cav.h)[1]
+    traffic, traffic_source = ncu_traffic("f32", n, cfg)
     cav.close()
     return {"workload": f"cavity {case.nx}x{case.ny}, Ra 1e7, Pr 0.71, U0 0.1, f32 storage",
             "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "peak_kind": peak_kind, "traffic": traffic,
-            "traffic_source": ("ncu capture of this kernel source (hash %s)" % kernel_hash()) if traffic else None,
-            "kernel": "step_tma_kernel", "algorithmic_bytes_per_launch": nbytes, "avg_launch_us": launch_s * 1e6,
+            "peak_kind": peak_kind, "traffic": traffic, "traffic_source": traffic_source,
+            "kernel": "step_tma_kernel", "tile_shape": cfg, "algorithmic_bytes_per_launch": nbytes, "avg_launch_us": launch_s * 1e6,
             "launches": k, "mlups": case.nx * case.ny / launch_s / 1e6}
 
 
@@ -354,7 +362,8 @@ def run_ours(args):
     bytes_per_launch = BYTES_PER_LU[args.store] * n_nodes * k_steps / k_launches
     achieved = bytes_per_launch / launch_s / 1e9
     peak, peak_kind = measured_peak()
-    traffic = NCU_TRAFFIC.get((args.store, args.size, kernel_hash()))
+    tile_shape = L.lbmfvm_kernel_info(cav.h)[1]
+    traffic, traffic_source = ncu_traffic(args.store, args.size, tile_shape)
 
     # The same kernel on a state ten times the L2 (4096^2, FP32; Ra 1e7 keeps
     # the thermal diffusivity inside the explicit limit): the HBM fraction of
@@ -415,8 +424,9 @@ def run_ours(args):
                    "wall_s": wall_s, "final_residual": last[0] if last else None,
                    "final_nusselt": last[1] if last else None},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": traffic,
-                     "traffic_source": ("ncu capture of this kernel source (hash %s)" % kernel_hash()) if traffic else None, "kernel": "step_kernel" if args.kernel == "generic" or args.store == "f64" else "step_tma_kernel", "peak_kind": peak_kind,
+                     "traffic": traffic, "traffic_source": traffic_source,
+                     "kernel": "step_kernel" if args.kernel == "generic" or args.store == "f64" else "step_tma_kernel",
+                     "tile_shape": tile_shape, "peak_kind": peak_kind,
                      "algorithmic_bytes_per_launch": bytes_per_launch, "avg_launch_us": launch_s * 1e6,
                      "coupled_steps_per_launch": k_steps / k_launches,
                      "us_per_coupled_step": launch_s * 1e6 * k_launches / k_steps},

@@ -166,12 +166,16 @@ typedef struct {
                                32x8, 256, 3; 32x16, 512, 2; 32x8, 256, 2 (two
                                blocks per SM); 32x8, 256 + 64 ring threads, 3;
                                the same with 3 halo rows (64-bit shapes 0-4 take 2).
-                               LBMFVM_TMA_DEFAULT: 4 when both population buffers
-                               and temperature planes fit in the L2, 5 otherwise
-                               (32- and 16-bit storage), 3 for 64-bit storage:
-                               the fastest measured on 1024^2 and 4096^2 cavities.
-                               LBMFVM_TMA_AUTOTUNE times every
-                               shape on the handle's own grid at create and keeps
+                               LBMFVM_TMA_DEFAULT: for a grid with fewer tiles
+                               than the GPU has SMs, 2 (32- and 16-bit storage)
+                               or 4 (64-bit), which spread it over more SMs;
+                               otherwise 4 when both population buffers and
+                               temperature planes fit in the L2, 5 if not (32-
+                               and 16-bit), 3 for 64-bit storage: the fastest
+                               measured on 64^2 to 4096^2 cavities.
+                               LBMFVM_TMA_AUTOTUNE times every shape (a
+                               captured graph of 32 launches, replayed twice)
+                               on the handle's own grid at create and keeps
                                the fastest (remembered per storage precision and
                                power-of-two size class for the process); shapes
                                never change results. */

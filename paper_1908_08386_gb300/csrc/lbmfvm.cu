@@ -988,13 +988,19 @@ int check_device_status(lbmfvm_t *h) {
 }
 
 // Autotuner of the TMA tile shape.  Each shape steps the handle's own grid
-// (from the cleared workspace, which is the rest state f = w_i, T = 0) a few
-// times; the fastest is kept and remembered for the storage precision and the
+// (from the cleared workspace, which is the rest state f = w_i, T = 0) in the
+// form the library runs it: a captured graph of kTuneSteps launches chained by
+// programmatic dependent launch, replayed once untimed and then timed over
+// kTuneReps replays with events on the handle's stream (timing launches one by
+// one from the host would measure the host's launch rate, not the kernel).
+// The fastest shape is kept and remembered for the storage precision and the
 // size class (the power of two of the nodes the tiles cover), so a class is
 // measured once per process.  Every shape computes the same arithmetic per
 // node, so the choice never changes results.  The population and temperature
-// buffers are cleared again afterwards.
-constexpr int kTuneSteps = 10;
+// buffers are cleared again afterwards.  Runs at creation, outside any stream
+// capture of the caller.
+constexpr int kTuneSteps = 32;
+constexpr int kTuneReps = 2;
 std::mutex g_tune_mu;
 std::map<std::pair<int, int>, int> g_tuned;
 
@@ -1032,13 +1038,23 @@ int autotune(lbmfvm_t *h) {
     for (int cfg = 0; cfg < kTmaConfigs && status == LBMFVM_OK; cfg++) {
         h->tma_config = cfg;
         if (setup_kernels(h) != LBMFVM_OK) continue;  // a shape that does not fit this device
-        for (int i = 0; i < 2; i++) launch_one(h, i & 1, h->s);
-        cudaEventRecord(e0, h->s);
-        for (int i = 0; i < kTuneSteps; i++) launch_one(h, i & 1, h->s);
-        cudaEventRecord(e1, h->s);
+        cudaGraph_t g = nullptr;
+        cudaGraphExec_t ge = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(h->s, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            for (int i = 0; i < kTuneSteps; i++) launch_one(h, i & 1, h->s);
+            e = cudaStreamEndCapture(h->s, &g);
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&ge, g, 0);
+        if (g) cudaGraphDestroy(g);
+        if (e == cudaSuccess) e = cudaGraphLaunch(ge, h->s);
+        if (e == cudaSuccess) e = cudaEventRecord(e0, h->s);
+        for (int r = 0; r < kTuneReps && e == cudaSuccess; r++) e = cudaGraphLaunch(ge, h->s);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, h->s);
         float ms = 0.0f;
-        cudaError_t e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
         if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (ge) cudaGraphExecDestroy(ge);
         if (e != cudaSuccess) {
             status = fail(h, LBMFVM_ERR_CUDA, "autotuning failed: %s", cudaGetErrorString(e));
             break;
@@ -1195,14 +1211,27 @@ int create_impl(const lbmfvm_grid_t *grid, const uint8_t *mask, double nu, doubl
     // the default shapes are the fastest measured ones: 64 x 16 with ring
     // warps for 32- and 16-bit storage (two population halo rows when both
     // population buffers and temperature planes fit in the L2, three
-    // otherwise), two blocks of 32 x 8 per SM for 64-bit
+    // otherwise), two blocks of 32 x 8 per SM for 64-bit.  A grid with fewer
+    // tiles than SMs is bound by the latency of one tile, not by the SMs'
+    // throughput, and takes the smaller tiles that spread it over more SMs:
+    // 64 x 8 (two blocks per SM) for 32- and 16-bit storage, 32 x 8 with ring
+    // warps for 64-bit.
     int shape_default = 3;
-    if (store_size(opts.store) != 8) {
-        int dev = 0, l2 = 0;
-        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) != cudaSuccess)
-            l2 = 0;
-        const size_t state = 2 * (9 * store_size(opts.store) + temp_size(opts.store)) * (size_t)L.plane;
-        shape_default = state <= (size_t)l2 ? 4 : 5;
+    {
+        int dev = 0, l2 = 0, sms = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            l2 = sms = 0;
+        const long long tiles = store_size(opts.store) == 8
+                                    ? (long long)((grid->nx + 31) / 32) * ((grid->ny + 7) / 8)
+                                    : (long long)((grid->nx + 63) / 64) * ((grid->ny + 15) / 16);
+        const bool small = tiles < sms;
+        if (store_size(opts.store) == 8) {
+            shape_default = small ? 4 : 3;
+        } else {
+            const size_t state = 2 * (9 * store_size(opts.store) + temp_size(opts.store)) * (size_t)L.plane;
+            shape_default = small ? 2 : state <= (size_t)l2 ? 4 : 5;
+        }
     }
     h->tma_config = opts.tma_config == LBMFVM_TMA_AUTOTUNE || opts.tma_config == LBMFVM_TMA_DEFAULT ? shape_default
                                                                                                   : opts.tma_config;

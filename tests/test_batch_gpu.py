@@ -150,3 +150,25 @@ def test_autotuned_shapes_change_no_result():
     assert np.array_equal(np.stack(tuned.fields()), np.stack(fixed.fields()))
     b = L.Batch(small_cases(), store="f16")  # autotuned by default
     assert 0 <= b.tma_config("f16") <= 5 and b.tma_config("f32") == -1  # upper levels not created yet
+
+
+def test_default_shape_spreads_small_grids_over_more_sms():
+    """The default tile shape: for a grid with fewer tiles than SMs the
+    smaller tiles (64 x 8, two blocks per SM, at 32 and 16 bits; 32 x 8 with
+    ring warps at 64 bits), else 64 x 16 with ring warps (two halo rows while
+    the state fits in the L2) or 32 x 8, two blocks per SM, at 64 bits."""
+    import torch
+
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    l2 = torch.cuda.get_device_properties(0).L2_cache_size
+    for n, store in ((64, "f32"), (128, "f16"), (1024, "f32"), (128, "f32x2"), (1024, "f32x2")):
+        cav = L.Cavity(n, n, Ra=1e5, Pr=0.71, Ma=MA, store=store)
+        if store == "f32x2":
+            want = 4 if ((n + 31) // 32) * ((n + 7) // 8) < sms else 3
+        elif ((n + 63) // 64) * ((n + 15) // 16) < sms:
+            want = 2
+        else:
+            per_node = 2 * (9 * (4 if store == "f32" else 2) + 4)
+            want = 4 if per_node * n * n <= l2 else 5
+        assert cav.tma_config == want, (n, store, cav.tma_config)
+        cav.close()

@@ -122,3 +122,24 @@ def test_substep_recipe_keeps_u0_and_the_relaxation_time():
     assert slowed > 0
     with pytest.raises(ValueError):
         WL.cavity_batch(2, 1, velocity="fast")
+
+
+def test_stored_oracle_steady_states_belong_to_the_bench_draw():
+    """tests/golden/steady_nusselt.json holds the FP64 oracle's steady states of
+    the seeded draw the bench's time-to-steady measurement runs: same cavities
+    (a draw of fewer cavities is a prefix of it), every residual below 1e-8,
+    Nusselt numbers in the range of natural convection in these cavities."""
+    import json
+    import os
+
+    p = os.path.join(os.path.dirname(__file__), "golden", "steady_nusselt.json")
+    d = json.load(open(p))
+    rows = d["cavities"]
+    cases = WL.cavity_batch(len(rows), d["seed"], sizes=tuple(d["sizes"]), velocity=d["velocity"])
+    assert [r["index"] for r in rows] == list(range(len(rows)))
+    for r, c in zip(rows, cases):
+        assert (r["nx"], r["ny"]) == (c.nx, c.ny)
+        assert r["Ra"] == c.Ra and r["Pr"] == c.Pr and r["Ma"] == c.Ma
+        assert r["residual"] < d["tol"] and 0.5 < r["nu_mean_hot"] < 20
+    short = WL.cavity_batch(16, d["seed"], sizes=tuple(d["sizes"]), velocity=d["velocity"])
+    assert [(c.nx, c.ny, c.Ra) for c in short] == [(c.nx, c.ny, c.Ra) for c in cases[:16]]
