@@ -14,8 +14,9 @@
  *   slice.
  * - 3x3 convolutions are cross-correlations with zero padding 1; weights are
  *   [Cout][9][Cin] with tap k = 3 ky + kx reading input (y + ky - 1,
- *   x + kx - 1).  Products are BF16 x BF16 on the tensor cores with FP32
- *   accumulation.
+ *   x + kx - 1).  Products are BF16 x BF16 on the tensor cores (tcgen05.mma,
+ *   FP32 accumulation in tensor memory) for the forward and adjoint
+ *   convolutions, warp-level mma for the weight gradient.
  * - The activation is the leaky ReLU with slope 1/16; its derivative is taken
  *   from the sign of the activation's output.
  * - All pointers are device pointers unless stated; stream is a cudaStream_t
@@ -23,8 +24,9 @@
  * - Return: 0 (LBMFVM_OK) or a negative status: -1 invalid argument (shape,
  *   alignment, NULL), -3 a CUDA error.  lbmfvm_sg_last_error() gives the
  *   message of the calling thread's last failure.
- * - Shape rules: H % 8 == 0 and W % 16 == 0 for 3x3 convolutions; Cin % 16
- *   == 0 and Cout % 32 == 0; channel strides multiples of 8 and slice
+ * - Shape rules: H % 8 == 0 and 16 <= W <= 256 with W % 16 == 0 for 3x3
+ *   convolutions; Cin % 16 == 0 and Cout % 32 == 0, Cout <= 256 for the
+ *   forward and adjoint convolutions; channel strides multiples of 8 and slice
  *   pointers 16-byte aligned.
  */
 #ifndef LBMFVM_SURROGATE_H
@@ -119,6 +121,11 @@ int lbmfvm_sg_resample_mask(const uint8_t *mask, int32_t nx, int32_t ny, uint8_t
  * floats each, row-major. */
 int lbmfvm_sg_resample_fields(const float *pred, int32_t H, int32_t W, const uint8_t *mask, int32_t nx, int32_t ny,
                               float U0, float *u, float *v, float *T, void *stream);
+
+/* Synchronises stream and reads the status word of the 3x3 convolution's
+ * bounded device waits: 0, or -4 if a wait ran out since the last check (that
+ * launch's output was not written; the word is cleared), -3 on a CUDA error. */
+int lbmfvm_sg_check(void *stream);
 
 const char *lbmfvm_sg_last_error(void);
 

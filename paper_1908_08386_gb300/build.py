@@ -1,6 +1,6 @@
 """Build the sm_103a CUDA library ``liblbmfvm.so`` in place with nvcc.
 
-Seven translation units compiled in parallel, one ``-gencode`` (compute_103a /
+Eight translation units compiled in parallel, one ``-gencode`` (compute_103a /
 sm_103a), static CUDA runtime, so the library loads on a machine without a GPU driver (the driver
 is only needed at the first CUDA call).
 """
@@ -17,9 +17,9 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "liblbmfvm.so")
 SOURCES = [os.path.join(CSRC, f) for f in ("lbmfvm.cu", "step_f32.cu", "step_f16.cu", "step_f64.cu", "fv_modes.cu",
-                                            "residual_noalloc.cu", "surrogate.cu")]
+                                            "residual_noalloc.cu", "surrogate.cu", "conv_tc.cu")]
 DEPS = SOURCES + [os.path.join(CSRC, "kernels.cuh"), os.path.join(CSRC, "batch.inl"), os.path.join(CSRC, "checkpoint.inl"),
-                  os.path.join(CSRC, "step_shapes.inl"), os.path.join(INCLUDE, "lbmfvm.h"),
+                  os.path.join(CSRC, "step_shapes.inl"), os.path.join(CSRC, "conv_tc.h"), os.path.join(INCLUDE, "lbmfvm.h"),
                   os.path.join(INCLUDE, "surrogate.h")]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 

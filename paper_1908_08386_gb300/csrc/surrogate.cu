@@ -1,21 +1,15 @@
 // Kernels of the learned warm start (include/surrogate.h).
 //
-// The 3x3 convolutions are implicit GEMMs on the tensor cores: BF16 x BF16
-// products with FP32 accumulation by warp-level mma (m16n8k16), operands
-// staged in shared memory by cp.async and read with ldmatrix.  Rows of 16
-// bytes are XOR-swizzled so that the eight rows one ldmatrix phase reads fall
-// in distinct bank groups.
-//
-// forward / adjoint (conv3x3_kernel): one block computes an 8 x 16 pixel
-//   tile of one image for 32 output channels; four warps, each two rows of 16
-//   pixels (two m16 tiles) by four n8 tiles.  Per 16 input channels it stages
-//   the tile's input with a one-pixel halo (10 x 18 pixels) and the weights of
-//   all nine taps, double-buffered, and runs the nine taps from the same
-//   staged input.
+// The forward and adjoint 3x3 convolutions run on the fifth-generation tensor
+// cores (conv_tc.cu: tcgen05.mma with tensor-memory accumulators, TMA-staged
+// operands).  This file holds the rest:
 // weight gradient (wgrad_kernel): one block owns 32 output x 16 input
 //   channels and a strided share of the pixel tiles (split K); its nine warps
-//   take one tap each, so a staged tile serves all taps; partial sums end in
-//   FP32 atomics.
+//   take one tap each, so a staged tile serves all taps; products on the
+//   tensor cores by warp-level mma (m16n8k16, BF16, FP32 accumulation) from
+//   operands staged by cp.async and read transposed with ldmatrix (rows of
+//   16 bytes XOR-swizzled so that the eight rows one ldmatrix phase reads fall
+//   in distinct bank groups); partial sums end in FP32 atomics.
 // Everything else is small and elementwise.
 
 #include <cuda_bf16.h>
@@ -25,6 +19,7 @@
 #include <cstdarg>
 #include <cstdio>
 
+#include "conv_tc.h"
 #include "surrogate.h"
 
 namespace {
@@ -50,7 +45,6 @@ int launched(const char *what) {
 using bf16 = __nv_bfloat16;
 constexpr float kLeak = 1.0f / 16.0f;
 
-__device__ __forceinline__ float leaky(float v) { return v > 0.0f ? v : kLeak * v; }
 __device__ __forceinline__ float dleaky(float y) { return y > 0.0f ? 1.0f : kLeak; }
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
@@ -68,11 +62,6 @@ __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-__device__ __forceinline__ void ldsm_x4(uint32_t &r0, uint32_t &r1, uint32_t &r2, uint32_t &r3, const void *p) {
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];"
-                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
-                 : "r"(smem_addr(p)));
-}
 __device__ __forceinline__ void ldsm_x4_t(uint32_t &r0, uint32_t &r1, uint32_t &r2, uint32_t &r3, const void *p) {
     asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0, %1, %2, %3}, [%4];"
                  : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
@@ -95,126 +84,10 @@ __device__ __forceinline__ int sw32(int r, int c) { return r * 16 + ((c ^ ((r >>
 __device__ __forceinline__ int sw64(int r, int c) { return r * 32 + ((c ^ ((r >> 1) & 3)) << 3); }
 
 // ---------------------------------------------------------------------------
-// 3x3 convolution (forward and adjoint)
-// ---------------------------------------------------------------------------
-constexpr int kTH = 8, kTW = 16;             // output tile: 8 rows x 16 pixels
-constexpr int kPH = kTH + 2, kPW = kTW + 2;  // staged input with halo
-constexpr int kBN = 32;                      // output channels per block
-constexpr int kKC = 16;                      // input channels per stage
-
-struct ConvArgs {
-    const bf16 *x;
-    const bf16 *w;
-    const float *bias;
-    bf16 *y;
-    const bf16 *m;
-    int ldx, ldy, ldm, B, H, W, Cin, Cout, mode;
-};
-
-__global__ void __launch_bounds__(128) conv3x3_kernel(const ConvArgs a) {
-    __shared__ __align__(128) bf16 patch[2][kPH * kPW * kKC];
-    __shared__ __align__(128) bf16 wts[2][9 * kBN * kKC];
-    const int tx0 = blockIdx.x * kTW, ty0 = blockIdx.y * kTH;
-    const int nco = a.Cout / kBN;
-    const int b = blockIdx.z / nco, co0 = (blockIdx.z % nco) * kBN;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-
-    auto stage_in = [&](int s, int c0) {
-        for (int i = tid; i < kPH * kPW * 2; i += 128) {
-            const int pix = i >> 1, half = i & 1;
-            const int gy = ty0 + pix / kPW - 1, gx = tx0 + pix % kPW - 1;
-            const bool in = gy >= 0 && gy < a.H && gx >= 0 && gx < a.W;
-            const bf16 *src = in ? a.x + ((long long)(b * a.H + gy) * a.W + gx) * a.ldx + c0 + half * 8 : a.x;
-            cp_async16(&patch[s][sw32(pix, half)], src, in ? 16 : 0);
-        }
-        for (int i = tid; i < 9 * kBN * 2; i += 128) {
-            const int row = i >> 1, half = i & 1;  // row = tap * 32 + co
-            const int tap = row / kBN, co = row % kBN;
-            cp_async16(&wts[s][sw32(row, half)], a.w + ((long long)(co0 + co) * 9 + tap) * a.Cin + c0 + half * 8, 16);
-        }
-        cp_async_commit();
-    };
-
-    float acc[2][4][4];
-#pragma unroll
-    for (int i = 0; i < 2; i++)
-#pragma unroll
-        for (int j = 0; j < 4; j++)
-#pragma unroll
-            for (int k = 0; k < 4; k++) acc[i][j][k] = 0.0f;
-
-    const int nch = a.Cin / kKC;
-    const int mi = lane >> 3, lr = lane & 7;
-    stage_in(0, 0);
-    for (int c = 0; c < nch; c++) {
-        if (c + 1 < nch) {
-            stage_in((c + 1) & 1, (c + 1) * kKC);
-            cp_async_wait<1>();
-        } else {
-            cp_async_wait<0>();
-        }
-        __syncthreads();
-        const bf16 *P = patch[c & 1];
-        const bf16 *Wt = wts[c & 1];
-#pragma unroll
-        for (int tap = 0; tap < 9; tap++) {
-            const int ky = tap / 3, kx = tap % 3;
-            uint32_t bfr[4][2];
-#pragma unroll
-            for (int j = 0; j < 2; j++) {
-                // matrices: (co +0..7, ci 0..7), (co +0..7, ci 8..15), (co +8..15, ci 0..7), (co +8..15, ci 8..15)
-                const int row = tap * kBN + j * 16 + (mi >> 1) * 8 + lr;
-                ldsm_x4(bfr[2 * j][0], bfr[2 * j][1], bfr[2 * j + 1][0], bfr[2 * j + 1][1], &Wt[sw32(row, mi & 1)]);
-            }
-#pragma unroll
-            for (int mt = 0; mt < 2; mt++) {
-                const int orow = warp * 2 + mt;
-                // matrices: (px 0..7, ci 0..7), (px 8..15, ci 0..7), (px 0..7, ci 8..15), (px 8..15, ci 8..15)
-                const int pix = (orow + ky) * kPW + (mi & 1) * 8 + lr + kx;
-                uint32_t afr[4];
-                ldsm_x4(afr[0], afr[1], afr[2], afr[3], &P[sw32(pix, mi >> 1)]);
-#pragma unroll
-                for (int nt = 0; nt < 4; nt++) mma16816(acc[mt][nt], afr, bfr[nt]);
-            }
-        }
-        __syncthreads();
-    }
-    // epilogue: accumulator (row g, cols 2t, 2t+1) and (row g + 8, ...)
-    const int g = lane >> 2, t = lane & 3;
-#pragma unroll
-    for (int mt = 0; mt < 2; mt++) {
-        const int yy = ty0 + warp * 2 + mt;
-#pragma unroll
-        for (int half = 0; half < 2; half++) {
-            const int xx = tx0 + g + half * 8;
-            const long long pix = (long long)(b * a.H + yy) * a.W + xx;
-#pragma unroll
-            for (int nt = 0; nt < 4; nt++) {
-                const int co = co0 + nt * 8 + 2 * t;
-                float v0 = acc[mt][nt][2 * half], v1 = acc[mt][nt][2 * half + 1];
-                if (a.mode == LBMFVM_SG_DLEAKY) {
-                    const __nv_bfloat162 mm = *reinterpret_cast<const __nv_bfloat162 *>(a.m + pix * a.ldm + co);
-                    v0 *= dleaky(__bfloat162float(mm.x));
-                    v1 *= dleaky(__bfloat162float(mm.y));
-                } else {
-                    if (a.bias) {
-                        v0 += a.bias[co];
-                        v1 += a.bias[co + 1];
-                    }
-                    if (a.mode == LBMFVM_SG_LEAKY) {
-                        v0 = leaky(v0);
-                        v1 = leaky(v1);
-                    }
-                }
-                *reinterpret_cast<__nv_bfloat162 *>(a.y + pix * a.ldy + co) = __floats2bfloat162_rn(v0, v1);
-            }
-        }
-    }
-}
-
-// ---------------------------------------------------------------------------
 // weight gradient of the 3x3 convolution
 // ---------------------------------------------------------------------------
+constexpr int kTH = 8, kTW = 16;             // pixel tile: 8 rows x 16 pixels
+constexpr int kPH = kTH + 2, kPW = kTW + 2;  // staged input with halo
 constexpr int kWCo = 32, kWCi = 16;  // channels per block
 
 struct WgradArgs {
@@ -553,11 +426,15 @@ int lbmfvm_sg_conv3x3(const uint16_t *x, int32_t ldx, const uint16_t *w, const f
     if (ldx < Cin || ldy < Cout || ldx % 8 || ldy % 8 || (m && (ldm < Cout || ldm % 8)) || !aligned16(x) ||
         !aligned16(w) || !aligned16(y) || (m && !aligned16(m)))
         return sg_fail(kErrArg, "conv3x3: strides or alignment");
-    ConvArgs a{reinterpret_cast<const bf16 *>(x), reinterpret_cast<const bf16 *>(w), bias, reinterpret_cast<bf16 *>(y),
-               reinterpret_cast<const bf16 *>(m), ldx, ldy, ldm, B, H, W, Cin, Cout, mode};
-    dim3 grid(W / kTW, H / kTH, B * (Cout / kBN));
-    conv3x3_kernel<<<grid, 128, 0, (cudaStream_t)stream>>>(a);
-    return launched("conv3x3");
+    return lbmfvm_sg_tc::conv3x3(x, ldx, w, bias, y, ldy, m, ldm, B, H, W, Cin, Cout, mode, (cudaStream_t)stream,
+                                 g_sg_err, sizeof(g_sg_err));
+}
+
+int lbmfvm_sg_check(void *stream) {
+    const int r = lbmfvm_sg_tc::check((cudaStream_t)stream);
+    if (r == -4) return sg_fail(-4, "a bounded wait of the tensor-core convolution ran out");
+    if (r) return sg_fail(kErrCuda, "status check failed");
+    return kOk;
 }
 
 int lbmfvm_sg_flip(const uint16_t *w, uint16_t *wt, int32_t Cin, int32_t Cout, void *stream) {

@@ -19,8 +19,11 @@ MUTANTS = {
     "tau_without_half": ("o->tau = nu / CS2 + 0.5;", "o->tau = nu / CS2 + 0.6;"),
     "stream_push_direction": ("int s = nbr(o, i, j, -EX[q], -EY[q]);\n                o->f[q * n + k]",
                               "int s = nbr(o, i, j, -EX[q], EY[q]);\n                o->f[q * n + k]"),
-    "nee_partner_velocity": ("feq(q, rf, o->uw[k], o->vw[k])", "feq(q, rf, uf, vf)"),
-    "nee_wall_density_unit": ("feq(q, rf, o->uw[k], o->vw[k])", "feq(q, 1.0, o->uw[k], o->vw[k])"),
+    # (the finite-difference walls start from the same equilibrium: name the
+    # extrapolation's site by the term that follows it)
+    "nee_partner_velocity": ("feq(q, rf, o->uw[k], o->vw[k]) + o->f[q * n + p]", "feq(q, rf, uf, vf) + o->f[q * n + p]"),
+    "nee_wall_density_unit": ("feq(q, rf, o->uw[k], o->vw[k]) + o->f[q * n + p]",
+                              "feq(q, 1.0, o->uw[k], o->vw[k]) + o->f[q * n + p]"),
     "nee_equilibrium_only": ("+ o->f[q * n + p] - feq(q, rf, uf, vf);", ";"),
     "fv_convective_sign": ("acc += -Fl * Tf + alpha", "acc += Fl * Tf + alpha"),
     "quick_downstream_weight": ("0.375 * o->T[down]", "0.25 * o->T[down]"),

@@ -60,6 +60,33 @@ def test_conv3x3_matches_the_reference(mode):
     assert np.all(got[..., :32] == 0.0)  # nothing outside the slice
 
 
+# a block takes up to four 128-position tiles, each with its own
+# tensor-memory accumulator (two at 160 and 256 output channels): full blocks,
+# a last block with fewer tiles (W = 128: nine tiles per image), images of
+# fewer tiles than a block holds
+@pytest.mark.parametrize("B,H,W,cin,cout", [(3, 8, 16, 16, 32), (1, 8, 128, 32, 32), (2, 16, 16, 160, 160),
+                                             (1, 8, 32, 256, 96), (1, 8, 64, 96, 256), (2, 24, 48, 64, 64),
+                                             (18, 128, 128, 16, 32), (32, 64, 64, 32, 64), (64, 32, 32, 32, 96),
+                                             (32, 32, 32, 256, 96)])
+def test_tensor_core_conv3x3_covers_the_network_shapes(B, H, W, cin, cout):
+    """The tcgen05 convolution on the widths, depths and image sizes of the
+    network (tiles of 128 padded positions that cross image rows and, for
+    W = 16, several rows; the adjoint's 256 output channels; a 16-channel
+    input; blocks of several tiles), each output element against the FP64
+    reference; the status word of the bounded waits stays clear."""
+    rng = np.random.default_rng(B * 1000 + W + cin + cout)
+    x, xr = bf(rng.standard_normal((B, H, W, cin)))
+    w, wr = bf(rng.standard_normal((cout, 9, cin)) / math.sqrt(9 * cin))
+    bias = torch.from_numpy(rng.standard_normal(cout).astype(np.float32)).cuda()
+    y = torch.full((B, H, W, cout), float("nan"), dtype=torch.bfloat16, device="cuda")
+    S.conv3x3(S.View(x), w.data_ptr(), bias.data_ptr(), S.View(y), B, H, W, cin, cout, S.LEAKY)
+    S.check()
+    ref = R.leaky(R.conv3x3(xr, wr.reshape(cout, 3, 3, cin), f64(bias)))
+    got = f64(y)
+    assert np.isfinite(got).all()  # every output position written
+    assert rel(got, ref) <= 1e-2
+
+
 def test_adjoint_and_weight_gradient_match_the_reference():
     rng = np.random.default_rng(2)
     B, H, W, cin, cout = 2, 16, 32, 32, 64
