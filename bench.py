@@ -443,9 +443,11 @@ def run_ours(args):
 
 def golden_steady_nusselt(seed, sizes, velocity):
     """Steady hot-wall Nusselt numbers of the FP64 oracle for the seeded draw
-    (tests/golden/steady_nusselt.json, written by the oracle script beside
-    it), or None when the draw is not the stored one."""
-    p = os.path.join(ROOT, "tests", "golden", "steady_nusselt.json")
+    (tests/golden/steady_nusselt*.json, written by the oracle script beside
+    them), or None when the draw is not a stored one."""
+    name = "steady_nusselt.json" if tuple(sizes) == (64, 96, 128) else \
+        "steady_nusselt_%s.json" % "_".join(str(x) for x in sizes)
+    p = os.path.join(ROOT, "tests", "golden", name)
     try:
         d = json.load(open(p))
     except Exception:

@@ -4,7 +4,7 @@
 //
 // Implicit GEMM.  A tile is M = 128 consecutive output positions of one image
 // and all N = Cout output channels; K runs over the nine taps and the input
-// channels in chunks of 16.  Positions are counted in a padded row
+// channels, 16 per MMA.  Positions are counted in a padded row
 // layout of Wp = W + 8 pixels per row: image pixel (y, x) sits at position
 // q = (y + 1) Wp + 8 + x, and the eight positions before each row's pixels
 // hold zeros, so that the left neighbour of x = 0 (q - 1) and the right
@@ -12,24 +12,27 @@
 // (ky, kx) of output position q reads input position q + (ky - 1) Wp + kx - 1,
 // so for a tile of 128 consecutive positions each tap's A operand is again a
 // run of 128 consecutive positions: the shared-memory descriptor of a tap is
-// the staged rows' base shifted by 16 bytes per position, with no re-staging.
+// the staged rows' base shifted by one row per position, with no re-staging.
 //
-// Shared-memory operand layout (no swizzle, K-major): channels in planes of
-// eight; within a plane one 16-byte row per position (A) or per output
-// channel (B), consecutive, so that eight rows form one 128-byte core matrix
-// (stride between eight-row groups 128 bytes) and the second plane of a
-// 16-channel chunk lies one plane further (the K-direction stride).  One TMA
-// box per stage brings both planes of the staged rows, each row from x = -8
-// (the pad positions, which the out-of-bounds fill makes zero) to W - 1, rows
-// outside the image zero-filled; a second box brings the chunk's two planes
-// of weights for all nine taps.
+// Shared-memory operand layout (K-major, swizzled): a pipeline stage holds KC
+// input channels (16, 32 or 64); each staged position (A) and each output
+// channel of each tap (B) is one row of 2 KC bytes (32, 64 or 128), rows
+// consecutive, in the 32-, 64- or 128-byte swizzle that TMA writes and the
+// matrix descriptors name.  The swizzle acts on absolute shared-memory
+// address bits, so a descriptor moved by whole rows (a tap's shift) or by 32
+// bytes inside a row (a K step of 16 channels) reads the same layout.  One TMA
+// box per stage brings the staged rows (one request per position: the
+// chunk's channels of a pixel are contiguous in the NHWC tensor), each row
+// from x = -8 (the pad positions, which the out-of-bounds fill makes zero) to
+// W - 1, rows outside the image zero-filled; a second box brings the chunk's
+// weights for all nine taps.
 //
 // A block holds G tiles of 128 consecutive positions, each with its own
 // accumulator in tensor memory: the staged rows and weights of a chunk serve
 // all of them (the halo rows and the weights are staged once per G tiles).
 //
 // Pipeline: thread 0 issues the two TMA loads of a stage on the stage's full
-// barrier, the 9 G MMAs of a chunk once it has landed, and a tcgen05.commit
+// barrier, the 9 (KC / 16) G MMAs of a chunk once it has landed, and a tcgen05.commit
 // on the stage's empty barrier; a stage is refilled once the MMAs of the chunk
 // before it have completed, so that the tensor pipe always has the current
 // chunk queued.  After the last chunk a commit on the done barrier releases
@@ -70,15 +73,16 @@ struct Params {
     int ldy, ldm, H, W, Cout, mode;
     int Wp;           // padded row length in positions
     int tiles;        // tiles of 128 positions per image
-    int G;            // tiles per block, each with its own accumulator
     int supers;       // blocks per image: ceil(tiles / G)
     uint32_t acc;     // TMEM columns between accumulators
-    int nch;          // 16-channel chunks of the input
+    int nch;          // chunks of KC input channels
     int stages;
-    int nrows;        // padded rows staged per tile (the largest any tile needs)
-    uint32_t a_plane; // bytes of one 8-channel plane of the staged rows
-    uint32_t b_plane; // bytes of one 8-channel plane of one tap's weights (Cout x 16)
-    uint32_t stage;   // bytes of one stage: two A planes and 18 B planes
+    int nrows;        // padded rows staged per block (the largest any block needs)
+    uint32_t rowb;    // bytes of one staged row (one position or one output channel): 2 KC
+    uint32_t a_bytes; // bytes of the staged rows of activations (nrows Wp rows)
+    uint32_t b_off;   // offset of the weights in a stage (a_bytes rounded up to 1 KB)
+    uint32_t b_tap;   // bytes of one tap's weights (Cout rows)
+    uint32_t stage;   // bytes of one stage: activations, then the nine taps' weights
     uint32_t ncols;   // TMEM columns allocated (G * acc)
     uint32_t idesc;   // instruction descriptor
 };
@@ -117,12 +121,12 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
     }
 }
 
-__device__ __forceinline__ void tma_load_5d(void *dst, const CUtensorMap *map, int c0, int c1, int c2, int c3,
-                                            int c4, uint64_t *bar) {
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int c0, int c1, int c2,
+                                            uint64_t *bar) {
     asm volatile(
-        "cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, "
-        "%6}], [%7];" ::"r"(saddr(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(saddr(bar))
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::
+            "r"(saddr(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(saddr(bar))
         : "memory");
 }
 __device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, int c0, int c1, int c2, int c3,
@@ -133,12 +137,15 @@ __device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, i
         "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(saddr(bar))
         : "memory");
 }
-// Shared-memory matrix descriptor, no swizzle: start address, the stride
-// between the two 8-channel planes of a K chunk (leading byte offset) and the
-// stride between groups of eight rows (stride byte offset, 128 bytes).
-__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo) {
-    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
-           ((uint64_t)((128u >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+// Shared-memory matrix descriptor of a K-major operand in swizzled rows of
+// rowb bytes (the layout TMA writes with the matching swizzle): start
+// address, the stride between groups of eight rows (8 rowb), the swizzle.
+// The swizzle applies to the absolute shared-memory address, so a start
+// moved by whole rows (the taps' shifts) or by 32 bytes within a row (the K
+// steps) needs no base offset.
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t rowb, uint32_t layout) {
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | (1ull << 16) | ((uint64_t)(((8u * rowb) >> 4) & 0x3FFFu) << 32) |
+           (1ull << 46) | ((uint64_t)layout << 61);
 }
 
 __device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate) {
@@ -171,17 +178,23 @@ __device__ __forceinline__ float dleaky(float y) { return y > 0.0f ? 1.0f : kLea
 // First padded row a tile stages (the row of its first input position).
 __device__ __forceinline__ int first_row(int q0, int Wp) { return (q0 - Wp - 1) / Wp; }
 
+// KC input channels per stage and G tiles per block are template parameters,
+// so that the issuing thread's nine KC / 16 G MMAs per chunk unroll into
+// descriptor additions of constants.
+template <int KC, int G>
 __global__ void __launch_bounds__(kThreads, 1)
     conv3x3_tc_kernel(const Params p, const __grid_constant__ CUtensorMap map_x,
                       const __grid_constant__ CUtensorMap map_w) {
+    constexpr uint32_t ROWB = 2 * KC;                              // bytes per staged row
+    constexpr uint32_t LAYOUT = KC == 16 ? 6u : (KC == 32 ? 4u : 2u);  // 32-, 64-, 128-byte swizzle
     extern __shared__ __align__(1024) uint8_t smem[];
     __shared__ __align__(8) uint64_t full[kMaxStages], empty[kMaxStages], done;
     __shared__ uint32_t tmem_base;
     __shared__ int failed;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int b = blockIdx.x / p.supers, t0 = (blockIdx.x % p.supers) * p.G;
-    const int g_n = p.tiles - t0 < p.G ? p.tiles - t0 : p.G;  // tiles of this block
+    const int b = blockIdx.x / p.supers, t0 = (blockIdx.x % p.supers) * G;
+    const int g_n = p.tiles - t0 < G ? p.tiles - t0 : G;  // tiles of this block
     const int q0 = p.Wp + kPad + kM * t0;  // first output position of the block
     const int ry0 = first_row(q0, p.Wp);
     uint8_t *base = smem + ((1024 - (saddr(smem) & 1023u)) & 1023u);
@@ -210,12 +223,12 @@ __global__ void __launch_bounds__(kThreads, 1)
         auto load = [&](int c) {
             const int s = c % p.stages;
             uint8_t *st = base + (size_t)s * p.stage;
-            mbar_expect_tx(&full[s], p.stage);
-            // both 8-channel planes of the staged rows, each row from x = -8
+            mbar_expect_tx(&full[s], p.a_bytes + 9u * p.b_tap);
+            // the chunk's channels of the staged rows, each row from x = -8
             // (the pad positions, zero-filled) to W - 1
-            tma_load_5d(st, &map_x, 0, -kPad, ry0 - 1, 2 * c, b, &full[s]);
-            // both planes of the chunk's weights for all nine taps
-            tma_load_4d(st + 2 * p.a_plane, &map_w, 0, 0, 2 * c, 0, &full[s]);
+            tma_load_4d(st, &map_x, c * KC, -kPad, ry0 - 1, b, &full[s]);
+            // the chunk's channels of every output channel's weights, all taps
+            tma_load_3d(st + p.b_off, &map_w, c * KC, 0, 0, &full[s]);
         };
         const int pre = p.nch < p.stages ? p.nch : p.stages;
         for (int c = 0; c < pre; c++) load(c);
@@ -226,13 +239,23 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (!(ok = mbar_wait(&full[s], (uint32_t)(c / p.stages) & 1u))) break;
             tc_after_sync();
             const uint32_t st = saddr(base + (size_t)s * p.stage);
+            // descriptors of the first tile's centre tap and the first tap's
+            // weights; every other operand is a constant number of 16-byte
+            // units away (start addresses live in the descriptor's low bits)
+            const uint64_t a0 = sdesc(st + (uint32_t)(q0 - ry0 * p.Wp) * ROWB, ROWB, LAYOUT);
+            const uint64_t b0 = sdesc(st + p.b_off, ROWB, LAYOUT);
+            const int wp16 = p.Wp * (int)(ROWB / 16), tap16 = (int)(p.b_tap / 16);
 #pragma unroll
             for (int tap = 0; tap < 9; tap++) {
-                const int off = (tap / 3 - 1) * p.Wp + (tap % 3 - 1);
-                const uint64_t bd = sdesc(st + 2u * p.a_plane + (uint32_t)tap * 2u * p.b_plane, p.b_plane);
-                for (int g = 0; g < g_n; g++) {
-                    const uint32_t a = st + (uint32_t)(q0 + kM * g + off - ry0 * p.Wp) * 16u;
-                    mma(tmem + (uint32_t)g * p.acc, sdesc(a, p.a_plane), bd, p.idesc, (c | tap) != 0);
+                const int off16 = (tap / 3 - 1) * wp16 + (tap % 3 - 1) * (int)(ROWB / 16);
+#pragma unroll
+                for (int kk = 0; kk < KC / 16; kk++) {
+                    const uint64_t bd = b0 + (uint64_t)(tap * tap16 + 2 * kk);
+#pragma unroll
+                    for (int g = 0; g < G; g++)
+                        if (g < g_n)
+                            mma(tmem + (uint32_t)g * p.acc, a0 + (uint64_t)(off16 + g * kM * (int)(ROWB / 16) + 2 * kk), bd,
+                                p.idesc, (c | tap | kk) != 0);
                 }
             }
             mma_commit(&empty[s]);
@@ -335,7 +358,7 @@ int *status_word() {
 
 int conv3x3(const uint16_t *x, int ldx, const uint16_t *w, const float *bias, uint16_t *y, int ldy,
             const uint16_t *m, int ldm, int B, int H, int W, int Cin, int Cout, int mode, cudaStream_t stream,
-            char *msg, size_t msglen, int g_req) {
+            char *msg, size_t msglen, int g_req, int kc_req, int s_req) {
     auto fail = [&](int code, const char *what) {
         snprintf(msg, msglen, "conv3x3: %s", what);
         return code;
@@ -361,17 +384,13 @@ int conv3x3(const uint16_t *x, int ldx, const uint16_t *w, const float *bias, ui
     p.Wp = W + kPad;
     const int q_first = p.Wp + kPad, q_end = H * p.Wp + kPad + W;  // output positions [q_first, q_end)
     p.tiles = (q_end - q_first + kM - 1) / kM;
-    p.nch = Cin / 16;
-    p.b_plane = (uint32_t)Cout * 16u;
     p.acc = 32;
     while ((int)p.acc < Cout) p.acc <<= 1;
     // instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B,
     // both K-major, N = Cout, M = 128
     p.idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(Cout >> 3) << 17) | ((uint32_t)(kM >> 4) << 24);
     const size_t extra = 1024;  // alignment of the stage area
-    const size_t half = 110 * 1024, whole = 220 * 1024;
-    // Tiles per block: a block stages its rows and the chunk's weights once
-    // for all its tiles.
+    const size_t whole = 220 * 1024;
     auto rows_for = [&](int G) {
         int most = 0;
         for (int t0 = 0; t0 < p.tiles; t0 += G) {
@@ -382,63 +401,99 @@ int conv3x3(const uint16_t *x, int ldx, const uint16_t *w, const float *bias, ui
         }
         return most;
     };
-    auto stage_for = [&](int G) { return 2u * (uint32_t)rows_for(G) * p.Wp * 16u + 18u * p.b_plane; };
-    int G = g_req;
+    // a stage: the staged rows of KC channels, then the nine taps' weights,
+    // each part starting on a 1 KB boundary (every TMA destination on a
+    // swizzle-pattern boundary)
+    auto up1k = [](size_t v) { return (v + 1023) & ~(size_t)1023; };
+    auto stage_for = [&](int G, int KC) {
+        const size_t rowb = 2 * (size_t)KC;
+        return up1k(up1k((size_t)rows_for(G) * p.Wp * rowb) + 9 * (size_t)Cout * rowb);
+    };
+    // Channels per stage KC (64, 32 or 16: rows of 128, 64 or 32 bytes, one
+    // TMA request per position and chunk) and 128-position tiles per block G
+    // (a block stages its rows and the chunk's weights once for all its
+    // tiles, each with its own accumulator): the widest rows, then the most
+    // tiles (at most four) that let a stage fit twice in shared memory.
+    // Measured on the network's layers (every combination of 16, 32, 64
+    // channels per stage, 1, 2, 4 tiles per block and 2 to 6 stages): 16
+    // channels per stage, tiles per block by accumulator width (two of 32 or
+    // 128 columns, four of 64, one of 256, so that two blocks share an SM),
+    // 32 channels per stage for one 256-column tile where two such stages
+    // fit, and two stages per block (two blocks per SM beat deeper pipelines:
+    // one block's fill and epilogue overlap the other's MMAs).
+    int KC = kc_req, G = g_req;
     if (G <= 0) {
-        // measured on the network's layers: four tiles per block while the
-        // tensor memory holds them (two of 160 or 256 channels), fewer when a
-        // stage would not fit twice
-        G = (int)(512 / p.acc) < 4 ? (int)(512 / p.acc) : 4;
-        while (G > 1 && (G / 2 >= p.tiles || (whole - extra) / stage_for(G) < 2)) G >>= 1;
+        G = p.acc == 64 ? 4 : (p.acc == 256 ? 1 : 2);
+        while (G > 1 && G / 2 >= p.tiles) G >>= 1;
     }
+    if (KC <= 0) KC = (G == 1 && Cin % 32 == 0 && (whole - extra) / stage_for(G, 32) >= 2) ? 32 : 16;
+    if (KC != 16 && KC != 32 && KC != 64) return fail(-1, "channels per stage must be 16, 32 or 64");
+    if (Cin % KC) return fail(-1, "Cin is not a multiple of the channels per stage");
     if (G < 1 || (uint32_t)G * p.acc > 512u) return fail(-1, "tiles per block exceed the tensor memory");
-    p.G = G;
+    p.nch = Cin / KC;
+    p.rowb = 2u * (uint32_t)KC;
     p.supers = (p.tiles + G - 1) / G;
     p.ncols = (uint32_t)G * p.acc;
     p.nrows = rows_for(G);
-    p.a_plane = (uint32_t)p.nrows * p.Wp * 16u;
-    p.stage = 2u * p.a_plane + 18u * p.b_plane;
-    // stages: two blocks per SM when their columns fit the tensor memory and
-    // two or more stages fit in half the shared memory, else one block with
-    // as many as fit
-    int stages = p.ncols <= 256u ? (int)((half - extra) / p.stage) : 0;
-    if (stages < 2) stages = (int)((whole - extra) / p.stage);
+    p.a_bytes = (uint32_t)p.nrows * p.Wp * p.rowb;
+    p.b_off = (uint32_t)up1k(p.a_bytes);
+    p.b_tap = (uint32_t)Cout * p.rowb;
+    p.stage = (uint32_t)stage_for(G, KC);
+    // two stages per block (measured, above)
+    int stages = s_req > 0 ? s_req : 2;
     if (stages > kMaxStages) stages = kMaxStages;
+    if ((size_t)stages * p.stage + extra > whole) return fail(-1, "the stages do not fit in shared memory");
     if (stages < 2) return fail(-1, "a pipeline stage does not fit twice in shared memory");
     p.stages = stages;
     const size_t smem = (size_t)stages * p.stage + extra;
 
-    // Activations as (8 channels, x, y, plane of 8 channels, image): one box
-    // of both planes of a chunk over the staged rows lands plane after plane,
-    // each a run of positions; x starts at -8 so that the pad positions come
-    // back zero, and rows outside the image are zero-filled.
+    // Activations as (channel, x, y, image): one box of the chunk's KC
+    // channels over the staged rows lands as nrows Wp rows of 2 KC bytes in
+    // the swizzle of the descriptors; x starts at -8 so that the pad
+    // positions come back zero, and rows outside the image are zero-filled.
+    const CUtensorMapSwizzle sw = KC == 16 ? CU_TENSOR_MAP_SWIZZLE_32B
+                                           : (KC == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B);
     CUtensorMap mx, mw;
-    const cuuint64_t xdim[5] = {8, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)(Cin / 8), (cuuint64_t)B};
-    const cuuint64_t xstr[4] = {(cuuint64_t)ldx * 2, (cuuint64_t)W * ldx * 2, 16, (cuuint64_t)H * W * ldx * 2};
-    const cuuint32_t xbox[5] = {8, (cuuint32_t)p.Wp, (cuuint32_t)p.nrows, 2, 1}, one5[5] = {1, 1, 1, 1, 1};
-    if (enc(&mx, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<uint16_t *>(x), xdim, xstr, xbox, one5,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+    const cuuint64_t xdim[4] = {(cuuint64_t)Cin, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)B};
+    const cuuint64_t xstr[3] = {(cuuint64_t)ldx * 2, (cuuint64_t)W * ldx * 2, (cuuint64_t)H * W * ldx * 2};
+    const cuuint32_t xbox[4] = {(cuuint32_t)KC, (cuuint32_t)p.Wp, (cuuint32_t)p.nrows, 1}, one4[4] = {1, 1, 1, 1};
+    if (enc(&mx, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<uint16_t *>(x), xdim, xstr, xbox, one4,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return fail(-3, "activation tensor map");
-    // Weights [Cout][9][Cin] as (8 channels, output channel, plane, tap): one
-    // box of a chunk's two planes for all taps lands tap-plane after
-    // tap-plane, each Cout rows of 16 bytes.
-    const cuuint64_t wdim[4] = {8, (cuuint64_t)Cout, (cuuint64_t)(Cin / 8), 9};
-    const cuuint64_t wstr[3] = {(cuuint64_t)9 * Cin * 2, 16, (cuuint64_t)Cin * 2};
-    const cuuint32_t wbox[4] = {8, (cuuint32_t)Cout, 2, 9};
-    if (enc(&mw, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<uint16_t *>(w), wdim, wstr, wbox, one5,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+    // Weights [Cout][9][Cin] as (input channel, output channel, tap): one box
+    // of the chunk's channels lands tap after tap, each Cout rows of 2 KC
+    // bytes.
+    const cuuint64_t wdim[3] = {(cuuint64_t)Cin, (cuuint64_t)Cout, 9};
+    const cuuint64_t wstr[2] = {(cuuint64_t)9 * Cin * 2, (cuuint64_t)Cin * 2};
+    const cuuint32_t wbox[3] = {(cuuint32_t)KC, (cuuint32_t)Cout, 9};
+    if (enc(&mw, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<uint16_t *>(w), wdim, wstr, wbox, one4,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return fail(-3, "weight tensor map");
 
-    cudaError_t e = cudaFuncSetAttribute(conv3x3_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    using Kernel = void (*)(const Params, const CUtensorMap, const CUtensorMap);
+    Kernel kern = nullptr;
+    switch (KC * 8 + G) {
+        case 16 * 8 + 1: kern = conv3x3_tc_kernel<16, 1>; break;
+        case 16 * 8 + 2: kern = conv3x3_tc_kernel<16, 2>; break;
+        case 16 * 8 + 4: kern = conv3x3_tc_kernel<16, 4>; break;
+        case 32 * 8 + 1: kern = conv3x3_tc_kernel<32, 1>; break;
+        case 32 * 8 + 2: kern = conv3x3_tc_kernel<32, 2>; break;
+        case 32 * 8 + 4: kern = conv3x3_tc_kernel<32, 4>; break;
+        case 64 * 8 + 1: kern = conv3x3_tc_kernel<64, 1>; break;
+        case 64 * 8 + 2: kern = conv3x3_tc_kernel<64, 2>; break;
+        case 64 * 8 + 4: kern = conv3x3_tc_kernel<64, 4>; break;
+        default: return fail(-1, "tiles per block must be 1, 2 or 4");
+    }
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int per_sm = 0;
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, conv3x3_tc_kernel, kThreads, smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
     if (e != cudaSuccess) return fail(-3, cudaGetErrorString(e));
     // the blocks an SM holds must find their tensor-memory columns free, so
     // that no allocation waits
     if (per_sm < 1 || (uint32_t)per_sm * p.ncols > 512u) return fail(-1, "tensor memory would be oversubscribed");
-    conv3x3_tc_kernel<<<B * p.supers, kThreads, smem, stream>>>(p, mx, mw);
+    kern<<<B * p.supers, kThreads, smem, stream>>>(p, mx, mw);
     e = cudaGetLastError();
     if (e != cudaSuccess) return fail(-3, cudaGetErrorString(e));
     return 0;

@@ -1,10 +1,11 @@
-"""Writes steady_nusselt.json: the FP64 oracle's steady hot-wall Nusselt
-numbers (residual below 1e-8, checked every 1000 steps; Eq. 90, trapezoid
-mean) of the seeded uneven-cavity draw that bench.py's time-to-steady
-measurement runs (workloads.cavity_batch(count, 20190822, sizes=(64, 96, 128)),
-U0 capped).  Calls only the oracle; one process per cavity.
+"""Writes steady_nusselt.json (sides 64, 96, 128) or steady_nusselt_<sides>.json
+(other sides): the FP64 oracle's steady hot-wall Nusselt numbers (residual
+below 1e-8, checked every 1000 steps; Eq. 90, trapezoid mean) of the seeded
+uneven-cavity draw that bench.py's time-to-steady measurement runs
+(workloads.cavity_batch(count, 20190822, sizes=sides), U0 capped).  Calls
+only the oracle; one process per cavity.
 
-    python tests/golden/make_steady_nusselt.py [count] [processes]
+    python tests/golden/make_steady_nusselt.py [count] [processes] [sides, e.g. 128,192,256]
 """
 
 import json
@@ -22,12 +23,13 @@ SIZES = (64, 96, 128)
 TOL = 1e-8
 
 
-def steady_nusselt(i):
+def steady_nusselt(args):
+    i, sizes = args
     os.environ["OMP_NUM_THREADS"] = "1"
     import oracle
     from paper_1908_08386_gb300 import workloads as WL
 
-    c = WL.cavity_batch(i + 1, SEED, sizes=SIZES)[i]
+    c = WL.cavity_batch(i + 1, SEED, sizes=sizes)[i]
     o = oracle.Oracle.from_groups(c.nx, c.ny, c.Ra, c.Pr, c.Ma, mask=c.mask, t_init=c.t_init)
     t0 = time.time()
     r = float("inf")
@@ -44,12 +46,20 @@ def steady_nusselt(i):
 def main():
     count = int(sys.argv[1]) if len(sys.argv) > 1 else 32
     procs = int(sys.argv[2]) if len(sys.argv) > 2 else os.cpu_count()
+    sizes = tuple(int(x) for x in sys.argv[3].split(",")) if len(sys.argv) > 3 else SIZES
     with mp.get_context("spawn").Pool(procs) as pool:
-        rows = pool.map(steady_nusselt, range(count), chunksize=1)
+        # the largest cavities first, so that the pool ends together
+        from paper_1908_08386_gb300 import workloads as WL
+
+        cases = WL.cavity_batch(count, SEED, sizes=sizes)
+        order = sorted(range(count), key=lambda i: -cases[i].nx * cases[i].ny)
+        rows = pool.map(steady_nusselt, [(i, sizes) for i in order], chunksize=1)
+    rows.sort(key=lambda r: r["index"])
     out = {"_source": "FP64 CPU oracle (oracle/lbmfvm_oracle.c) run to a steady residual below 1e-8 "
                       "(checks every 1000 steps) by tests/golden/make_steady_nusselt.py",
-           "seed": SEED, "sizes": list(SIZES), "velocity": "capped", "tol": TOL, "cavities": rows}
-    with open(os.path.join(HERE, "steady_nusselt.json"), "w") as fh:
+           "seed": SEED, "sizes": list(sizes), "velocity": "capped", "tol": TOL, "cavities": rows}
+    name = "steady_nusselt.json" if sizes == SIZES else "steady_nusselt_%s.json" % "_".join(map(str, sizes))
+    with open(os.path.join(HERE, name), "w") as fh:
         json.dump(out, fh, indent=1)
 
 
