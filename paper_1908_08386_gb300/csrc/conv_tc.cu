@@ -27,20 +27,23 @@
 // W - 1, rows outside the image zero-filled; a second box brings the chunk's
 // weights for all nine taps.
 //
-// A block holds G tiles of 128 consecutive positions, each with its own
-// accumulator in tensor memory: the staged rows and weights of a chunk serve
-// all of them (the halo rows and the weights are staged once per G tiles).
+// A unit is G tiles of 128 consecutive positions of one image, each with its
+// own accumulator in tensor memory: the staged rows and weights of a chunk
+// serve all of them (the halo rows and the weights are staged once per G
+// tiles).
 //
-// Pipeline: thread 0 issues the two TMA loads of a stage on the stage's full
-// barrier, the 9 (KC / 16) G MMAs of a chunk once it has landed, and a tcgen05.commit
-// on the stage's empty barrier; a stage is refilled once the MMAs of the chunk
-// before it have completed, so that the tensor pipe always has the current
-// chunk queued.  After the last chunk a commit on the done barrier releases
-// the epilogue: each warp reads its 32 TMEM lanes (positions) of every
-// accumulator, adds the bias
-// and applies the activation (or multiplies by the activation's derivative),
-// and stores BF16.  Every wait is bounded (1 s); a wait that runs out sets a
-// device status word, and the block drains what it issued before leaving.
+// Persistent pipeline, one block per SM taking units in turn, three roles:
+// one thread of warp 0 issues the two TMA loads of every chunk into a ring of
+// stages (each refilled once the MMAs that read it have completed); one
+// thread of warp 1 issues the 9 (KC / 16) G MMAs of a chunk once it has
+// landed, commits the stage back to the loader, and after a unit's last chunk
+// commits its accumulator set to the epilogue; warps 2-5 (each one quarter of
+// the 128 tensor-memory lanes) read the set, add the bias and apply the
+// activation (or multiply by the activation's derivative), store BF16 and
+// hand the set back.  Two accumulator sets alternate, so a unit's epilogue
+// overlaps the next unit's MMAs.  Every wait is bounded (1 s); a wait that
+// runs out sets a device status word, and the block drains its copies and
+// MMAs before it leaves.
 
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -58,8 +61,8 @@ namespace {
 
 using bf16 = __nv_bfloat16;
 
-constexpr int kM = 128;        // output positions per block (TMEM lanes)
-constexpr int kThreads = 128;  // four warps; warp w reads TMEM lanes 32w..32w+31
+constexpr int kM = 128;        // output positions per tile (TMEM lanes)
+constexpr int kThreads = 192;  // a loading warp, an issuing warp, four epilogue warps
 constexpr int kPad = 8;        // zero positions before each padded row (128 bytes per plane)
 constexpr int kMaxStages = 8;
 constexpr uint64_t kWaitNs = 1000000000ull;
@@ -70,10 +73,10 @@ struct Params {
     bf16 *y;
     const bf16 *m;
     int *status;
-    int ldy, ldm, H, W, Cout, mode;
+    int ldy, ldm, B, H, W, Cout, mode;
     int Wp;           // padded row length in positions
     int tiles;        // tiles of 128 positions per image
-    int supers;       // blocks per image: ceil(tiles / G)
+    int supers;       // units per image: ceil(tiles / G)
     uint32_t acc;     // TMEM columns between accumulators
     int nch;          // chunks of KC input channels
     int stages;
@@ -83,7 +86,7 @@ struct Params {
     uint32_t b_off;   // offset of the weights in a stage (a_bytes rounded up to 1 KB)
     uint32_t b_tap;   // bytes of one tap's weights (Cout rows)
     uint32_t stage;   // bytes of one stage: activations, then the nine taps' weights
-    uint32_t ncols;   // TMEM columns allocated (G * acc)
+    uint32_t ncols;   // TMEM columns allocated (two sets of G accumulators)
     uint32_t idesc;   // instruction descriptor
 };
 
@@ -178,37 +181,61 @@ __device__ __forceinline__ float dleaky(float y) { return y > 0.0f ? 1.0f : kLea
 // First padded row a tile stages (the row of its first input position).
 __device__ __forceinline__ int first_row(int q0, int Wp) { return (q0 - Wp - 1) / Wp; }
 
-// KC input channels per stage and G tiles per block are template parameters,
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(bar)) : "memory");
+}
+
+// Persistent: a block takes units (G consecutive tiles of one image) in turn,
+// with three roles.  Warp 0 (one thread) loads the stages of every chunk of
+// every unit through a ring of p.stages stages; warp 1 (one thread) issues the
+// MMAs of a unit into one of two accumulator sets in tensor memory and
+// commits each stage back to the loader; warps 2-5 read the finished set
+// (each its quarter of the 128 lanes), apply the epilogue and store, and
+// hand the set back, so that a unit's epilogue overlaps the next unit's MMAs.
+// KC input channels per stage and G tiles per unit are template parameters,
 // so that the issuing thread's nine KC / 16 G MMAs per chunk unroll into
 // descriptor additions of constants.
 template <int KC, int G>
 __global__ void __launch_bounds__(kThreads, 1)
     conv3x3_tc_kernel(const Params p, const __grid_constant__ CUtensorMap map_x,
                       const __grid_constant__ CUtensorMap map_w) {
-    constexpr uint32_t ROWB = 2 * KC;                              // bytes per staged row
+    constexpr uint32_t ROWB = 2 * KC;                                  // bytes per staged row
     constexpr uint32_t LAYOUT = KC == 16 ? 6u : (KC == 32 ? 4u : 2u);  // 32-, 64-, 128-byte swizzle
     extern __shared__ __align__(1024) uint8_t smem[];
-    __shared__ __align__(8) uint64_t full[kMaxStages], empty[kMaxStages], done;
+    __shared__ __align__(8) uint64_t full[kMaxStages], empty[kMaxStages], accf[2], acce[2], drain;
     __shared__ uint32_t tmem_base;
-    __shared__ int failed;
+    __shared__ volatile int abort_flag;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int b = blockIdx.x / p.supers, t0 = (blockIdx.x % p.supers) * G;
-    const int g_n = p.tiles - t0 < G ? p.tiles - t0 : G;  // tiles of this block
-    const int q0 = p.Wp + kPad + kM * t0;  // first output position of the block
-    const int ry0 = first_row(q0, p.Wp);
+    const int units = p.B * p.supers;
+    const uint32_t set_cols = (uint32_t)G * p.acc;  // columns of one accumulator set
     uint8_t *base = smem + ((1024 - (saddr(smem) & 1023u)) & 1023u);
+    auto geometry = [&](int u, int &b, int &q0, int &ry0, int &g_n) {
+        b = u / p.supers;
+        const int t0 = (u % p.supers) * G;
+        g_n = p.tiles - t0 < G ? p.tiles - t0 : G;
+        q0 = p.Wp + kPad + kM * t0;  // first output position of the unit
+        ry0 = first_row(q0, p.Wp);
+    };
+    auto give_up = [&]() {
+        abort_flag = 1;
+        atomicExch(p.status, 1);
+    };
 
     if (tid == 0) {
         for (int s = 0; s < p.stages; s++) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
-        mbar_init(&done, 1);
-        failed = 0;
+        for (int i = 0; i < 2; i++) {
+            mbar_init(&accf[i], 1);
+            mbar_init(&acce[i], 4);  // one arrival per epilogue warp
+        }
+        mbar_init(&drain, 1);
+        abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 0) {
+    if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(&tmem_base)),
                      "r"(p.ncols)
                      : "memory");
@@ -219,113 +246,152 @@ __global__ void __launch_bounds__(kThreads, 1)
     tc_after_sync();
     const uint32_t tmem = tmem_base;
 
-    if (tid == 0) {
-        auto load = [&](int c) {
-            const int s = c % p.stages;
-            uint8_t *st = base + (size_t)s * p.stage;
-            mbar_expect_tx(&full[s], p.a_bytes + 9u * p.b_tap);
-            // the chunk's channels of the staged rows, each row from x = -8
-            // (the pad positions, zero-filled) to W - 1
-            tma_load_4d(st, &map_x, c * KC, -kPad, ry0 - 1, b, &full[s]);
-            // the chunk's channels of every output channel's weights, all taps
-            tma_load_3d(st + p.b_off, &map_w, c * KC, 0, 0, &full[s]);
-        };
-        const int pre = p.nch < p.stages ? p.nch : p.stages;
-        for (int c = 0; c < pre; c++) load(c);
-        bool ok = true;
-        int issued = 0;  // chunks whose MMAs were issued
-        for (int c = 0; c < p.nch && ok; c++) {
-            const int s = c % p.stages;
-            if (!(ok = mbar_wait(&full[s], (uint32_t)(c / p.stages) & 1u))) break;
+    if (warp == 0) {
+        if (lane == 0) {
+            // loader: chunk loads n = 0, 1, ... into stage n % stages
+            int n = 0;
+            for (int u = blockIdx.x; u < units && !abort_flag; u += gridDim.x) {
+                int b, q0, ry0, g_n;
+                geometry(u, b, q0, ry0, g_n);
+                for (int c = 0; c < p.nch; c++, n++) {
+                    const int s = n % p.stages;
+                    if (n >= p.stages && !mbar_wait(&empty[s], (uint32_t)(n / p.stages - 1) & 1u)) {
+                        give_up();
+                        break;
+                    }
+                    uint8_t *st = base + (size_t)s * p.stage;
+                    mbar_expect_tx(&full[s], p.a_bytes + 9u * p.b_tap);
+                    // the chunk's channels of the staged rows, each row from
+                    // x = -8 (the pad positions, zero-filled) to W - 1
+                    tma_load_4d(st, &map_x, c * KC, -kPad, ry0 - 1, b, &full[s]);
+                    // the chunk's channels of every output channel's weights
+                    tma_load_3d(st + p.b_off, &map_w, c * KC, 0, 0, &full[s]);
+                }
+            }
+            // every load issued has landed before the block leaves
+            for (int m = n - p.stages < 0 ? 0 : n - p.stages; m < n; m++)
+                mbar_wait(&full[m % p.stages], (uint32_t)(m / p.stages) & 1u);
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        if (lane == 0) {
+            int n = 0, i = 0;
+            for (int u = blockIdx.x; u < units && !abort_flag; u += gridDim.x, i++) {
+                int b, q0, ry0, g_n;
+                geometry(u, b, q0, ry0, g_n);
+                const int set = i & 1;
+                // the epilogue has emptied this set (its use two units ago)
+                if (i >= 2 && !mbar_wait(&acce[set], (uint32_t)((i >> 1) - 1) & 1u)) {
+                    give_up();
+                    break;
+                }
+                tc_after_sync();
+                const uint32_t acc0 = tmem + (uint32_t)set * set_cols;
+                for (int c = 0; c < p.nch; c++, n++) {
+                    const int s = n % p.stages;
+                    if (!mbar_wait(&full[s], (uint32_t)(n / p.stages) & 1u)) {
+                        give_up();
+                        break;
+                    }
+                    tc_after_sync();
+                    const uint32_t st = saddr(base + (size_t)s * p.stage);
+                    // descriptors of the first tile's centre tap and the first
+                    // tap's weights; every other operand is a constant number
+                    // of 16-byte units away (start addresses live in the
+                    // descriptor's low bits)
+                    const uint64_t a0 = sdesc(st + (uint32_t)(q0 - ry0 * p.Wp) * ROWB, ROWB, LAYOUT);
+                    const uint64_t b0 = sdesc(st + p.b_off, ROWB, LAYOUT);
+                    const int wp16 = p.Wp * (int)(ROWB / 16), tap16 = (int)(p.b_tap / 16);
+#pragma unroll
+                    for (int tap = 0; tap < 9; tap++) {
+                        const int off16 = (tap / 3 - 1) * wp16 + (tap % 3 - 1) * (int)(ROWB / 16);
+#pragma unroll
+                        for (int kk = 0; kk < KC / 16; kk++) {
+                            const uint64_t bd = b0 + (uint64_t)(tap * tap16 + 2 * kk);
+#pragma unroll
+                            for (int g = 0; g < G; g++)
+                                if (g < g_n)
+                                    mma(acc0 + (uint32_t)g * p.acc,
+                                        a0 + (uint64_t)(off16 + g * kM * (int)(ROWB / 16) + 2 * kk), bd, p.idesc,
+                                        (c | tap | kk) != 0);
+                        }
+                    }
+                    mma_commit(&empty[s]);
+                }
+                if (abort_flag) break;
+                mma_commit(&accf[set]);
+            }
+            // every MMA issued has completed before the block leaves
+            mma_commit(&drain);
+            mbar_wait(&drain, 0);
+        }
+        __syncwarp();
+    } else {
+        // epilogue: warp w reads tensor-memory lanes 32 (w % 4) .. + 31
+        const int quarter = warp & 3;
+        int i = 0;
+        for (int u = blockIdx.x; u < units && !abort_flag; u += gridDim.x, i++) {
+            int b, q0, ry0, g_n;
+            geometry(u, b, q0, ry0, g_n);
+            const int set = i & 1;
+            if (!mbar_wait(&accf[set], (uint32_t)(i >> 1) & 1u)) {
+                give_up();
+                break;
+            }
             tc_after_sync();
-            const uint32_t st = saddr(base + (size_t)s * p.stage);
-            // descriptors of the first tile's centre tap and the first tap's
-            // weights; every other operand is a constant number of 16-byte
-            // units away (start addresses live in the descriptor's low bits)
-            const uint64_t a0 = sdesc(st + (uint32_t)(q0 - ry0 * p.Wp) * ROWB, ROWB, LAYOUT);
-            const uint64_t b0 = sdesc(st + p.b_off, ROWB, LAYOUT);
-            const int wp16 = p.Wp * (int)(ROWB / 16), tap16 = (int)(p.b_tap / 16);
+            for (int g = 0; g < g_n; g++) {
+                const int q = q0 + kM * g + quarter * 32 + lane;
+                const int yy = q / p.Wp - 1, xx = q % p.Wp - kPad;
+                const bool valid = yy >= 0 && yy < p.H && xx >= 0 && xx < p.W;
+                const long long pix = ((long long)b * p.H + yy) * p.W + xx;
+                for (int j = 0; j < p.Cout / 16; j++) {
+                    uint32_t r[16];
+                    tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)set * set_cols +
+                                  (uint32_t)g * p.acc + (uint32_t)(16 * j),
+                              r);
+                    if (!valid) continue;
+                    float v[16];
 #pragma unroll
-            for (int tap = 0; tap < 9; tap++) {
-                const int off16 = (tap / 3 - 1) * wp16 + (tap % 3 - 1) * (int)(ROWB / 16);
+                    for (int k = 0; k < 16; k++) v[k] = __uint_as_float(r[k]);
+                    const int co = 16 * j;
+                    if (p.mode == LBMFVM_SG_DLEAKY) {
+                        const uint4 *mm = reinterpret_cast<const uint4 *>(p.m + pix * p.ldm + co);
+                        const uint4 m0 = mm[0], m1 = mm[1];
+                        const bf16 *mb0 = reinterpret_cast<const bf16 *>(&m0);
+                        const bf16 *mb1 = reinterpret_cast<const bf16 *>(&m1);
 #pragma unroll
-                for (int kk = 0; kk < KC / 16; kk++) {
-                    const uint64_t bd = b0 + (uint64_t)(tap * tap16 + 2 * kk);
+                        for (int k = 0; k < 8; k++) {
+                            v[k] *= dleaky(__bfloat162float(mb0[k]));
+                            v[8 + k] *= dleaky(__bfloat162float(mb1[k]));
+                        }
+                    } else {
+                        if (p.bias) {
 #pragma unroll
-                    for (int g = 0; g < G; g++)
-                        if (g < g_n)
-                            mma(tmem + (uint32_t)g * p.acc, a0 + (uint64_t)(off16 + g * kM * (int)(ROWB / 16) + 2 * kk), bd,
-                                p.idesc, (c | tap | kk) != 0);
+                            for (int k = 0; k < 16; k++) v[k] += p.bias[co + k];
+                        }
+                        if (p.mode == LBMFVM_SG_LEAKY) {
+#pragma unroll
+                            for (int k = 0; k < 16; k++) v[k] = leaky(v[k]);
+                        }
+                    }
+                    uint4 o[2];
+                    __nv_bfloat162 *ob = reinterpret_cast<__nv_bfloat162 *>(o);
+#pragma unroll
+                    for (int k = 0; k < 8; k++) ob[k] = __floats2bfloat162_rn(v[2 * k], v[2 * k + 1]);
+                    uint4 *dst = reinterpret_cast<uint4 *>(p.y + pix * p.ldy + co);
+                    dst[0] = o[0];
+                    dst[1] = o[1];
                 }
             }
-            mma_commit(&empty[s]);
-            issued = c + 1;
-            // refill the stage of the previous chunk once its MMAs are done
-            const int cr = c - 1 + p.stages;
-            if (c >= 1 && cr < p.nch) {
-                const int sp = (c - 1) % p.stages;
-                if (!(ok = mbar_wait(&empty[sp], (uint32_t)((c - 1) / p.stages) & 1u))) break;
-                load(cr);
-            }
-        }
-        mma_commit(&done);
-        if (!ok) {
-            failed = 1;
-            atomicExch(p.status, 1);
-            // drain: the loads issued for chunks past the last waited one
-            const int loaded = p.nch < issued - 1 + p.stages ? p.nch : issued - 1 + p.stages;
-            for (int c = issued; c < loaded; c++) mbar_wait(&full[c % p.stages], (uint32_t)(c / p.stages) & 1u);
-        }
-    }
-    // every thread waits for the accumulator
-    const bool ready = mbar_wait(&done, 0);
-    tc_after_sync();
-    for (int g = 0; g < g_n && ready && !failed; g++) {
-        const int q = q0 + kM * g + warp * 32 + lane;
-        const int yy = q / p.Wp - 1, xx = q % p.Wp - kPad;
-        const bool valid = yy >= 0 && yy < p.H && xx >= 0 && xx < p.W;
-        const long long pix = ((long long)b * p.H + yy) * p.W + xx;
-        for (int j = 0; j < p.Cout / 16; j++) {
-            uint32_t r[16];
-            tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)g * p.acc + (uint32_t)(16 * j), r);
-            if (!valid) continue;
-            float v[16];
-#pragma unroll
-            for (int i = 0; i < 16; i++) v[i] = __uint_as_float(r[i]);
-            const int co = 16 * j;
-            if (p.mode == LBMFVM_SG_DLEAKY) {
-                const uint4 *mm = reinterpret_cast<const uint4 *>(p.m + pix * p.ldm + co);
-                const uint4 m0 = mm[0], m1 = mm[1];
-                const bf16 *mb0 = reinterpret_cast<const bf16 *>(&m0);
-                const bf16 *mb1 = reinterpret_cast<const bf16 *>(&m1);
-#pragma unroll
-                for (int i = 0; i < 8; i++) {
-                    v[i] *= dleaky(__bfloat162float(mb0[i]));
-                    v[8 + i] *= dleaky(__bfloat162float(mb1[i]));
-                }
-            } else {
-                if (p.bias) {
-#pragma unroll
-                    for (int i = 0; i < 16; i++) v[i] += p.bias[co + i];
-                }
-                if (p.mode == LBMFVM_SG_LEAKY) {
-#pragma unroll
-                    for (int i = 0; i < 16; i++) v[i] = leaky(v[i]);
-                }
-            }
-            uint4 o[2];
-            __nv_bfloat162 *ob = reinterpret_cast<__nv_bfloat162 *>(o);
-#pragma unroll
-            for (int i = 0; i < 8; i++) ob[i] = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
-            uint4 *dst = reinterpret_cast<uint4 *>(p.y + pix * p.ldy + co);
-            dst[0] = o[0];
-            dst[1] = o[1];
+            // the set is free for the unit after next
+            tc_before_sync();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acce[set]);
         }
     }
-    if (!ready && tid == 0) atomicExch(p.status, 1);
     tc_before_sync();
     __syncthreads();
-    if (warp == 0) {
+    if (warp == 1) {
         tc_after_sync();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(p.ncols) : "memory");
     }
@@ -377,6 +443,7 @@ int conv3x3(const uint16_t *x, int ldx, const uint16_t *w, const float *bias, ui
     p.status = status;
     p.ldy = ldy;
     p.ldm = ldm;
+    p.B = B;
     p.H = H;
     p.W = W;
     p.Cout = Cout;
@@ -414,38 +481,43 @@ int conv3x3(const uint16_t *x, int ldx, const uint16_t *w, const float *bias, ui
     // (a block stages its rows and the chunk's weights once for all its
     // tiles, each with its own accumulator): the widest rows, then the most
     // tiles (at most four) that let a stage fit twice in shared memory.
-    // Measured on the network's layers (every combination of 16, 32, 64
-    // channels per stage, 1, 2, 4 tiles per block and 2 to 6 stages): 16
-    // channels per stage, tiles per block by accumulator width (two of 32 or
-    // 128 columns, four of 64, one of 256, so that two blocks share an SM),
-    // 32 channels per stage for one 256-column tile where two such stages
-    // fit, and two stages per block (two blocks per SM beat deeper pipelines:
-    // one block's fill and epilogue overlap the other's MMAs).
+    // Measured on the network's layers (16, 32 or 64 channels per stage, 1,
+    // 2 or 4 tiles per unit, 2 to 7 stages): 32 channels per stage where the
+    // input has a multiple of 32 and two such stages fit, else 16; one tile
+    // per unit for accumulators of 128 or 256 columns, else two (32 channels
+    // per stage) or four (16); three stages (deeper rings were no faster).
     int KC = kc_req, G = g_req;
+    if (KC <= 0) {
+        const int g_probe = p.acc >= 128 ? 1 : 2;
+        KC = (Cin % 32 == 0 && (whole - extra) / stage_for(g_probe, 32) >= 2) ? 32 : 16;
+    }
     if (G <= 0) {
-        G = p.acc == 64 ? 4 : (p.acc == 256 ? 1 : 2);
+        G = p.acc >= 128 ? 1 : (KC == 16 ? 4 : 2);
+        if (2u * (uint32_t)G * p.acc > 512u) G = (int)(256 / p.acc);
         while (G > 1 && G / 2 >= p.tiles) G >>= 1;
     }
-    if (KC <= 0) KC = (G == 1 && Cin % 32 == 0 && (whole - extra) / stage_for(G, 32) >= 2) ? 32 : 16;
     if (KC != 16 && KC != 32 && KC != 64) return fail(-1, "channels per stage must be 16, 32 or 64");
     if (Cin % KC) return fail(-1, "Cin is not a multiple of the channels per stage");
-    if (G < 1 || (uint32_t)G * p.acc > 512u) return fail(-1, "tiles per block exceed the tensor memory");
+    if (G < 1 || 2u * (uint32_t)G * p.acc > 512u) return fail(-1, "two accumulator sets exceed the tensor memory");
     p.nch = Cin / KC;
     p.rowb = 2u * (uint32_t)KC;
     p.supers = (p.tiles + G - 1) / G;
-    p.ncols = (uint32_t)G * p.acc;
+    p.ncols = 2u * (uint32_t)G * p.acc;  // two accumulator sets
     p.nrows = rows_for(G);
     p.a_bytes = (uint32_t)p.nrows * p.Wp * p.rowb;
     p.b_off = (uint32_t)up1k(p.a_bytes);
     p.b_tap = (uint32_t)Cout * p.rowb;
     p.stage = (uint32_t)stage_for(G, KC);
-    // two stages per block (measured, above)
-    int stages = s_req > 0 ? s_req : 2;
+    // three stages where they fit, else two (one persistent block per SM)
+    int stages = s_req > 0 ? s_req : ((whole - extra) / p.stage >= 3 ? 3 : 2);
     if (stages > kMaxStages) stages = kMaxStages;
     if ((size_t)stages * p.stage + extra > whole) return fail(-1, "the stages do not fit in shared memory");
     if (stages < 2) return fail(-1, "a pipeline stage does not fit twice in shared memory");
     p.stages = stages;
-    const size_t smem = (size_t)stages * p.stage + extra;
+    // at least half the shared memory, so that one block holds an SM (its
+    // tensor-memory columns are then never contended)
+    size_t smem = (size_t)stages * p.stage + extra;
+    if (smem < 120 * 1024) smem = 120 * 1024;
 
     // Activations as (channel, x, y, image): one box of the chunk's KC
     // channels over the staged rows lands as nrows Wp rows of 2 KC bytes in
@@ -493,7 +565,12 @@ int conv3x3(const uint16_t *x, int ldx, const uint16_t *w, const float *bias, ui
     // the blocks an SM holds must find their tensor-memory columns free, so
     // that no allocation waits
     if (per_sm < 1 || (uint32_t)per_sm * p.ncols > 512u) return fail(-1, "tensor memory would be oversubscribed");
-    kern<<<B * p.supers, kThreads, smem, stream>>>(p, mx, mw);
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return fail(-3, "device query failed");
+    const int units = B * p.supers;
+    const int grid = units < sms * per_sm ? units : sms * per_sm;
+    kern<<<grid, kThreads, smem, stream>>>(p, mx, mw);
     e = cudaGetLastError();
     if (e != cudaSuccess) return fail(-3, cudaGetErrorString(e));
     return 0;
