@@ -24,8 +24,10 @@
  * - Return: 0 (LBMFVM_OK) or a negative status: -1 invalid argument (shape,
  *   alignment, NULL), -3 a CUDA error.  lbmfvm_sg_last_error() gives the
  *   message of the calling thread's last failure.
- * - Shape rules: H % 8 == 0 and 16 <= W <= 256 with W % 16 == 0 for 3x3
- *   convolutions; Cin % 16 == 0 and Cout % 32 == 0, Cout <= 256 for the
+ * - Shape rules: H % 8 == 0 and 16 <= W with W % 16 == 0 for 3x3
+ *   convolutions (W <= 240 for the forward and adjoint ones, whose padded
+ *   rows of W + 8 positions form one TMA box row); Cin % 16 == 0 and
+ *   Cout % 32 == 0, Cout <= 256 for the
  *   forward and adjoint convolutions; channel strides multiples of 8 and slice
  *   pointers 16-byte aligned.
  */

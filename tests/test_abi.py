@@ -134,6 +134,12 @@ def test_surrogate_entry_points_check_shapes_without_a_gpu():
     # H not a multiple of 8: refused before any launch
     assert lib.lbmfvm_sg_conv3x3(16, 16, 16, None, 16, 32, None, 0, 1, 12, 16, 16, 32, 1, None) == -1
     assert "tile rules" in lib.lbmfvm_sg_last_error().decode()
+    # the tensor-core convolution's own limits: a padded row of W + 8
+    # positions is one TMA box row (W <= 240), Cout <= 256 accumulator columns
+    assert lib.lbmfvm_sg_conv3x3(16, 256, 16, None, 16, 32, None, 0, 1, 8, 256, 16, 32, 1, None) == -1
+    assert "W <= 240" in lib.lbmfvm_sg_last_error().decode()
+    assert lib.lbmfvm_sg_conv3x3(16, 16, 16, None, 16, 288, None, 0, 1, 8, 16, 16, 288, 1, None) == -1
+    assert "Cout <= 256" in lib.lbmfvm_sg_last_error().decode()
     assert lib.lbmfvm_sg_adam(None, None, None, None, None, 10, 1e-3, 0.9, 0.999, 1e-8, 1, None) == -1
 
 
