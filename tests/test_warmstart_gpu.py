@@ -45,7 +45,10 @@ def test_trained_network_saves_steps_and_keeps_the_steady_state():
     # same steady state, to the accuracy a 1e-6 residual leaves
     assert np.abs(nu_warm - nu_cold).max() <= 1e-2 * np.abs(nu_cold).max()
     print(f"steps to 1e-6: warm {warm.sum()} / cold {cold.sum()} = {warm.sum() / cold.sum():.4f}")
-    assert warm.sum() <= 0.92 * cold.sum(), (warm.sum(), cold.sum())
+    # measured on GB300: 743 000 against 882 500 steps (0.842); the step
+    # counts follow from deterministic kernels and weights, so the bound sits
+    # just above the measurement
+    assert warm.sum() <= 0.85 * cold.sum(), (warm.sum(), cold.sum())
     untrained = S.Surrogate(net.widths, seed=3)
     blind, rb, _ = run(cases, untrained)
     assert (rb < 1e-6).all()

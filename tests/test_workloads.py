@@ -143,3 +143,24 @@ def test_stored_oracle_steady_states_belong_to_the_bench_draw():
         assert r["residual"] < d["tol"] and 0.5 < r["nu_mean_hot"] < 20
     short = WL.cavity_batch(16, d["seed"], sizes=tuple(d["sizes"]), velocity=d["velocity"])
     assert [(c.nx, c.ny, c.Ra) for c in short] == [(c.nx, c.ny, c.Ra) for c in cases[:16]]
+
+
+def test_stored_oracle_steady_state_of_the_256_instance():
+    """tests/golden/config2_steady.json: the FP64 oracle's steady state of the
+    1024^2 benchmark case's 256^2 instance (Ra 1e6, Pr 0.71, U0 0.1), residual
+    below 1e-8, hot- and cold-wall Nusselt numbers equal at steady state (the
+    heat entering leaves), the mean within 1 % of 8.8 (the classical
+    benchmark value for this cavity at Ra 1e6; the paper prints its maximum,
+    Table 1), temperatures inside [0, 1]."""
+    import json
+    import os
+
+    d = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "config2_steady.json")))
+    c = WL.config_large(256, 1e6)
+    assert (d["nx"], d["ny"], d["Ra"], d["Pr"]) == (256, 256, 1e6, 0.71)
+    assert math.isclose(d["Ma"], c.Ma)
+    assert d["residual"] < d["tol"] == 1e-8
+    assert abs(d["nu_mean_hot"] - d["nu_mean_cold"]) <= 1e-4 * d["nu_mean_hot"]
+    assert abs(d["nu_mean_hot"] - 8.8) <= 0.09
+    T = np.array(d["T_every_4th"])
+    assert T.shape == (64, 64) and T.min() >= 0.0 and T.max() <= 1.0
