@@ -47,18 +47,27 @@ def main():
     count = int(sys.argv[1]) if len(sys.argv) > 1 else 32
     procs = int(sys.argv[2]) if len(sys.argv) > 2 else os.cpu_count()
     sizes = tuple(int(x) for x in sys.argv[3].split(",")) if len(sys.argv) > 3 else SIZES
+    name = "steady_nusselt.json" if sizes == SIZES else "steady_nusselt_%s.json" % "_".join(map(str, sizes))
+    # rows already stored for this draw are kept (a longer draw extends a
+    # shorter one: its first cavities are the same)
+    kept = {}
+    try:
+        old = json.load(open(os.path.join(HERE, name)))
+        if old.get("seed") == SEED and tuple(old.get("sizes", ())) == sizes and old.get("tol") == TOL:
+            kept = {r["index"]: r for r in old["cavities"] if r["index"] < count}
+    except (OSError, ValueError):
+        pass
     with mp.get_context("spawn").Pool(procs) as pool:
         # the largest cavities first, so that the pool ends together
         from paper_1908_08386_gb300 import workloads as WL
 
         cases = WL.cavity_batch(count, SEED, sizes=sizes)
-        order = sorted(range(count), key=lambda i: -cases[i].nx * cases[i].ny)
-        rows = pool.map(steady_nusselt, [(i, sizes) for i in order], chunksize=1)
+        todo = sorted((i for i in range(count) if i not in kept), key=lambda i: -cases[i].nx * cases[i].ny)
+        rows = list(kept.values()) + pool.map(steady_nusselt, [(i, sizes) for i in todo], chunksize=1)
     rows.sort(key=lambda r: r["index"])
     out = {"_source": "FP64 CPU oracle (oracle/lbmfvm_oracle.c) run to a steady residual below 1e-8 "
                       "(checks every 1000 steps) by tests/golden/make_steady_nusselt.py",
            "seed": SEED, "sizes": list(sizes), "velocity": "capped", "tol": TOL, "cavities": rows}
-    name = "steady_nusselt.json" if sizes == SIZES else "steady_nusselt_%s.json" % "_".join(map(str, sizes))
     with open(os.path.join(HERE, name), "w") as fh:
         json.dump(out, fh, indent=1)
 
