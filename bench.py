@@ -545,7 +545,7 @@ def main():
     ap.add_argument("--sizes", default="64,96,128,192,256,384,512")
     ap.add_argument("--velocity", choices=["capped", "substeps"], default="capped",
                     help="velocity scale of the uneven draw: capped U0, or U0 = 0.1 with energy sub-steps")
-    ap.add_argument("--tts-cavities", type=int, default=32,
+    ap.add_argument("--tts-cavities", type=int, default=64,
                     help="cavities of the default line's time-to-steady sample (0 skips it)")
     ap.add_argument("--tts-sizes", default="64,96,128")
     ap.add_argument("--seed", type=int, default=20190822)
