@@ -51,6 +51,7 @@
 #include <stdint.h>
 
 #include <cstdio>
+#include <mutex>
 
 #include "conv_tc.h"
 #include "surrogate.h"
@@ -414,10 +415,16 @@ EncodeTiledFn encode_tiled() {
     return fn;
 }
 
+// One status word per device, allocated on the device's first use.
 int *status_word() {
-    static int *word = nullptr;
-    if (!word && cudaMalloc(&word, sizeof(int)) == cudaSuccess) cudaMemset(word, 0, sizeof(int));
-    return word;
+    constexpr int kMaxDevices = 64;
+    static int *words[kMaxDevices] = {};
+    static std::mutex mu;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return nullptr;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!words[dev] && cudaMalloc(&words[dev], sizeof(int)) == cudaSuccess) cudaMemset(words[dev], 0, sizeof(int));
+    return words[dev];
 }
 
 }  // namespace
