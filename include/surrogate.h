@@ -129,6 +129,14 @@ int lbmfvm_sg_resample_fields(const float *pred, int32_t H, int32_t W, const uin
  * launch's output was not written; the word is cleared), -3 on a CUDA error. */
 int lbmfvm_sg_check(void *stream);
 
+/* Fault-injection hook for testing the bounded waits of the forward and
+ * adjoint convolutions: block 0 of the next lbmfvm_sg_conv3x3 launch skips its
+ * first staged load, so that the waits for it give up after about a second
+ * each; that block's output is not written, the status word is set (the next
+ * lbmfvm_sg_check returns -4) and the block drains what it issued before it
+ * returns.  Nothing faults and the CUDA context stays usable.  Returns 0. */
+int lbmfvm_sg_inject_stall(void);
+
 const char *lbmfvm_sg_last_error(void);
 
 #ifdef __cplusplus

@@ -23,6 +23,10 @@ int conv3x3(const uint16_t *x, int ldx, const uint16_t *w, const float *bias, ui
 // CUDA error.
 int check(cudaStream_t stream);
 
+// The next conv3x3 call's block 0 skips its first staged load, so that its
+// bounded waits run out (a test of the failure path: nothing faults).
+void inject_stall();
+
 }  // namespace lbmfvm_sg_tc
 
 #endif

@@ -430,6 +430,11 @@ int lbmfvm_sg_conv3x3(const uint16_t *x, int32_t ldx, const uint16_t *w, const f
                                  g_sg_err, sizeof(g_sg_err));
 }
 
+int lbmfvm_sg_inject_stall(void) {
+    lbmfvm_sg_tc::inject_stall();
+    return kOk;
+}
+
 int lbmfvm_sg_check(void *stream) {
     const int r = lbmfvm_sg_tc::check((cudaStream_t)stream);
     if (r == -4) return sg_fail(-4, "a bounded wait of the tensor-core convolution ran out");

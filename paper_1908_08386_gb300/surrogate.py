@@ -32,7 +32,7 @@ SG_EXPORTS = (
     "lbmfvm_sg_conv3x3", "lbmfvm_sg_flip", "lbmfvm_sg_conv3x3_wgrad", "lbmfvm_sg_pool2", "lbmfvm_sg_pool2_backward",
     "lbmfvm_sg_upsample2", "lbmfvm_sg_upsample2_backward", "lbmfvm_sg_conv1x1", "lbmfvm_sg_conv1x1_backward",
     "lbmfvm_sg_mse", "lbmfvm_sg_adam", "lbmfvm_sg_encode", "lbmfvm_sg_resample_mask", "lbmfvm_sg_resample_fields",
-    "lbmfvm_sg_check", "lbmfvm_sg_last_error",
+    "lbmfvm_sg_check", "lbmfvm_sg_inject_stall", "lbmfvm_sg_last_error",
 )
 
 _ready = False
@@ -59,6 +59,7 @@ def _lib():
             "lbmfvm_sg_resample_mask": [vp, i32, i32, vp, i32, i32, vp],
             "lbmfvm_sg_resample_fields": [vp, i32, i32, vp, i32, i32, f, vp, vp, vp, vp],
             "lbmfvm_sg_check": [vp],
+            "lbmfvm_sg_inject_stall": [],
         }
         for name, args in sig.items():
             fn = getattr(L, name)

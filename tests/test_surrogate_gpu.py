@@ -290,3 +290,26 @@ def test_encode_and_resampling_follow_their_definitions():
     assert Tn[j, i] == pytest.approx(min(max(val[2], 0.0), 1.0), rel=1e-5, abs=1e-7)
     assert np.all(un[big == 1] == 0) and np.all(un[0, :] == 0) and np.all(un[:, -1] == 0)
     assert Tn.min() >= 0.0 and Tn.max() <= 1.0
+
+
+def test_convolution_waits_give_up_and_report_without_a_fault():
+    """A staged load that never comes (injected on the host: block 0 skips
+    it) makes the convolution's bounded waits run out: the status word
+    reports it (-4), nothing faults, and the next convolution on the same
+    context is correct."""
+    rng = np.random.default_rng(9)
+    B, H, W, cin, cout = 2, 16, 32, 32, 64
+    x, xr = bf(rng.standard_normal((B, H, W, cin)))
+    w, wr = bf(rng.standard_normal((cout, 9, cin)) / math.sqrt(9 * cin))
+    y = torch.zeros(B, H, W, cout, dtype=torch.bfloat16, device="cuda")
+    S.check()
+    S.call("lbmfvm_sg_inject_stall")
+    S.conv3x3(S.View(x), w.data_ptr(), None, S.View(y), B, H, W, cin, cout, S.LINEAR)
+    with pytest.raises(S.LbmfvmError) as e:
+        S.check()
+    assert e.value.code == -4
+    S.check()  # the word was cleared
+    S.conv3x3(S.View(x), w.data_ptr(), None, S.View(y), B, H, W, cin, cout, S.LINEAR)
+    S.check()
+    ref = R.conv3x3(xr, wr.reshape(cout, 3, 3, cin), 0.0)
+    assert rel(f64(y), ref) <= 1e-2
