@@ -29,6 +29,8 @@ struct lbmfvm_batch {
     lbmfvm_grid_t atlas_grid;       // what the upper grids are created from
     AtlasSpec spec;
     lbmfvm_opts_t opts;
+    bool auto_shape = false;        // tile shapes chosen by the library (not pinned by opts.tma_config)
+    int base_cfg[3] = {-1, -1, -1}; // each level's shape for its whole packed grid
     struct Cav {
         lbmfvm_grid_t grid;
         int x0, y0;
@@ -202,13 +204,39 @@ int bcheck_h(lbmfvm_batch_t *b, lbmfvm_t *h, int code) {
     return code;
 }
 
+// A level whose active cavities, once some have left it, fill fewer tiles
+// than the GPU has SMs is bound by the latency of one tile rather than by
+// throughput: it takes the small-grid shape a single cavity of that size
+// would (64 x 8 for 32- and 16-bit storage, 32 x 8 with ring warps for
+// 64-bit), and its own shape again when the active set grows.  Shapes never
+// change results.
+int reshape_level(lbmfvm_batch_t *b, int l) {
+    lbmfvm_t *h = b->lv[l];
+    if (!b->auto_shape || !h || !h->use_tma || h->fv_quick || h->L.split || h->grid2) return LBMFVM_OK;
+    if (b->base_cfg[l] < 0) b->base_cfg[l] = h->tma_config;
+    long long active = 0, all = 0;
+    for (size_t c = 0; c < h->atlas_cavs.size(); c++) {
+        const long long nodes = (long long)h->atlas_cavs[c].nx * h->atlas_cavs[c].ny;
+        all += nodes;
+        if (h->atlas_active[c]) active += nodes;
+    }
+    if (active == 0) return LBMFVM_OK;  // nothing to step: keep the shape
+    const bool wide = store_size(h->prec) == 8;
+    const long long tiles = wide ? active / (32 * 8) : active / (64 * 16);
+    const int want = (active < all && tiles < h->num_sms) ? (wide ? 4 : 2) : b->base_cfg[l];
+    if (want == h->tma_config) return LBMFVM_OK;
+    h->tma_config = want;
+    return setup_kernels(h);  // new tensor maps and tile lists; the step graph is captured again
+}
+
 int set_active(lbmfvm_batch_t *b, int i, bool active) {
     if (b->cav[i].active == active) return LBMFVM_OK;
     lbmfvm_t *h = hnd(b, i);
     if (!active) b->cav[i].parity = h->parity;
     b->cav[i].active = active;
     h->atlas_active[i] = active ? 1 : 0;
-    return bcheck_h(b, h, upload_tiles(h, h->tile_w, h->tile_h));
+    if (int r = bcheck_h(b, h, upload_tiles(h, h->tile_w, h->tile_h))) return r;
+    return bcheck_h(b, h, reshape_level(b, b->cav[i].level));
 }
 
 // The packed grid of ladder level l, created (every cavity inactive) on first use.
@@ -489,6 +517,7 @@ int lbmfvm_batch_create(int32_t n, const lbmfvm_grid_t *grids, const uint8_t *co
     b->atlas_grid = atlas;
     b->spec = std::move(spec);
     b->opts = o;
+    b->auto_shape = o.tma_config == LBMFVM_TMA_AUTOTUNE || o.tma_config == LBMFVM_TMA_DEFAULT;
     // wall temperatures per cavity for the initial-state kernel
     std::vector<double> tw(4 * (size_t)n);
     for (int i = 0; i < n; i++)

@@ -173,3 +173,27 @@ def test_default_shape_spreads_small_grids_over_more_sms():
             want = 4 if per_node * n * n <= l2 else 5
         assert cav.tma_config == want, (n, store, cav.tma_config)
         cav.close()
+
+
+def test_level_shape_follows_the_active_set_and_changes_no_result():
+    """Once the conductive cavities have converged and left, the convective
+    one alone fills fewer tiles than the GPU has SMs: its level takes the
+    small-grid shape (64 x 8, two blocks per SM) and stays bitwise equal to
+    the same batch pinned to one shape."""
+    cap = lambda n, Ra, Pr: min(0.1, 0.2 * math.sqrt(Ra * Pr) / (n - 1)) * math.sqrt(3.0)
+    cases = [WL.CavityCase(160, 160, 1e3, 0.71, cap(160, 1e3, 0.71), name=f"conduction{k}") for k in range(4)]
+    cases.append(WL.CavityCase(256, 256, 1e6, 0.71, MA, name="convection"))
+    auto = L.Batch(cases, store="f32", tma_config="default")
+    pinned = L.Batch(cases, store="f32", tma_config=1)
+    active = None
+    for _ in range(40):
+        auto.run(tol=1e-5, check_every=500, max_steps=10000)
+        pinned.run(tol=1e-5, check_every=500, max_steps=10000)
+        active = [auto.info(i)[1] for i in range(len(cases))]
+        if not any(active[:4]) or not active[4]:
+            break
+    assert not any(active[:4]) and active[4], active
+    assert auto.tma_config("f32") == 2 and pinned.tma_config("f32") == 1
+    for i in range(len(cases)):
+        assert np.array_equal(np.stack(auto.fields(i)), np.stack(pinned.fields(i))), cases[i].name
+        assert auto.info(i)[0] == pinned.info(i)[0]
