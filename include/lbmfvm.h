@@ -425,7 +425,11 @@ int lbmfvm_batch_substeps(const lbmfvm_batch_t *b, int32_t i, int32_t *substeps)
  * second rule off. */
 int lbmfvm_batch_set_polish(lbmfvm_batch_t *b, int32_t prec, double r_switch, int32_t stall_checks);
 /* TMA tile shape of the batch's packed grid in precision prec (-1 while that
- * level of the ladder has not been created). */
+ * level of the ladder has not been created).  Unless opts.tma_config pinned a
+ * shape, a level changes its shape with its active set: once cavities have
+ * left it and the rest fill fewer tiles than the GPU has SMs, it takes the
+ * small-grid shape of LBMFVM_TMA_DEFAULT, and its first shape again when the
+ * set grows (shapes never change results). */
 int lbmfvm_batch_kernel_info(const lbmfvm_batch_t *b, int32_t prec, int32_t *tma_config);
 /* Storage precision cavity i is currently stepped in (lbmfvm_prec). */
 int lbmfvm_batch_precision(const lbmfvm_batch_t *b, int32_t i, int32_t *prec);
